@@ -1,0 +1,184 @@
+/*
+ * skeweig.h -- C ABI of a single-GPU (GB300, sm_103a) dense eigensolver for
+ * real skew-symmetric matrices, following the two-step method of Penke,
+ * Marek, Vorwerk, Draxl and Benner ("High Performance Solution of
+ * Skew-symmetric Eigenvalue Problems with Applications in Solving the
+ * Bethe-Salpeter Eigenvalue Problem", Parallel Computing).
+ *
+ * Problem (Sec. 1 and Algorithm 1): A = -A^T in R^{n x n}.  Its eigenvalues
+ * are +-i*lambda_j (Sec. 2.1: they come in pairs and the eigenvectors of the
+ * pair are complex conjugates, so half the spectrum suffices, Sec. 4.1 "50%").
+ * The solver returns the nev <= floor(n/2) largest lambda_j >= 0, descending,
+ * and eigenvectors Z = Z_re + i Z_im with
+ *     A Z[:, j] = i * lambda[j] * Z[:, j],   Z^H Z = I.
+ * conj(Z[:, j]) is the eigenvector of -i*lambda[j].
+ *
+ * Route (all on the device, Algorithm 1 in its two-step form, Sec. 2.1/2.3.2):
+ *   full-to-band (blocked Householder panels, compact WY Q = I - V T V^T,
+ *   Eq. 7; skew trailing update A <- A + V W^T - W V^T, Eqs. 8-10 with
+ *   U1 = -U2), band-to-tridiagonal bulge chase (Sec. 2.3.2, skew SYR2/SYMV),
+ *   the Lemma-1 link tridiag(alpha, 0, alpha) = -i D^H T D, bisection and
+ *   inverse iteration on that symmetric tridiagonal (Sec. 3), back
+ *   transformation by D (Algorithm 1 step 3) on real and imaginary parts
+ *   separately (Sec. 2.3), then by Q_trd and Q_band (Sec. 2.1, step 3 a/b).
+ *
+ * Conventions for every entry point unless stated otherwise:
+ *   - Matrices are column-major FP64: element (i, j) at ptr[i + j*ld].
+ *   - Pointers are DEVICE pointers owned by the caller (the *_host entry is
+ *     the exception).  Only the strict lower triangle of A is read; A is
+ *     treated as L - L^T and is never written.
+ *   - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Work is stream-ordered.
+ *   - Return codes: 0 success; -k argument k invalid; 1000 + j inverse
+ *     iteration did not converge for eigenpair j (results still written);
+ *     SKEW_ERR_* below.
+ */
+#ifndef SKEWEIG_H
+#define SKEWEIG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SKEW_OK 0
+#define SKEW_INFO_INVIT_BASE 1000      /* 1000 + j: eigenvector j did not converge */
+#define SKEW_ERR_CUDA 2001             /* a CUDA runtime call failed */
+#define SKEW_ERR_NOMEM 2002            /* device allocation failed */
+#define SKEW_ERR_DEVICE_TIMEOUT 2003   /* a capped device-side wait gave up */
+#define SKEW_ERR_UNSUPPORTED 2004      /* mode/size not supported on this GPU */
+#define SKEW_ERR_NONFINITE 2005        /* A holds NaN or Inf (check_finite) */
+#define SKEW_ERR_WORKSPACE 2006        /* caller workspace too small */
+#define SKEW_ERR_LAUNCH 2007           /* cooperative launch could not fit */
+
+typedef enum {
+    SKEW_MODE_FP64 = 0,            /* every step in FP64 */
+    SKEW_MODE_MIXED_BF16X3 = 1,    /* dense contractions as BF16x3 splits on tcgen05 */
+    SKEW_MODE_MIXED_INT8 = 2       /* INT8 Ozaki splits: tcgen05 kind::i8 is not
+                                      available on sm_103a -> SKEW_ERR_UNSUPPORTED */
+} skew_mode;
+
+/* Fault hooks (host-side injection for tests; never fault the GPU). */
+#define SKEW_FAULT_NOMEM 1         /* pretend the workspace allocation failed */
+#define SKEW_FAULT_INVIT_NOCONV 2  /* give inverse iteration zero iterations */
+#define SKEW_FAULT_TINY_WAIT 4     /* make device waits give up at once */
+
+typedef struct {
+    int mode;          /* skew_mode; default SKEW_MODE_FP64 */
+    int band;          /* panel width = band width b, a multiple of 64; 0 -> 64 */
+    int check_finite;  /* 1: scan A for NaN/Inf first (SKEW_ERR_NONFINITE) */
+    int fault;         /* SKEW_FAULT_* bits, tests only; 0 in production */
+    int reserved[4];
+} skew_opts;
+
+/* Default options (FP64 mode, b = 64). */
+void skew_opts_default(skew_opts* opts);
+
+/* Human-readable text for a return code. Never NULL. */
+const char* skew_eig_strerror(int code);
+
+/*
+ * Full solve, device buffers.  Eigenvalues lambda[0..nev-1] (descending,
+ * >= 0) and, unless Z_re == Z_im == NULL, Z_re / Z_im (n x nev, leading
+ * dimension n).  Allocates its workspace with cudaMallocAsync on `stream`,
+ * synchronises `stream` at the end and returns the numerical status.
+ * Arguments: 1 n >= 0, 2 A (n x n, ld lda), 3 lda >= max(1, n),
+ * 4 0 <= nev <= n/2, 5 lambda (NULL only if nev == 0), 6/7 Z_re/Z_im (both
+ * NULL or both set), 8 stream.
+ */
+int skew_eig(int n, const double* A, int lda, int nev, double* lambda,
+             double* Z_re, double* Z_im, void* stream);
+
+/* Bytes of device workspace skew_eig_ex needs for (n, nev, opts). */
+size_t skew_eig_workspace_size(int n, int nev, const skew_opts* opts);
+
+/*
+ * Asynchronous full solve with caller workspace (>= skew_eig_workspace_size
+ * bytes, 256-byte aligned).  ldz >= max(1, n) is the leading dimension of
+ * Z_re / Z_im.  The numerical status is written to *d_info (device int) in
+ * stream order; the return value only reports argument and launch errors.
+ * Arguments are numbered as in skew_eig with 8 ldz, 9 opts (NULL = default),
+ * 10 workspace, 11 ws_bytes, 12 d_info, 13 stream.
+ */
+int skew_eig_ex(int n, const double* A, int lda, int nev, double* lambda,
+                double* Z_re, double* Z_im, int ldz, const skew_opts* opts,
+                void* workspace, size_t ws_bytes, int* d_info, void* stream);
+
+/*
+ * Full solve from HOST buffers (A, lambda, Z_re, Z_im in host memory, ideally
+ * pinned).  Copies A in, solves, copies results out; synchronises `stream`.
+ * Same argument numbering and return codes as skew_eig.
+ */
+int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda,
+                  double* Z_re, double* Z_im, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points (the steps of Algorithm 1 one at a time; used by the
+ * per-stage parity tests).  Each takes a caller workspace of at least the
+ * size its *_ws function returns, and a device status word *d_status (int,
+ * set to a nonzero SKEW_ERR_* / 1000+j code on a device-side failure; the
+ * caller zeroes it).
+ * --------------------------------------------------------------------- */
+
+/* Full-to-band reduction (Sec. 2.3.2, Eqs. 7-10), in place on W (n x n, ld
+ * ldw).  On entry W's strict lower triangle holds A.  On exit, for panel
+ * p = 0..P-1 (P = max(0, floor((n-2)/b))): the lower triangles of the
+ * diagonal b x b blocks and the upper triangles of the blocks
+ * W[(p+1)b:(p+2)b, pb:(p+1)b] hold the band (lower bandwidth b); the
+ * Householder vectors v (unit leading entry implicit) of panel p are stored
+ * below that, column pb+i holding v_i in rows (p+1)b+i+1 .. n-1 (Sec. 2.1:
+ * vectors stored in place of the eliminated columns).  Tfac (P x b x b,
+ * column-major b x b per panel) receives the upper-triangular T of
+ * Q_p = I - V_p T_p V_p^T.  b is a multiple of 64. */
+size_t skew_band_reduce_ws(int n, int b);
+int skew_band_reduce(int n, double* W, int ldw, int b, double* Tfac,
+                     void* ws, size_t ws_bytes, int* d_status, void* stream);
+
+/* Copy the band out of a reduced W into lower band storage AB ((2b+1) x n,
+ * ld ldab >= 2b+1): AB[d + c*ldab] = band(c+d, c), d = 0..b; rows b+1..2b
+ * (room for the bulge) are zeroed. */
+int skew_band_pack(int n, int b, const double* W, int ldw, double* AB, int ldab,
+                   void* stream);
+
+/* Band-to-tridiagonal bulge chase (Sec. 2.3.2).  AB as produced by
+ * skew_band_pack, overwritten.  Output alpha[0..n-2] with T[c, c+1] =
+ * alpha[c] (the Lemma-1 link input) and the chase reflectors: sweep s,
+ * step k has v (length b, v[0] = 1, zero-padded) at Vtrd[(k*(n-2) + s)*b]
+ * and tau at tautrd[k*(n-2) + s], k < skew_chase_steps(n, b). */
+int skew_chase_steps(int n, int b);
+size_t skew_chase_ws(int n, int b);
+int skew_band_to_tridiag(int n, int b, double* AB, int ldab, double* alpha,
+                         double* Vtrd, double* tautrd, void* ws, size_t ws_bytes,
+                         int* d_status, void* stream);
+
+/* Symmetric tridiagonal solve for S = tridiag(alpha, 0, alpha) (Lemma 1,
+ * Sec. 3: bisection + inverse iteration): the nev largest eigenvalues
+ * (descending) into lambda and, if Q != NULL, eigenvectors into Q (n x nev,
+ * ld ldq) with each vector's largest-modulus entry positive.  Here
+ * 1 <= nev <= n. */
+size_t skew_tridiag_ws(int n, int nev);
+int skew_tridiag_eig(int n, const double* alpha, int nev, double* lambda,
+                     double* Q, int ldq, void* ws, size_t ws_bytes,
+                     int* d_status, void* stream);
+
+/* Algorithm 1 step 3: X + iY = D Q, D = diag(i^r), r = 0..n-1. */
+int skew_dmap(int n, int k, const double* Q, int ldq, double* X, double* Y,
+              int ldz, void* stream);
+
+/* Z <- Q_trd Z (Sec. 2.1 step 3a) for the chase reflectors above; Z is
+ * n x k, ld ldz. */
+int skew_apply_qtrd(int n, int b, const double* Vtrd, const double* tautrd,
+                    double* Z, int ldz, int k, void* stream);
+
+/* Z <- Q_band Z (Sec. 2.1 step 3b) for a W / Tfac pair produced by
+ * skew_band_reduce; Z is n x k, ld ldz. */
+size_t skew_qband_ws(int n, int b, int k);
+int skew_apply_qband(int n, int b, const double* W, int ldw, const double* Tfac,
+                     double* Z, int ldz, int k, void* ws, size_t ws_bytes,
+                     void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKEWEIG_H */

@@ -85,13 +85,20 @@ int oracle_tridiagonalize(int n, const double *A, int lda, double *alpha,
         AT(V, c + 1, c, n) = 1.0;
         for (int i = 1; i < m; i++) AT(V, c + 1 + i, c, n) = x[i];
         const double *v = &AT(V, c + 1, c, n);
-        /* p = tau * A22 v, A22 = L[c+1:, c+1:] - L[c+1:, c+1:]^T */
-        for (int i = 0; i < m; i++) {
-            double s = 0.0;
-            for (int j = 0; j < i; j++) s += AT(L, c + 1 + i, c + 1 + j, n) * v[j];
-            for (int j = i + 1; j < m; j++) s -= AT(L, c + 1 + j, c + 1 + i, n) * v[j];
-            p[i] = t * s;
+        /* p = tau * A22 v, A22 = L[c+1:, c+1:] - L[c+1:, c+1:]^T, accumulated
+         * column by column: entry (i, j), i > j, adds L_ij v_j to p_i and
+         * subtracts L_ij v_i from p_j */
+        for (int i = 0; i < m; i++) p[i] = 0.0;
+        for (int j = 0; j < m; j++) {
+            const double *Lj = &AT(L, c + 1, c + 1 + j, n);
+            double sj = 0.0;
+            for (int i = j + 1; i < m; i++) {
+                p[i] += Lj[i] * v[j];
+                sj += Lj[i] * v[i];
+            }
+            p[j] -= sj;
         }
+        for (int i = 0; i < m; i++) p[i] *= t;
         /* A22 <- A22 + v p^T - p v^T (strict lower part) */
         for (int j = 0; j < m; j++)
             for (int i = j + 1; i < m; i++)

@@ -1,0 +1,288 @@
+"""Python binding of libskeweig.so, the GB300 skew-symmetric eigensolver.
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+(see ``include/skeweig.h`` for the contract of each entry point).  PyTorch
+supplies device memory and the current stream.  Matrices are column-major
+(Fortran-strided) float64 CUDA tensors; :func:`fortran` converts a tensor.
+
+If the shared library is missing the import still works but every call raises
+``RuntimeError`` -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libskeweig.so")
+
+SKEW_OK = 0
+SKEW_INFO_INVIT_BASE = 1000
+SKEW_ERR_CUDA = 2001
+SKEW_ERR_NOMEM = 2002
+SKEW_ERR_DEVICE_TIMEOUT = 2003
+SKEW_ERR_UNSUPPORTED = 2004
+SKEW_ERR_NONFINITE = 2005
+SKEW_ERR_WORKSPACE = 2006
+SKEW_ERR_LAUNCH = 2007
+
+SKEW_MODE_FP64 = 0
+SKEW_MODE_MIXED_BF16X3 = 1
+SKEW_MODE_MIXED_INT8 = 2
+
+SKEW_FAULT_NOMEM = 1
+SKEW_FAULT_INVIT_NOCONV = 2
+SKEW_FAULT_TINY_WAIT = 4
+
+# every entry point the header declares: name -> (restype, argtypes)
+_i, _d, _p, _sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+SIGNATURES = {
+    "skew_opts_default": (None, [_p]),
+    "skew_eig_strerror": (ctypes.c_char_p, [_i]),
+    "skew_eig": (_i, [_i, _p, _i, _i, _p, _p, _p, _p]),
+    "skew_eig_workspace_size": (_sz, [_i, _i, _p]),
+    "skew_eig_ex": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
+    "skew_eig_host": (_i, [_i, _p, _i, _i, _p, _p, _p, _p]),
+    "skew_band_reduce_ws": (_sz, [_i, _i]),
+    "skew_band_reduce": (_i, [_i, _p, _i, _i, _p, _p, _sz, _p, _p]),
+    "skew_band_pack": (_i, [_i, _i, _p, _i, _p, _i, _p]),
+    "skew_chase_steps": (_i, [_i, _i]),
+    "skew_chase_ws": (_sz, [_i, _i]),
+    "skew_band_to_tridiag": (_i, [_i, _i, _p, _i, _p, _p, _p, _p, _sz, _p, _p]),
+    "skew_tridiag_ws": (_sz, [_i, _i]),
+    "skew_tridiag_eig": (_i, [_i, _p, _i, _p, _p, _i, _p, _sz, _p, _p]),
+    "skew_dmap": (_i, [_i, _i, _p, _i, _p, _p, _i, _p]),
+    "skew_apply_qtrd": (_i, [_i, _i, _p, _p, _p, _i, _i, _p]),
+    "skew_qband_ws": (_sz, [_i, _i, _i]),
+    "skew_apply_qband": (_i, [_i, _i, _p, _i, _p, _p, _i, _i, _p, _sz, _p]),
+}
+
+
+class skew_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("band", ctypes.c_int), ("check_finite", ctypes.c_int),
+                ("fault", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libskeweig.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1912_04062_gb300/build.py "
+                               "(or __graft_entry__.build()) first; there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SkewError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        msg = lib().skew_eig_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (code {code})")
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise SkewError(code, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def fortran(t):
+    """Column-major (Fortran-strided) copy of a 2-D tensor, unless it already is."""
+    if t.dim() == 2 and t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def fortran_empty(rows: int, cols: int, device="cuda"):
+    torch = _torch()
+    return torch.empty((cols, rows), dtype=torch.float64, device=device).t()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _ld(t):
+    return max(1, t.stride(1)) if t.dim() == 2 else max(1, t.shape[0])
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _as_device_f64(A):
+    torch = _torch()
+    if not (A.is_cuda and A.dtype == torch.float64):
+        raise TypeError("expected a float64 CUDA tensor")
+    return fortran(A)
+
+
+@dataclass
+class Options:
+    mode: int = SKEW_MODE_FP64
+    band: int = 64
+    check_finite: int = 0
+    fault: int = 0
+
+    def c(self):
+        o = skew_opts()
+        lib().skew_opts_default(ctypes.byref(o))
+        o.mode, o.band, o.check_finite, o.fault = self.mode, self.band, self.check_finite, self.fault
+        return o
+
+
+def skew_eig(A, nev: int, vectors: bool = True, stream=None):
+    """Synchronous solve (device buffers).  Returns (lam, Z_re, Z_im)."""
+    torch = _torch()
+    A = _as_device_f64(A)
+    n = A.shape[0]
+    lam = torch.empty(max(nev, 1), dtype=torch.float64, device=A.device)
+    Zr = fortran_empty(n, nev, A.device) if vectors else None
+    Zi = fortran_empty(n, nev, A.device) if vectors else None
+    code = lib().skew_eig(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), _stream(stream))
+    _check(code, "skew_eig")
+    return lam[:nev], Zr, Zi
+
+
+def workspace_size(n: int, nev: int, opts: Options | None = None) -> int:
+    o = (opts or Options()).c()
+    return int(lib().skew_eig_workspace_size(n, nev, ctypes.byref(o)))
+
+
+def skew_eig_ex(A, nev: int, lam, Zr, Zi, workspace, d_info, opts: Options | None = None, stream=None) -> int:
+    """Asynchronous solve into caller buffers; returns the launch status."""
+    A = _as_device_f64(A)
+    n = A.shape[0]
+    o = (opts or Options()).c()
+    ldz = _ld(Zr) if Zr is not None else max(1, n)
+    return lib().skew_eig_ex(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), ldz, ctypes.byref(o),
+                             _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(d_info),
+                             _stream(stream))
+
+
+def skew_eig_host(A, nev: int, vectors: bool = True, stream=None):
+    """Solve from host (ideally pinned) float64 tensors; returns host tensors."""
+    torch = _torch()
+    A = fortran(A.to(torch.float64))
+    n = A.shape[0]
+    pin = torch.cuda.is_available()
+    lam = torch.empty(max(nev, 1), dtype=torch.float64, pin_memory=pin)
+    Zr = torch.empty((nev, n), dtype=torch.float64, pin_memory=pin).t() if vectors else None
+    Zi = torch.empty((nev, n), dtype=torch.float64, pin_memory=pin).t() if vectors else None
+    code = lib().skew_eig_host(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), _stream(stream))
+    _check(code, "skew_eig_host")
+    return lam[:nev], Zr, Zi
+
+
+# ----------------------------------------------------------------- stages
+def _status(device):
+    torch = _torch()
+    return torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def _ws(nbytes: int, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def band_reduce(A, b: int = 64, stream=None):
+    """Full-to-band reduction of skew A.  Returns (W, Tfac, status)."""
+    torch = _torch()
+    A = _as_device_f64(A)
+    n = A.shape[0]
+    W = fortran_empty(n, n, A.device)
+    W.copy_(A)
+    P = (n - 2) // b if n - 2 >= b else 0
+    Tfac = torch.zeros(max(P, 1) * b * b, dtype=torch.float64, device=A.device)
+    ws = _ws(lib().skew_band_reduce_ws(n, b), A.device)
+    st = _status(A.device)
+    code = lib().skew_band_reduce(n, _ptr(W), _ld(W), b, _ptr(Tfac), _ptr(ws), ws.numel(), _ptr(st), _stream(stream))
+    _check(code, "skew_band_reduce")
+    return W, Tfac, st
+
+
+def band_pack(W, b: int = 64, stream=None):
+    torch = _torch()
+    n = W.shape[0]
+    ldab = 2 * b + 1
+    AB = torch.zeros((max(n, 1), ldab), dtype=torch.float64, device=W.device)  # row c = column c of AB
+    _check(lib().skew_band_pack(n, b, _ptr(W), _ld(W), _ptr(AB), ldab, _stream(stream)), "skew_band_pack")
+    return AB
+
+
+def band_to_tridiag(AB, n: int, b: int = 64, stream=None):
+    """Bulge chase on packed band AB (n rows of length 2b+1).  Returns
+    (alpha, Vtrd, tautrd, status)."""
+    torch = _torch()
+    K = lib().skew_chase_steps(n, b)
+    nsw = max(n - 2, 1)
+    alpha = torch.zeros(max(n, 1), dtype=torch.float64, device=AB.device)
+    Vtrd = torch.zeros(max(K, 1) * nsw * b, dtype=torch.float64, device=AB.device)
+    tau = torch.zeros(max(K, 1) * nsw, dtype=torch.float64, device=AB.device)
+    ws = _ws(lib().skew_chase_ws(n, b), AB.device)
+    st = _status(AB.device)
+    code = lib().skew_band_to_tridiag(n, b, _ptr(AB), 2 * b + 1, _ptr(alpha), _ptr(Vtrd), _ptr(tau), _ptr(ws),
+                                      ws.numel(), _ptr(st), _stream(stream))
+    _check(code, "skew_band_to_tridiag")
+    return alpha[: max(n - 1, 0)], Vtrd, tau, st
+
+
+def tridiag_eig(alpha, nev: int, vectors: bool = True, stream=None):
+    """Eigenpairs of tridiag(alpha, 0, alpha): (lam desc, Q n x nev, status)."""
+    torch = _torch()
+    n = alpha.numel() + 1
+    a = torch.zeros(n, dtype=torch.float64, device=alpha.device)
+    a[: n - 1] = alpha
+    lam = torch.empty(nev, dtype=torch.float64, device=alpha.device)
+    Q = fortran_empty(n, nev, alpha.device) if vectors else None
+    ws = _ws(lib().skew_tridiag_ws(n, nev), alpha.device)
+    st = _status(alpha.device)
+    code = lib().skew_tridiag_eig(n, _ptr(a), nev, _ptr(lam), _ptr(Q), n, _ptr(ws), ws.numel(), _ptr(st),
+                                  _stream(stream))
+    _check(code, "skew_tridiag_eig")
+    return lam, Q, st
+
+
+def dmap(Q, stream=None):
+    n, k = Q.shape
+    Q = fortran(Q)
+    X = fortran_empty(n, k, Q.device)
+    Y = fortran_empty(n, k, Q.device)
+    _check(lib().skew_dmap(n, k, _ptr(Q), _ld(Q), _ptr(X), _ptr(Y), n, _stream(stream)), "skew_dmap")
+    return X, Y
+
+
+def apply_qtrd(Vtrd, tau, Z, b: int = 64, stream=None):
+    """Z <- Q_trd Z in place (Z Fortran-strided n x k)."""
+    n, k = Z.shape
+    _check(lib().skew_apply_qtrd(n, b, _ptr(Vtrd), _ptr(tau), _ptr(Z), _ld(Z), k, _stream(stream)), "skew_apply_qtrd")
+    return Z
+
+
+def apply_qband(W, Tfac, Z, b: int = 64, stream=None):
+    """Z <- Q_band Z in place."""
+    n, k = Z.shape
+    ws = _ws(lib().skew_qband_ws(n, b, k), Z.device)
+    _check(lib().skew_apply_qband(n, b, _ptr(W), _ld(W), _ptr(Tfac), _ptr(Z), _ld(Z), k, _ptr(ws), ws.numel(),
+                                  _stream(stream)), "skew_apply_qband")
+    return Z
+
+
+def strerror(code: int) -> str:
+    return lib().skew_eig_strerror(code).decode()

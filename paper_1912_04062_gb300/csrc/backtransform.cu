@@ -1,0 +1,161 @@
+// backtransform.cu -- eigenvector back transformations (Sec. 2.1, step 3 of
+// the two-step form: Q~ = Q_trd Q_diag, then Q = Q_band Q~; Sec. 2.3: applied
+// to the real and imaginary parts independently, realising the complex back
+// transformation in real arithmetic).
+//
+// Q_trd (bulge-chase reflectors).  Q_trd = prod over sweeps s (ascending) of
+// prod over steps k (ascending) of H_{s,k}; applying it means applying the
+// reflectors in reverse generation order.  H_{s,k} acts on rows
+// s+1+k b .. s+k b+b.  Grouping ell consecutive sweeps S = [s0, s0+ell) and
+// one step k into a block (a parallelogram of rows s0+1+k b .. s0+ell-1+k b+b)
+// the order "groups descending; inside a group k ascending; inside a block s
+// descending" equals the reverse generation order up to swaps of reflectors
+// with disjoint rows (for ell <= b, H_{s',k'} and H_{s,k} with s' > s and
+// k' > k never share a row; the same holds for equal s).  Each CTA owns a slab
+// of columns and keeps one block's row window in shared memory while it
+// applies the block's ell reflectors, so Z crosses HBM once per block instead
+// of once per reflector.
+//
+// Q_band (full-to-band panels, compact WY Q_p = I - V_p T_p V_p^T, Eq. 7):
+// for p descending, Z[o:, :] -= V_p (T_p (V_p^T Z[o:, :])) with FP64 GEMMs.
+#include "common.cuh"
+#include "internal.h"
+
+namespace sk {
+namespace {
+
+constexpr int QB = 64;             // band width
+constexpr int QELL = 64;           // sweeps per block
+constexpr int QH = QELL + QB - 1;  // window height
+constexpr int QLD = 132;           // smem leading dimension (= 4 mod 16: conflict-free)
+constexpr int QT = 256;
+
+__host__ __device__ inline int qsteps(int n, int b, int s) { return (s <= n - 3) ? 1 + (n - 3 - s) / b : 0; }
+
+// Thread t: column c = t / 4 of the slab, row phase q = t % 4 (rows 4i + q of
+// the reflector).  The four threads of a column are lanes of one warp, so a
+// reflector needs only warp shuffles and __syncwarp.
+__global__ void __launch_bounds__(QT)
+qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ tautrd, double* __restrict__ Z,
+            int ldz, int ncols, int slab) {
+    extern __shared__ double zw[];  // QLD x 64
+    const int nsw = n - 2;
+    const int c0 = blockIdx.x * slab;
+    const int nc = min(slab, ncols - c0);
+    if (nc <= 0) return;
+    const int t = threadIdx.x;
+    // every lane takes part in the shuffles; lanes past the slab work on
+    // scratch columns of the (always 64-column) window and store nothing
+    const int c = t >> 2, q = t & 3;
+    const int ngroups = (nsw + QELL - 1) / QELL;
+    for (int g = ngroups - 1; g >= 0; g--) {
+        const int s0 = g * QELL, s1 = min(nsw, s0 + QELL);
+        const int kmax = qsteps(n, QB, s0);
+        for (int k = 0; k < kmax; k++) {
+            const int top = s0 + 1 + k * QB;
+            if (top >= n) break;
+            const int H = min(QH, n - top);
+            for (int e = t; e < H * nc; e += QT) {
+                int i = e % H, cc = e / H;
+                zw[cc * QLD + i] = Z[(size_t)(c0 + cc) * ldz + top + i];
+            }
+            __syncthreads();
+            {
+                double* zc = zw + c * QLD;
+                for (int s = s1 - 1; s >= s0; s--) {
+                    if (k >= qsteps(n, QB, s)) continue;
+                    const size_t vi = (size_t)k * nsw + s;
+                    const double tau = tautrd[vi];
+                    if (tau == 0.0) continue;
+                    const double* v = Vtrd + vi * QB;
+                    const int off = s - s0;
+                    const int lim = min(QB, H - off);
+                    double vr[QB / 4];
+                    double a = 0.0;
+#pragma unroll
+                    for (int ii = 0; ii < QB / 4; ii++) {
+                        int i = 4 * ii + q;
+                        vr[ii] = (i < lim) ? __ldg(v + i) : 0.0;
+                        if (i < lim) a = fma(vr[ii], zc[off + i], a);
+                    }
+                    a += __shfl_xor_sync(0xffffffffu, a, 1);
+                    a += __shfl_xor_sync(0xffffffffu, a, 2);
+                    a *= tau;
+#pragma unroll
+                    for (int ii = 0; ii < QB / 4; ii++) {
+                        int i = 4 * ii + q;
+                        if (i < lim) zc[off + i] = fma(-a, vr[ii], zc[off + i]);
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            for (int e = t; e < H * nc; e += QT) {
+                int i = e % H, cc = e / H;
+                Z[(size_t)(c0 + cc) * ldz + top + i] = zw[cc * QLD + i];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+struct QbandWs {
+    double *V, *Y, *Y2;
+};
+
+QbandWs carve_qband(Carve& cv, int n, int b, int k) {
+    QbandWs w{};
+    w.V = cv.take<double>((size_t)n * b);
+    w.Y = cv.take<double>((size_t)b * k);
+    w.Y2 = cv.take<double>((size_t)b * k);
+    return w;
+}
+
+}  // namespace
+
+cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, double* Z, int ldz,
+                       int k) {
+    if (b != QB) return cudaErrorInvalidValue;
+    if (n < 3 || k <= 0) return cudaSuccess;
+    // slab width so that the CTA count fills the GPU in whole waves
+    const int sms = device_sms();
+    int per = 1, slab = 64;
+    while (true) {
+        slab = (k + sms * per - 1) / (sms * per);
+        if (slab <= 64) break;
+        per++;
+    }
+    if (slab < 8) slab = (k < 8) ? k : 8;
+    const int grid = (k + slab - 1) / slab;
+    const size_t smem = sizeof(double) * (size_t)QLD * 64;
+    cudaFuncSetAttribute(qtrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    qtrd_kernel<<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
+    return cudaGetLastError();
+}
+
+size_t qband_ws(int n, int b, int k) {
+    Carve cv(nullptr, ~size_t(0));
+    carve_qband(cv, n, b, k);
+    return cv.off + 256;
+}
+
+int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz,
+                int k, void* ws, size_t ws_bytes) {
+    const int P = num_panels(n, b);
+    if (P == 0 || k <= 0) return 0;
+    Carve cv(ws, ws_bytes);
+    QbandWs w = carve_qband(cv, n, b, k);
+    if (!cv.ok) return SKEW_ERR_WORKSPACE;
+    for (int p = P - 1; p >= 0; p--) {
+        const int o = (p + 1) * b, m = n - o;
+        const double* Tp = Tfac + (size_t)p * b * b;
+        double* Zo = Z + o;
+        if (panel_v(st, n, b, p, W, ldw, w.V, n) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (gemm(st, true, false, b, k, m, 1.0, w.V, n, Zo, ldz, 0.0, w.Y, b) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (gemm(st, false, false, b, k, b, 1.0, Tp, b, w.Y, b, 0.0, w.Y2, b) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (gemm(st, false, false, m, k, b, -1.0, w.V, n, w.Y2, b, 1.0, Zo, ldz) != cudaSuccess) return SKEW_ERR_CUDA;
+    }
+    return 0;
+}
+
+}  // namespace sk

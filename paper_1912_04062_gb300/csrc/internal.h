@@ -1,0 +1,90 @@
+// internal.h -- host-side launchers shared between the translation units of
+// the skew-symmetric eigensolver library.  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/skeweig.h"
+
+namespace sk {
+
+// ---- gemm_f64.cu -----------------------------------------------------------
+// C[M x N] = alpha * op(A) op(B) + beta * C, column-major FP64.
+// op(A) = A (ta = false) or A^T (ta = true); likewise op(B).
+// splitk > 1 splits the K range over CTAs and accumulates with atomics
+// (beta is applied first by a separate scaling launch).
+cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
+                 const double* A, int lda, const double* B, int ldb, double beta,
+                 double* C, int ldc, int splitk = 0);
+
+// P[m x nb] = S V where S = L - L^T is the skew matrix whose strict lower
+// triangle is stored in W (ld ldw); V is m x nb (ld ldv).  Split-K with
+// atomics; P is overwritten.
+cudaError_t skew_symm(cudaStream_t st, int m, int nb, const double* W, int ldw,
+                      const double* V, int ldv, double* P, int ldp, int splitk = 0);
+
+// Lower 64 x 64 tiles (diagonal tiles complete) of C[m x m] +=
+// X[m x k] Y[m x k]^T.  Used for the skew rank-2k update with
+// X = [V W], Y = [W -V].
+cudaError_t gemm_lower_tiles(cudaStream_t st, int m, int k, const double* X, int ldx,
+                             const double* Y, int ldy, double* C, int ldc);
+
+// ---- band_reduce.cu --------------------------------------------------------
+size_t band_reduce_ws(int n, int b);
+int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
+                void* ws, size_t ws_bytes, int* d_status);
+cudaError_t band_pack(cudaStream_t st, int n, int b, const double* W, int ldw,
+                      double* AB, int ldab);
+// Explicit V (m x b, ld ldv) of panel p from the reduced W.
+cudaError_t panel_v(cudaStream_t st, int n, int b, int p, const double* W, int ldw,
+                    double* V, int ldv);
+int num_panels(int n, int b);
+
+// ---- chase.cu ---------------------------------------------------------------
+int chase_steps(int n, int b);
+size_t chase_ws(int n, int b);
+int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha,
+          double* Vtrd, double* tautrd, void* ws, size_t ws_bytes, int* d_status,
+          unsigned spin_cap);
+
+// ---- tridiag.cu -------------------------------------------------------------
+size_t tridiag_ws(int n, int nev);
+// Eigenvalues (descending) and eigenvectors of tridiag(alpha, 0, alpha).
+// Vectors go to Qi in interleaved layout Qi[i * nev + k].
+int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* lambda,
+                double* Qi, void* ws, size_t ws_bytes, int* d_status, int maxit);
+// Interleaved Qi -> column-major X (and Y) with optional D map.
+cudaError_t interleaved_to_colmajor(cudaStream_t st, int n, int nev, const double* Qi,
+                                    double* X, double* Y, int ldz, bool dmap);
+cudaError_t dmap_colmajor(cudaStream_t st, int n, int k, const double* Q, int ldq,
+                          double* X, double* Y, int ldz);
+
+// ---- backtransform.cu -------------------------------------------------------
+cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd,
+                       const double* tautrd, double* Z, int ldz, int k);
+size_t qband_ws(int n, int b, int k);
+int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw,
+                const double* Tfac, double* Z, int ldz, int k, void* ws, size_t ws_bytes);
+
+// ---- misc -------------------------------------------------------------------
+int device_sms();
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Bump allocator over a caller workspace.
+struct Carve {
+    char* base;
+    size_t cap, off = 0;
+    bool ok = true;
+    Carve(void* b, size_t c) : base(static_cast<char*>(b)), cap(c) {}
+    template <typename T>
+    T* take(size_t count) {
+        size_t bytes = align_up(count * sizeof(T));
+        if (off + bytes > cap) { ok = false; return nullptr; }
+        T* p = reinterpret_cast<T*>(base + off);
+        off += bytes;
+        return p;
+    }
+};
+
+}  // namespace sk

@@ -1,0 +1,361 @@
+// skeweig.cu -- C ABI of the skew-symmetric eigensolver: argument checks,
+// workspace carve-up and the stage sequence of Algorithm 1 (two-step form) on
+// one stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sk {
+namespace {
+
+__global__ void copy_lower_kernel(int n, const double* __restrict__ A, int lda, double* __restrict__ W, int ldw,
+                                  int check, int* status) {
+    size_t total = (size_t)n * n;
+    bool bad = false;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % n), j = (int)(e / n);
+        double v = 0.0;
+        if (i > j) {
+            v = A[(size_t)j * lda + i];
+            if (check && !isfinite(v)) bad = true;
+        }
+        W[(size_t)j * ldw + i] = v;
+    }
+    if (bad) sk_set_error(status, SKEW_ERR_NONFINITE);
+}
+
+__global__ void split_z_kernel(int n, int nev, const double* __restrict__ Z, int ldzw, double* __restrict__ Zre,
+                               double* __restrict__ Zim, int ldz) {
+    size_t total = (size_t)n * nev;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % n), j = (int)(e / n);
+        Zre[(size_t)j * ldz + i] = Z[(size_t)j * ldzw + i];
+        Zim[(size_t)j * ldz + i] = Z[(size_t)(j + nev) * ldzw + i];
+    }
+}
+
+__global__ void store_status_kernel(const int* status, int* d_info) {
+    if (threadIdx.x == 0) *d_info = *status;
+}
+
+__global__ void zero_int_kernel(int* p) {
+    if (threadIdx.x == 0) *p = 0;
+}
+
+inline int grid_for(size_t total) {
+    size_t g = (total + 255) / 256;
+    return (int)(g > 16384 ? 16384 : (g == 0 ? 1 : g));
+}
+
+struct Plan {
+    int n, nev, b, P, K, nsw;
+    bool vectors;
+    size_t ldab;
+    // carved pointers
+    double *W, *Tfac, *AB, *Vtrd, *tautrd, *alpha, *Qi, *Z;
+    int* status;
+    void *ws_reduce, *ws_chase, *ws_tri, *ws_qband;
+    size_t sz_reduce, sz_chase, sz_tri, sz_qband;
+};
+
+bool carve_plan(Plan& p, void* base, size_t cap) {
+    Carve cv(base, cap);
+    const size_t n = (size_t)p.n, b = (size_t)p.b;
+    const size_t nn = n ? n : 1;
+    p.status = cv.take<int>(16);
+    p.W = cv.take<double>(nn * nn);
+    p.Tfac = cv.take<double>((size_t)(p.P ? p.P : 1) * b * b);
+    p.ldab = 2 * b + 1;
+    p.AB = cv.take<double>(p.ldab * nn);
+    const size_t nsw = (size_t)(p.nsw > 0 ? p.nsw : 1), K = (size_t)(p.K > 0 ? p.K : 1);
+    p.Vtrd = cv.take<double>(K * nsw * b);
+    p.tautrd = cv.take<double>(K * nsw);
+    p.alpha = cv.take<double>(nn);
+    const size_t ne = (size_t)(p.nev ? p.nev : 1);
+    p.Qi = p.vectors ? cv.take<double>(nn * ne) : nullptr;
+    p.Z = p.vectors ? cv.take<double>(nn * 2 * ne) : nullptr;
+    p.sz_reduce = band_reduce_ws(p.n, p.b);
+    p.ws_reduce = cv.take<char>(p.sz_reduce);
+    p.sz_chase = chase_ws(p.n, p.b);
+    p.ws_chase = cv.take<char>(p.sz_chase);
+    p.sz_tri = tridiag_ws(p.n, p.nev);
+    p.ws_tri = cv.take<char>(p.sz_tri);
+    p.sz_qband = p.vectors ? qband_ws(p.n, p.b, 2 * p.nev) : 0;
+    p.ws_qband = p.vectors ? cv.take<char>(p.sz_qband) : nullptr;
+    return cv.ok;
+}
+
+Plan make_plan(int n, int nev, const skew_opts* o, bool vectors) {
+    Plan p{};
+    p.n = n;
+    p.nev = nev;
+    p.b = (o && o->band > 0) ? o->band : 64;
+    p.P = num_panels(n, p.b);
+    p.K = chase_steps(n, p.b);
+    p.nsw = n - 2;
+    p.vectors = vectors;
+    return p;
+}
+
+size_t plan_bytes(int n, int nev, const skew_opts* o, bool vectors) {
+    Plan p = make_plan(n, nev, o, vectors);
+    Carve cv(nullptr, ~size_t(0));
+    // replicate carve_plan with a null base to size it
+    const size_t nn = n ? (size_t)n : 1, b = (size_t)p.b;
+    cv.take<int>(16);
+    cv.take<double>(nn * nn);
+    cv.take<double>((size_t)(p.P ? p.P : 1) * b * b);
+    cv.take<double>((2 * b + 1) * nn);
+    const size_t nsw = (size_t)(p.nsw > 0 ? p.nsw : 1), K = (size_t)(p.K > 0 ? p.K : 1);
+    cv.take<double>(K * nsw * b);
+    cv.take<double>(K * nsw);
+    cv.take<double>(nn);
+    const size_t ne = (size_t)(nev ? nev : 1);
+    if (vectors) {
+        cv.take<double>(nn * ne);
+        cv.take<double>(nn * 2 * ne);
+    }
+    cv.take<char>(band_reduce_ws(n, p.b));
+    cv.take<char>(chase_ws(n, p.b));
+    cv.take<char>(tridiag_ws(n, nev));
+    if (vectors) cv.take<char>(qband_ws(n, p.b, 2 * nev));
+    return cv.off + 256;
+}
+
+int check_args(int n, const void* A, int lda, int nev, const void* lambda, const void* Zre, const void* Zim) {
+    if (n < 0) return -1;
+    if (n > 0 && !A) return -2;
+    if (lda < (n > 1 ? n : 1)) return -3;
+    if (nev < 0 || nev > n / 2) return -4;
+    if (nev > 0 && !lambda) return -5;
+    if ((Zre == nullptr) != (Zim == nullptr)) return -6;
+    return 0;
+}
+
+int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double* lambda, double* Zre, double* Zim,
+              int ldz, const skew_opts* o, void* ws, size_t ws_bytes, int* d_info) {
+    const bool vectors = (Zre != nullptr);
+    Plan p = make_plan(n, nev, o, vectors);
+    if (p.b != 64) return SKEW_ERR_UNSUPPORTED;
+    if (o && o->mode != SKEW_MODE_FP64) return SKEW_ERR_UNSUPPORTED;
+    if (!carve_plan(p, ws, ws_bytes)) return SKEW_ERR_WORKSPACE;
+    const int maxit = (o && (o->fault & SKEW_FAULT_INVIT_NOCONV)) ? 0 : 5;
+
+    zero_int_kernel<<<1, 32, 0, st>>>(p.status);
+    copy_lower_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(n, A, lda, p.W, n, o ? o->check_finite : 0, p.status);
+    int rc = band_reduce(st, n, p.W, n, p.b, p.Tfac, p.ws_reduce, p.sz_reduce, p.status);
+    if (rc) return rc;
+    if (band_pack(st, n, p.b, p.W, n, p.AB, (int)p.ldab) != cudaSuccess) return SKEW_ERR_CUDA;
+    rc = chase(st, n, p.b, p.AB, (int)p.ldab, p.alpha, p.Vtrd, p.tautrd, p.ws_chase, p.sz_chase, p.status, 0);
+    if (rc) return rc;
+    rc = tridiag_eig(st, n, p.alpha, nev, lambda, vectors ? p.Qi : nullptr, p.ws_tri, p.sz_tri, p.status, maxit);
+    if (rc) return rc;
+    if (vectors) {
+        // Algorithm 1 step 3 (D map) fused with the interleaved -> column-major
+        // move; Z = [X | Y] is n x 2 nev with leading dimension n.
+        if (interleaved_to_colmajor(st, n, nev, p.Qi, p.Z, p.Z + (size_t)n * nev, n, true) != cudaSuccess)
+            return SKEW_ERR_CUDA;
+        if (apply_qtrd(st, n, p.b, p.Vtrd, p.tautrd, p.Z, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
+        rc = apply_qband(st, n, p.b, p.W, n, p.Tfac, p.Z, n, 2 * nev, p.ws_qband, p.sz_qband);
+        if (rc) return rc;
+        split_z_kernel<<<grid_for((size_t)n * nev), 256, 0, st>>>(n, nev, p.Z, n, Zre, Zim, ldz);
+    }
+    if (d_info) store_status_kernel<<<1, 32, 0, st>>>(p.status, d_info);
+    return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace sk
+
+using namespace sk;
+
+extern "C" {
+
+void skew_opts_default(skew_opts* opts) {
+    if (!opts) return;
+    std::memset(opts, 0, sizeof(*opts));
+    opts->mode = SKEW_MODE_FP64;
+    opts->band = 64;
+}
+
+const char* skew_eig_strerror(int code) {
+    if (code == 0) return "success";
+    if (code < 0 && code > -100) return "invalid argument (-k: argument k)";
+    if (code >= SKEW_INFO_INVIT_BASE && code < SKEW_ERR_CUDA) return "inverse iteration did not converge (1000 + j)";
+    switch (code) {
+    case SKEW_ERR_CUDA: return "CUDA runtime call failed";
+    case SKEW_ERR_NOMEM: return "device allocation failed";
+    case SKEW_ERR_DEVICE_TIMEOUT: return "device-side wait exceeded its cap";
+    case SKEW_ERR_UNSUPPORTED: return "mode or size not supported on this GPU";
+    case SKEW_ERR_NONFINITE: return "input holds NaN or Inf";
+    case SKEW_ERR_WORKSPACE: return "workspace too small";
+    case SKEW_ERR_LAUNCH: return "cooperative launch does not fit on this GPU";
+    default: return "unknown status code";
+    }
+}
+
+size_t skew_eig_workspace_size(int n, int nev, const skew_opts* opts) {
+    if (n < 0 || nev < 0) return 0;
+    return plan_bytes(n, nev, opts, true);
+}
+
+int skew_eig_ex(int n, const double* A, int lda, int nev, double* lambda, double* Z_re, double* Z_im, int ldz,
+                const skew_opts* opts, void* workspace, size_t ws_bytes, int* d_info, void* stream) {
+    int rc = check_args(n, A, lda, nev, lambda, Z_re, Z_im);
+    if (rc) return rc;
+    if (Z_re && ldz < (n > 1 ? n : 1)) return -8;
+    if (!workspace && n > 0) return -10;
+    if (opts && opts->mode == SKEW_MODE_MIXED_INT8) return SKEW_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0 || nev == 0) {
+        if (d_info) {
+            zero_int_kernel<<<1, 32, 0, st>>>(d_info);
+            if (cudaGetLastError() != cudaSuccess) return SKEW_ERR_CUDA;
+        }
+        return 0;
+    }
+    return run_solve(st, n, A, lda, nev, lambda, Z_re, Z_im, ldz, opts, workspace, ws_bytes, d_info);
+}
+
+int skew_eig(int n, const double* A, int lda, int nev, double* lambda, double* Z_re, double* Z_im, void* stream) {
+    int rc = check_args(n, A, lda, nev, lambda, Z_re, Z_im);
+    if (rc) return rc;
+    if (n == 0 || nev == 0) return 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool vectors = Z_re != nullptr;
+    size_t bytes = plan_bytes(n, nev, nullptr, vectors);
+    void* ws = nullptr;
+    if (cudaMallocAsync(&ws, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return SKEW_ERR_NOMEM;
+    }
+    // the last 256 bytes of the allocation (slack of plan_bytes) hold d_info
+    int* d_info = reinterpret_cast<int*>(static_cast<char*>(ws) + bytes - 256);
+    rc = run_solve(st, n, A, lda, nev, lambda, Z_re, Z_im, n, nullptr, ws, bytes - 256, d_info);
+    int info = 0;
+    if (rc == 0) {
+        if (cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+    }
+    cudaFreeAsync(ws, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SKEW_ERR_CUDA;
+    return rc ? rc : info;
+}
+
+int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda, double* Z_re, double* Z_im,
+                  void* stream) {
+    int rc = check_args(n, A, lda, nev, lambda, Z_re, Z_im);
+    if (rc) return rc;
+    if (n == 0 || nev == 0) return 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool vectors = Z_re != nullptr;
+    const size_t nn = (size_t)n;
+    size_t bytes = plan_bytes(n, nev, nullptr, vectors);
+    size_t io = align_up(sizeof(double) * nn * n) + align_up(sizeof(double) * nev) +
+                (vectors ? 2 * align_up(sizeof(double) * nn * nev) : 0) + 256;
+    char* base = nullptr;
+    if (cudaMallocAsync((void**)&base, bytes + io, st) != cudaSuccess) {
+        cudaGetLastError();
+        return SKEW_ERR_NOMEM;
+    }
+    double* dA = reinterpret_cast<double*>(base + bytes);
+    double* dl = reinterpret_cast<double*>(base + bytes + align_up(sizeof(double) * nn * n));
+    double* dzr = vectors ? reinterpret_cast<double*>(reinterpret_cast<char*>(dl) + align_up(sizeof(double) * nev)) : nullptr;
+    double* dzi = vectors ? reinterpret_cast<double*>(reinterpret_cast<char*>(dzr) + align_up(sizeof(double) * nn * nev)) : nullptr;
+    int* d_info = reinterpret_cast<int*>(base + bytes - 256);
+    int info = 0;
+    rc = 0;
+    if (cudaMemcpy2DAsync(dA, sizeof(double) * nn, A, sizeof(double) * (size_t)lda, sizeof(double) * nn, nn,
+                          cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = SKEW_ERR_CUDA;
+    if (!rc) rc = run_solve(st, n, dA, n, nev, dl, dzr, dzi, n, nullptr, base, bytes - 256, d_info);
+    if (!rc) {
+        if (cudaMemcpyAsync(lambda, dl, sizeof(double) * nev, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+        if (vectors) {
+            if (cudaMemcpyAsync(Z_re, dzr, sizeof(double) * nn * nev, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+            if (cudaMemcpyAsync(Z_im, dzi, sizeof(double) * nn * nev, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+        }
+        if (cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+    }
+    cudaFreeAsync(base, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SKEW_ERR_CUDA;
+    return rc ? rc : info;
+}
+
+// ---------------------------------------------------------------- stages
+size_t skew_band_reduce_ws(int n, int b) { return band_reduce_ws(n, b); }
+
+int skew_band_reduce(int n, double* W, int ldw, int b, double* Tfac, void* ws, size_t ws_bytes, int* d_status,
+                     void* stream) {
+    if (n < 0) return -1;
+    if (ldw < (n > 1 ? n : 1)) return -3;
+    if (b <= 0 || b % 64) return -4;
+    return band_reduce(static_cast<cudaStream_t>(stream), n, W, ldw, b, Tfac, ws, ws_bytes, d_status);
+}
+
+int skew_band_pack(int n, int b, const double* W, int ldw, double* AB, int ldab, void* stream) {
+    if (n < 0) return -1;
+    if (b <= 0) return -2;
+    if (ldab < 2 * b + 1) return -6;
+    return band_pack(static_cast<cudaStream_t>(stream), n, b, W, ldw, AB, ldab) == cudaSuccess ? 0 : SKEW_ERR_CUDA;
+}
+
+int skew_chase_steps(int n, int b) { return chase_steps(n, b); }
+size_t skew_chase_ws(int n, int b) { return chase_ws(n, b); }
+
+int skew_band_to_tridiag(int n, int b, double* AB, int ldab, double* alpha, double* Vtrd, double* tautrd, void* ws,
+                         size_t ws_bytes, int* d_status, void* stream) {
+    if (n < 0) return -1;
+    if (b != 64) return -2;
+    if (ldab < 2 * b + 1) return -4;
+    return chase(static_cast<cudaStream_t>(stream), n, b, AB, ldab, alpha, Vtrd, tautrd, ws, ws_bytes, d_status, 0);
+}
+
+size_t skew_tridiag_ws(int n, int nev) {
+    return tridiag_ws(n, nev) + align_up(sizeof(double) * (size_t)(n > 0 ? n : 1) * (nev > 0 ? nev : 1)) + 256;
+}
+
+int skew_tridiag_eig(int n, const double* alpha, int nev, double* lambda, double* Q, int ldq, void* ws,
+                     size_t ws_bytes, int* d_status, void* stream) {
+    if (n < 1) return -1;
+    if (nev < 1 || nev > n) return -3;
+    if (Q && ldq < n) return -6;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Carve cv(ws, ws_bytes);
+    double* Qi = Q ? cv.take<double>((size_t)n * nev) : nullptr;
+    size_t rest = tridiag_ws(n, nev);
+    void* tws = cv.take<char>(rest);
+    if (!cv.ok) return SKEW_ERR_WORKSPACE;
+    int rc = tridiag_eig(st, n, alpha, nev, lambda, Qi, tws, rest, d_status, 5);
+    if (rc) return rc;
+    if (Q && interleaved_to_colmajor(st, n, nev, Qi, Q, nullptr, ldq, false) != cudaSuccess) return SKEW_ERR_CUDA;
+    return 0;
+}
+
+int skew_dmap(int n, int k, const double* Q, int ldq, double* X, double* Y, int ldz, void* stream) {
+    if (n < 0) return -1;
+    if (k < 0) return -2;
+    return dmap_colmajor(static_cast<cudaStream_t>(stream), n, k, Q, ldq, X, Y, ldz) == cudaSuccess ? 0 : SKEW_ERR_CUDA;
+}
+
+int skew_apply_qtrd(int n, int b, const double* Vtrd, const double* tautrd, double* Z, int ldz, int k, void* stream) {
+    if (n < 0) return -1;
+    if (b != 64) return -2;
+    return apply_qtrd(static_cast<cudaStream_t>(stream), n, b, Vtrd, tautrd, Z, ldz, k) == cudaSuccess ? 0
+                                                                                                      : SKEW_ERR_CUDA;
+}
+
+size_t skew_qband_ws(int n, int b, int k) { return qband_ws(n, b, k); }
+
+int skew_apply_qband(int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz, int k, void* ws,
+                     size_t ws_bytes, void* stream) {
+    if (n < 0) return -1;
+    if (b <= 0 || b % 64) return -2;
+    return apply_qband(static_cast<cudaStream_t>(stream), n, b, W, ldw, Tfac, Z, ldz, k, ws, ws_bytes);
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports every entry point include/skeweig.h
+declares; host-side argument checks work without a GPU (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "skeweig.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(skew_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def sk():
+    from paper_1912_04062_gb300 import build
+    build.build()
+    import paper_1912_04062_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def test_every_declared_symbol_is_exported(sk):
+    names = _declared()
+    assert len(names) >= 15
+    L = ctypes.CDLL(sk.LIB_PATH)
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(sk.SIGNATURES), set(names) ^ set(sk.SIGNATURES)
+
+
+def test_strerror_and_defaults(sk):
+    L = sk.lib()
+    for code in [0, -3, 1005, 2001, 2002, 2003, 2004, 2005, 2006, 2007, 9999]:
+        assert L.skew_eig_strerror(code)
+    o = sk.skew_opts()
+    L.skew_opts_default(ctypes.byref(o))
+    assert o.mode == 0 and o.band == 64
+
+
+def test_argument_checks_are_host_side(sk):
+    L = sk.lib()
+    nul = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+    assert L.skew_eig(-1, fake, 1, 0, fake, nul, nul, nul) == -1
+    assert L.skew_eig(4, nul, 4, 1, fake, nul, nul, nul) == -2
+    assert L.skew_eig(4, fake, 3, 1, fake, nul, nul, nul) == -3
+    assert L.skew_eig(4, fake, 4, 3, fake, nul, nul, nul) == -4
+    assert L.skew_eig(5, fake, 5, 3, fake, nul, nul, nul) == -4
+    assert L.skew_eig(4, fake, 4, 1, nul, nul, nul, nul) == -5
+    assert L.skew_eig(4, fake, 4, 1, fake, fake, nul, nul) == -6
+    # no-op cases
+    assert L.skew_eig(0, nul, 1, 0, nul, nul, nul, nul) == 0
+    assert L.skew_eig(1, fake, 1, 0, nul, nul, nul, nul) == 0
+    assert L.skew_eig(9, fake, 9, 0, nul, nul, nul, nul) == 0
+    # INT8 Ozaki mode is rejected before any device work
+    o = sk.skew_opts()
+    L.skew_opts_default(ctypes.byref(o))
+    o.mode = sk.SKEW_MODE_MIXED_INT8
+    assert L.skew_eig_ex(8, fake, 8, 2, fake, fake, fake, 8, ctypes.byref(o), fake, 1 << 20, fake, nul) == \
+        sk.SKEW_ERR_UNSUPPORTED
+
+
+def test_workspace_size_grows(sk):
+    sizes = [sk.workspace_size(n, n // 2) for n in (64, 512, 4096)]
+    assert sizes[0] < sizes[1] < sizes[2]
+    # dominant terms: W (n^2), chase reflectors (~n^2), interleaved LU (4 n nev)
+    n = 4096
+    assert sizes[2] >= 8 * (2 * n * n)
