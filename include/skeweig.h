@@ -113,6 +113,42 @@ int skew_eig_ex(int n, const double* A, int lda, int nev, double* lambda,
 int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda,
                   double* Z_re, double* Z_im, void* stream);
 
+/* Stages timed by skew_eig_profile (Algorithm 1, two-step form):
+ * 0 ingest (copy of the strict lower triangle), 1 full-to-band reduction,
+ * 2 band pack, 3 bulge chase, 4 tridiagonal solve (bisection + inverse
+ * iteration), 5 D map, 6 Q_trd back-transform, 7 Q_band back-transform,
+ * 8 output copy. */
+#define SKEW_NSTAGES 9
+
+/*
+ * skew_eig_ex plus CUDA events between the stages above, recorded on
+ * `stream`; synchronises `stream`, writes the stage durations in milliseconds
+ * to the HOST array stage_ms[SKEW_NSTAGES] and returns the numerical status
+ * (0, 1000 + j or SKEW_ERR_*).  Arguments as skew_eig_ex; 12 stage_ms.
+ */
+int skew_eig_profile(int n, const double* A, int lda, int nev, double* lambda,
+                     double* Z_re, double* Z_im, int ldz, const skew_opts* opts,
+                     void* workspace, size_t ws_bytes, float* stage_ms, void* stream);
+
+/*
+ * Accuracy of a computed decomposition (Algorithm 1 "Ensure"), on the device,
+ * restricted to the columns cols[0..ncols-1] of Z (cols == NULL: all nev
+ * columns, ncols == nev; cols is a DEVICE int array):
+ *   out3[0] = ||A Z_S - Z_S diag(i lambda_S)||_F
+ *   out3[1] = ||Z_S^H Z - I_S||_F   (I_S: the columns S of the identity)
+ *   out3[2] = ||A||_F
+ * out3 is a HOST array; the call synchronises `stream`.  Workspace of at
+ * least skew_metrics_ws(n, nev, ncols) bytes.
+ */
+size_t skew_metrics_ws(int n, int nev, int ncols);
+int skew_eig_metrics(int n, const double* A, int lda, int nev, const double* lambda,
+                     const double* Z_re, const double* Z_im, int ldz, const int* cols,
+                     int ncols, double* out3, void* ws, size_t ws_bytes, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process
+ * (diagnostics; counts host-side launch calls). */
+long long skew_launch_count(void);
+
 /* ------------------------------------------------------------------------
  * Stage entry points (the steps of Algorithm 1 one at a time; used by the
  * per-stage parity tests).  Each takes a caller workspace of at least the

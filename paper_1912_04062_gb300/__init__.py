@@ -44,6 +44,10 @@ SIGNATURES = {
     "skew_eig_workspace_size": (_sz, [_i, _i, _p]),
     "skew_eig_ex": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
     "skew_eig_host": (_i, [_i, _p, _i, _i, _p, _p, _p, _p]),
+    "skew_eig_profile": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
+    "skew_metrics_ws": (_sz, [_i, _i, _i]),
+    "skew_eig_metrics": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _i, _p, _p, _sz, _p]),
+    "skew_launch_count": (ctypes.c_longlong, []),
     "skew_band_reduce_ws": (_sz, [_i, _i]),
     "skew_band_reduce": (_i, [_i, _p, _i, _i, _p, _p, _sz, _p, _p]),
     "skew_band_pack": (_i, [_i, _i, _p, _i, _p, _i, _p]),
@@ -174,6 +178,46 @@ def skew_eig_ex(A, nev: int, lam, Zr, Zi, workspace, d_info, opts: Options | Non
     return lib().skew_eig_ex(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), ldz, ctypes.byref(o),
                              _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(d_info),
                              _stream(stream))
+
+
+STAGES = ["ingest", "band_reduce", "band_pack", "chase", "tridiag", "dmap", "qtrd", "qband", "output"]
+
+
+def skew_eig_profile(A, nev: int, lam, Zr, Zi, workspace, opts: Options | None = None, stream=None):
+    """Synchronous solve into caller buffers with per-stage CUDA-event times.
+    Returns (status, {stage: ms})."""
+    A = _as_device_f64(A)
+    n = A.shape[0]
+    o = (opts or Options()).c()
+    ldz = _ld(Zr) if Zr is not None else max(1, n)
+    ms = (ctypes.c_float * len(STAGES))()
+    code = lib().skew_eig_profile(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), ldz, ctypes.byref(o),
+                                  _ptr(workspace), workspace.numel() * workspace.element_size(), ms,
+                                  _stream(stream))
+    return code, dict(zip(STAGES, [float(x) for x in ms]))
+
+
+def metrics(A, lam, Zr, Zi, cols=None, stream=None):
+    """(residual, orthogonality, ||A||_F) over the columns `cols` (all if None)."""
+    torch = _torch()
+    A = _as_device_f64(A)
+    n = A.shape[0]
+    nev = Zr.shape[1]
+    dcols = None
+    ncols = nev
+    if cols is not None:
+        dcols = torch.as_tensor(cols, dtype=torch.int32, device=A.device)
+        ncols = dcols.numel()
+    ws = _ws(lib().skew_metrics_ws(n, nev, ncols), A.device)
+    out = (ctypes.c_double * 3)()
+    code = lib().skew_eig_metrics(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), _ld(Zr), _ptr(dcols),
+                                  ncols, out, _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "skew_eig_metrics")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def launch_count() -> int:
+    return int(lib().skew_launch_count())
 
 
 def skew_eig_host(A, nev: int, vectors: bool = True, stream=None):

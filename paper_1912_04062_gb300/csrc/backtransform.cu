@@ -130,6 +130,7 @@ cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd, const 
     const size_t smem = sizeof(double) * (size_t)QLD * 64;
     cudaFuncSetAttribute(qtrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     qtrd_kernel<<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
+    count_launch();
     return cudaGetLastError();
 }
 

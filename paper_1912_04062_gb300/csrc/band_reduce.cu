@@ -248,6 +248,7 @@ cudaError_t panel_v(cudaStream_t st, int n, int b, int p, const double* W, int l
     const int o = (p + 1) * b, m = n - o;
     if (m <= 0) return cudaSuccess;
     panel_v_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, W + (size_t)p * b * ldw + o, ldw, V, ldv);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -286,10 +287,13 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         if (cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st) !=
             cudaSuccess)
             return SKEW_ERR_LAUNCH;
+        count_launch();
         // ---- T factor (Eq. 7)
         panel_v_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, panel, ldw, w.V, n);
+        count_launch();
         if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.V, n, 0.0, w.G, b) != cudaSuccess) return SKEW_ERR_CUDA;
         tfactor_kernel<<<1, 128, sizeof(double) * (b * b + b), st>>>(b, taup, w.G, Tp);
+        count_launch();
         // ---- a3: P = A22 V (skew, lower triangle only)
         if (skew_symm(st, m, b, A22, ldw, w.V, n, w.Pm, n) != cudaSuccess) return SKEW_ERR_CUDA;
         // ---- a4: Y = P T; C = T^T (V^T Y); W = Y - V C / 2
@@ -299,6 +303,7 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         if (gemm(st, false, false, m, b, b, -0.5, w.V, n, w.C2, b, 1.0, w.Y, n) != cudaSuccess) return SKEW_ERR_CUDA;
         // ---- a5: A22 += [V W][W -V]^T (lower tiles)
         concat_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, w.V, w.Y, n, w.X2, w.Y2);
+        count_launch();
         if (gemm_lower_tiles(st, m, 2 * b, w.X2, n, w.Y2, n, A22, ldw) != cudaSuccess) return SKEW_ERR_CUDA;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
@@ -307,6 +312,7 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
 cudaError_t band_pack(cudaStream_t st, int n, int b, const double* W, int ldw, double* AB, int ldab) {
     if (n <= 0) return cudaSuccess;
     band_pack_kernel<<<grid_for((size_t)n * (2 * b + 1)), 256, 0, st>>>(n, b, W, ldw, AB, ldab, num_panels(n, b));
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -232,8 +232,10 @@ int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha, do
         void* args[] = {&n, &AB, &ldab, &alpha, &Vtrd, &tautrd, &prog, &d_status};
         if (cudaLaunchCooperativeKernel((void*)chase_kernel, dim3(G), dim3(CH_THREADS), args, smem, st) != cudaSuccess)
             return SKEW_ERR_LAUNCH;
+        count_launch();
     }
     chase_tail_kernel<<<1, 32, 0, st>>>(n, AB, ldab, alpha);
+    count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
 }
 

@@ -235,6 +235,7 @@ cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double 
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K <= 0) {
         scale_kernel<<<min(1024, (M * N + 255) / 256 + 1), 256, 0, st>>>(M, N, beta, C, ldc);
+        count_launch();
         return cudaGetLastError();
     }
     const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
@@ -243,6 +244,7 @@ cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double 
     s = (K + kchunk - 1) / kchunk;
     if (s > 1) {
         scale_kernel<<<min(4096, (M * N + 255) / 256 + 1), 256, 0, st>>>(M, N, beta, C, ldc);
+        count_launch();
     }
     dim3 grid(tm, tn, s);
     if (!ta && !tb)
@@ -253,6 +255,7 @@ cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double 
         gemm_kernel<A_PLAIN_T, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk);
     else
         gemm_kernel<A_PLAIN_T, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -264,10 +267,12 @@ cudaError_t skew_symm(cudaStream_t st, int m, int nb, const double* W, int ldw, 
     int kchunk = ((m + s - 1) / s + BK - 1) / BK * BK;
     s = (m + kchunk - 1) / kchunk;
     scale_kernel<<<min(4096, (m * nb + 255) / 256 + 1), 256, 0, st>>>(m, nb, 0.0, P, ldp);
+    count_launch();
     dim3 grid(tm, tn, s);
     // force the atomic path even when s == 1 (P was zeroed above)
     if (s == 1) grid.z = 1;
     gemm_kernel<A_SKEW, false><<<grid, NT, 0, st>>>(m, nb, m, 1.0, W, ldw, V, ldv, 0.0, P, ldp, kchunk);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -277,6 +282,7 @@ cudaError_t gemm_lower_tiles(cudaStream_t st, int m, int k, const double* X, int
     const long long T = (m + BM - 1) / BM;
     const long long nt = T * (T + 1) / 2;
     lower_tiles_kernel<<<(unsigned)nt, NT, 0, st>>>(m, k, X, ldx, Y, ldy, C, ldc);
+    count_launch();
     return cudaGetLastError();
 }
 

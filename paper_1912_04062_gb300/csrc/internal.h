@@ -67,7 +67,15 @@ size_t qband_ws(int n, int b, int k);
 int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw,
                 const double* Tfac, double* Z, int ldz, int k, void* ws, size_t ws_bytes);
 
+// ---- metrics.cu -------------------------------------------------------------
+size_t metrics_ws(int n, int nev, int s);
+int metrics(cudaStream_t st, int n, const double* A, int lda, int nev, const double* lambda, const double* X,
+            const double* Y, int ldz, const int* cols, int s, double* out3, void* ws, size_t ws_bytes);
+
 // ---- misc -------------------------------------------------------------------
+// Host-side count of kernel launches issued by this library (diagnostics).
+void count_launch(int k = 1);
+long long launch_count();
 int device_sms();
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 

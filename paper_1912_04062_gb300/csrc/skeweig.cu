@@ -1,6 +1,7 @@
 // skeweig.cu -- C ABI of the skew-symmetric eigensolver: argument checks,
 // workspace carve-up and the stage sequence of Algorithm 1 (two-step form) on
 // one stream.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -137,8 +138,16 @@ int check_args(int n, const void* A, int lda, int nev, const void* lambda, const
     return 0;
 }
 
+// Optional per-stage CUDA events recorded on the solve stream.
+struct StageEvents {
+    cudaEvent_t ev[SKEW_NSTAGES + 1];
+};
+
 int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double* lambda, double* Zre, double* Zim,
-              int ldz, const skew_opts* o, void* ws, size_t ws_bytes, int* d_info) {
+              int ldz, const skew_opts* o, void* ws, size_t ws_bytes, int* d_info, StageEvents* prof = nullptr) {
+    auto mark = [&](int i) {
+        if (prof) cudaEventRecord(prof->ev[i], st);
+    };
     const bool vectors = (Zre != nullptr);
     Plan p = make_plan(n, nev, o, vectors);
     if (p.b != 64) return SKEW_ERR_UNSUPPORTED;
@@ -146,30 +155,56 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     if (!carve_plan(p, ws, ws_bytes)) return SKEW_ERR_WORKSPACE;
     const int maxit = (o && (o->fault & SKEW_FAULT_INVIT_NOCONV)) ? 0 : 5;
 
+    mark(0);
     zero_int_kernel<<<1, 32, 0, st>>>(p.status);
+    count_launch();
     copy_lower_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(n, A, lda, p.W, n, o ? o->check_finite : 0, p.status);
+    count_launch();
+    mark(1);
     int rc = band_reduce(st, n, p.W, n, p.b, p.Tfac, p.ws_reduce, p.sz_reduce, p.status);
     if (rc) return rc;
+    mark(2);
     if (band_pack(st, n, p.b, p.W, n, p.AB, (int)p.ldab) != cudaSuccess) return SKEW_ERR_CUDA;
+    mark(3);
     rc = chase(st, n, p.b, p.AB, (int)p.ldab, p.alpha, p.Vtrd, p.tautrd, p.ws_chase, p.sz_chase, p.status, 0);
     if (rc) return rc;
+    mark(4);
     rc = tridiag_eig(st, n, p.alpha, nev, lambda, vectors ? p.Qi : nullptr, p.ws_tri, p.sz_tri, p.status, maxit);
     if (rc) return rc;
+    mark(5);
     if (vectors) {
         // Algorithm 1 step 3 (D map) fused with the interleaved -> column-major
         // move; Z = [X | Y] is n x 2 nev with leading dimension n.
         if (interleaved_to_colmajor(st, n, nev, p.Qi, p.Z, p.Z + (size_t)n * nev, n, true) != cudaSuccess)
             return SKEW_ERR_CUDA;
-        if (apply_qtrd(st, n, p.b, p.Vtrd, p.tautrd, p.Z, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
+    }
+    mark(6);
+    if (vectors && apply_qtrd(st, n, p.b, p.Vtrd, p.tautrd, p.Z, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
+    mark(7);
+    if (vectors) {
         rc = apply_qband(st, n, p.b, p.W, n, p.Tfac, p.Z, n, 2 * nev, p.ws_qband, p.sz_qband);
         if (rc) return rc;
-        split_z_kernel<<<grid_for((size_t)n * nev), 256, 0, st>>>(n, nev, p.Z, n, Zre, Zim, ldz);
     }
-    if (d_info) store_status_kernel<<<1, 32, 0, st>>>(p.status, d_info);
+    mark(8);
+    if (vectors) {
+        split_z_kernel<<<grid_for((size_t)n * nev), 256, 0, st>>>(n, nev, p.Z, n, Zre, Zim, ldz);
+        count_launch();
+    }
+    if (d_info) {
+        store_status_kernel<<<1, 32, 0, st>>>(p.status, d_info);
+        count_launch();
+    }
+    mark(9);
     return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
 }
 
+std::atomic<long long> g_launches{0};
+
 }  // namespace
+
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 }  // namespace sk
 
 using namespace sk;
@@ -215,6 +250,7 @@ int skew_eig_ex(int n, const double* A, int lda, int nev, double* lambda, double
     if (n == 0 || nev == 0) {
         if (d_info) {
             zero_int_kernel<<<1, 32, 0, st>>>(d_info);
+            count_launch();
             if (cudaGetLastError() != cudaSuccess) return SKEW_ERR_CUDA;
         }
         return 0;
@@ -285,6 +321,54 @@ int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda, doub
     if (cudaStreamSynchronize(st) != cudaSuccess) return SKEW_ERR_CUDA;
     return rc ? rc : info;
 }
+
+int skew_eig_profile(int n, const double* A, int lda, int nev, double* lambda, double* Z_re, double* Z_im, int ldz,
+                     const skew_opts* opts, void* workspace, size_t ws_bytes, float* stage_ms, void* stream) {
+    int rc = check_args(n, A, lda, nev, lambda, Z_re, Z_im);
+    if (rc) return rc;
+    if (Z_re && ldz < (n > 1 ? n : 1)) return -8;
+    if (!workspace && n > 0) return -10;
+    if (!stage_ms) return -12;
+    if (opts && opts->mode == SKEW_MODE_MIXED_INT8) return SKEW_ERR_UNSUPPORTED;
+    for (int i = 0; i < SKEW_NSTAGES; i++) stage_ms[i] = 0.0f;
+    if (n == 0 || nev == 0) return 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    StageEvents ev;
+    for (int i = 0; i <= SKEW_NSTAGES; i++)
+        if (cudaEventCreate(&ev.ev[i]) != cudaSuccess) return SKEW_ERR_CUDA;
+    int* d_info = nullptr;
+    // status word: the caller workspace's carve starts with it (see carve_plan)
+    rc = run_solve(st, n, A, lda, nev, lambda, Z_re, Z_im, ldz, opts, workspace, ws_bytes, nullptr, &ev);
+    int info = 0;
+    if (rc == 0) {
+        d_info = static_cast<int*>(workspace);
+        if (cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+    if (rc == 0)
+        for (int i = 0; i < SKEW_NSTAGES; i++) cudaEventElapsedTime(&stage_ms[i], ev.ev[i], ev.ev[i + 1]);
+    for (int i = 0; i <= SKEW_NSTAGES; i++) cudaEventDestroy(ev.ev[i]);
+    return rc ? rc : info;
+}
+
+size_t skew_metrics_ws(int n, int nev, int ncols) { return metrics_ws(n, nev, ncols > 0 ? ncols : 1); }
+
+int skew_eig_metrics(int n, const double* A, int lda, int nev, const double* lambda, const double* Z_re,
+                     const double* Z_im, int ldz, const int* cols, int ncols, double* out3, void* ws, size_t ws_bytes,
+                     void* stream) {
+    if (n < 1) return -1;
+    if (!A) return -2;
+    if (lda < n) return -3;
+    if (nev < 1 || nev > n) return -4;
+    if (!lambda || !Z_re || !Z_im) return -5;
+    if (ldz < n) return -8;
+    if (ncols < 1 || (!cols && ncols != nev) || ncols > nev) return -10;
+    if (!out3) return -11;
+    return metrics(static_cast<cudaStream_t>(stream), n, A, lda, nev, lambda, Z_re, Z_im, ldz, cols, ncols, out3, ws,
+                   ws_bytes);
+}
+
+long long skew_launch_count(void) { return launch_count(); }
 
 // ---------------------------------------------------------------- stages
 size_t skew_band_reduce_ws(int n, int b) { return band_reduce_ws(n, b); }

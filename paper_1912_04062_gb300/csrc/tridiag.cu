@@ -299,15 +299,20 @@ int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* la
     TriWs w = carve_tri(cv, n, nev);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
     tri_prep_kernel<<<1, 1024, 0, st>>>(n, alpha, w.a2, w.sc);
+    count_launch();
     bisect_kernel<<<(nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2, w.sc, lambda);
+    count_launch();
     if (Qi) {
         // cluster tolerance relative to ||S||_1: 1e-3 for small n (the usual
         // inverse-iteration choice), shrinking like n^-1.5 so that clusters stay
         // small for dense spectra while eps*||S||/gap stays below n*eps.
         double ctol = fmin(1e-3, 10.0 / ((double)n * sqrt((double)n)));
         set_int_kernel<<<1, 32, 0, st>>>(w.fail, 0x7fffffff);
+        count_launch();
         invit_kernel<<<(nev + 63) / 64, 64, 0, st>>>(n, nev, alpha, lambda, w.sc, ctol, maxit, w.bf, Qi, w.fail);
+        count_launch();
         invit_status_kernel<<<1, 32, 0, st>>>(w.fail, nev, d_status);
+        count_launch();
     }
     return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
 }
@@ -317,6 +322,7 @@ cudaError_t interleaved_to_colmajor(cudaStream_t st, int n, int nev, const doubl
     if (n <= 0 || nev <= 0) return cudaSuccess;
     dim3 grid((n + 31) / 32, (nev + 31) / 32), block(32, 8);
     transpose_dmap_kernel<<<grid, block, 0, st>>>(n, nev, Qi, X, Y, ldz, dmap ? 1 : 0);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -325,6 +331,7 @@ cudaError_t dmap_colmajor(cudaStream_t st, int n, int k, const double* Q, int ld
     size_t total = (size_t)n * k;
     int grid = (int)((total + 255) / 256 > 8192 ? 8192 : (total + 255) / 256);
     dmap_colmajor_kernel<<<grid, 256, 0, st>>>(n, k, Q, ldq, X, Y, ldz);
+    count_launch();
     return cudaGetLastError();
 }
 

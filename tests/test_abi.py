@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "skeweig.h")
 def _declared():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(skew_\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?(?:long\s+long|\w+)\s*\*?\s*(skew_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 

@@ -265,3 +265,29 @@ def test_failure_paths_report_status():
     lam2, X2, Y2 = gpu_solve(A, nev)
     m = oracle.scaled_metrics(A, lam2, X2, Y2)
     assert m["resid"] <= 50 and m["orth"] <= 50
+
+
+def test_device_metrics_match_definitions():
+    # a15: the library's residual / orthogonality kernels against the numpy
+    # definitions, on all columns and on a column sample
+    import paper_1912_04062_gb300 as sk
+    torch = _torch()
+    A = inputs.bse(300, seed=12)
+    n, nev = 300, 150
+    dA = to_dev(A)
+    lam, Zr, Zi = sk.skew_eig(dA, nev)
+    torch.cuda.synchronize()
+    L, X, Y = lam.cpu().numpy(), Zr.cpu().numpy(), Zi.cpu().numpy()
+    Xp = X.copy()
+    Xp[:, 3] += 1e-9   # make both metrics visibly nonzero
+    Zr.copy_(torch.from_numpy(Xp))
+    r, o, f = sk.metrics(dA, lam, Zr, Zi)
+    assert r == pytest.approx(oracle.residual(A, L, Xp, Y), rel=1e-6)
+    assert o == pytest.approx(oracle.orthogonality(Xp, Y), rel=1e-6)
+    assert f == pytest.approx(np.linalg.norm(A), rel=1e-12)
+    cols = [0, 3, 17, 149]
+    r2, o2, _ = sk.metrics(dA, lam, Zr, Zi, cols=cols)
+    assert r2 == pytest.approx(oracle.residual(A, L[cols], Xp[:, cols], Y[:, cols]), rel=1e-6)
+    G = (Xp[:, cols].T @ Xp + Y[:, cols].T @ Y) - np.eye(nev)[cols]
+    H = Xp[:, cols].T @ Y - Y[:, cols].T @ Xp
+    assert o2 == pytest.approx(np.sqrt(np.sum(G * G) + np.sum(H * H)), rel=1e-6)
