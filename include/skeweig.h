@@ -198,6 +198,26 @@ int skew_tridiag_eig(int n, const double* alpha, int nev, double* lambda,
                      double* Q, int ldq, void* ws, size_t ws_bytes,
                      int* d_status, void* stream);
 
+/*
+ * skew_tridiag_eig without any device allocation: the same computation and
+ * results, with the scratch memory in a static device array of
+ * SKEW_NOALLOC_SCRATCH_BYTES (6 MiB) that every device loading the library
+ * holds until the process exits.  For callers that may not allocate device
+ * memory (their application owns every allocation, or cudaMalloc's device
+ * synchronisation is not allowed); the paper has no counterpart.
+ * Limit: with Q, about 41 * n * nev + 8 n bytes must fit (e.g. n = 512,
+ * nev = 256); larger sizes return SKEW_ERR_WORKSPACE.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  All calls
+ * share the array, which keeps the previous call's contents: calls that
+ * overlap on the GPU race, so serialise them.  Arguments 1 n >= 1, 2 alpha
+ * (device, n-1), 3 1 <= nev <= n, 4 lambda (device, nev), 5 Q (device or
+ * NULL), 6 ldq >= n, 7 d_status (device int, zeroed by the caller), 8 stream.
+ */
+#define SKEW_NOALLOC_SCRATCH_BYTES (6u << 20)
+int skew_tridiag_eig_noalloc(int n, const double* alpha, int nev, double* lambda,
+                             double* Q, int ldq, int* d_status, void* stream);
+
 /* Algorithm 1 step 3: X + iY = D Q, D = diag(i^r), r = 0..n-1. */
 int skew_dmap(int n, int k, const double* Q, int ldq, double* X, double* Y,
               int ldz, void* stream);

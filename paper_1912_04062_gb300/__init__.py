@@ -56,6 +56,7 @@ SIGNATURES = {
     "skew_band_to_tridiag": (_i, [_i, _i, _p, _i, _p, _p, _p, _p, _sz, _p, _p]),
     "skew_tridiag_ws": (_sz, [_i, _i]),
     "skew_tridiag_eig": (_i, [_i, _p, _i, _p, _p, _i, _p, _sz, _p, _p]),
+    "skew_tridiag_eig_noalloc": (_i, [_i, _p, _i, _p, _p, _i, _p, _p]),
     "skew_dmap": (_i, [_i, _i, _p, _i, _p, _p, _i, _p]),
     "skew_apply_qtrd": (_i, [_i, _i, _p, _p, _p, _i, _i, _p]),
     "skew_qband_ws": (_sz, [_i, _i, _i]),
@@ -300,6 +301,21 @@ def tridiag_eig(alpha, nev: int, vectors: bool = True, stream=None):
     code = lib().skew_tridiag_eig(n, _ptr(a), nev, _ptr(lam), _ptr(Q), n, _ptr(ws), ws.numel(), _ptr(st),
                                   _stream(stream))
     _check(code, "skew_tridiag_eig")
+    return lam, Q, st
+
+
+def tridiag_eig_noalloc(alpha, nev: int, vectors: bool = True, stream=None):
+    """tridiag_eig through the entry point that allocates no device memory
+    (its scratch is a static device array inside the library)."""
+    torch = _torch()
+    n = alpha.numel() + 1
+    a = torch.zeros(n, dtype=torch.float64, device=alpha.device)
+    a[: n - 1] = alpha
+    lam = torch.empty(nev, dtype=torch.float64, device=alpha.device)
+    Q = fortran_empty(n, nev, alpha.device) if vectors else None
+    st = _status(alpha.device)
+    code = lib().skew_tridiag_eig_noalloc(n, _ptr(a), nev, _ptr(lam), _ptr(Q), n, _ptr(st), _stream(stream))
+    _check(code, "skew_tridiag_eig_noalloc")
     return lam, Q, st
 
 
