@@ -49,6 +49,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--sample-cols", type=int, default=128)
+    p.add_argument("--form", default="mixed", choices=["mixed", "fp64"],
+                   help="mixed: BF16x6 tensor-core contractions + FP64 refinement; fp64: every step FP64")
+    p.add_argument("--fp64-compare", type=int, default=1,
+                   help="also time this many solves of the FP64 form (reported beside the mixed form)")
     return p.parse_args()
 
 
@@ -182,13 +186,15 @@ def run_ours(args, ws, rank, local):
     A = inputs.bse_device(n, seed=3 + rank, device=dev)
     torch.cuda.synchronize()
 
-    wsz = sk.workspace_size(n, nev)
+    mixed = args.form == "mixed"
+    opts = sk.Options(mode=sk.SKEW_MODE_MIXED_REFINED if mixed else sk.SKEW_MODE_FP64)
+    wsz = sk.workspace_size(n, nev, opts)
     work = torch.empty(wsz, dtype=torch.uint8, device=dev)
     lam = torch.empty(nev, dtype=torch.float64, device=dev)
     Zr, Zi = sk.fortran_empty(n, nev, dev), sk.fortran_empty(n, nev, dev)
 
     for _ in range(args.warmup):
-        code, _st = sk.skew_eig_profile(A, nev, lam, Zr, Zi, work)
+        code, _st = sk.skew_eig_profile(A, nev, lam, Zr, Zi, work, opts)
         if code not in (0,):
             raise RuntimeError(f"warm-up solve failed: {code} {sk.strerror(code)}")
 
@@ -201,7 +207,7 @@ def run_ours(args, ws, rank, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        code, st = sk.skew_eig_profile(A, nev, lam, Zr, Zi, work)
+        code, st = sk.skew_eig_profile(A, nev, lam, Zr, Zi, work, opts)
         if code != 0:
             raise RuntimeError(f"solve failed: {code} {sk.strerror(code)}")
         for k, v in st.items():
@@ -225,13 +231,51 @@ def run_ours(args, ws, rank, local):
     acc = {"resid_scaled": res * f / (n * eps * fro), "orth_scaled": orth * f / (n * eps),
            "sampled_cols": int(len(cols)), "lambda_max": float(lam.max().item()),
            "lambda_min": float(lam.min().item())}
+    if mixed:
+        it, em, nc = sk.refine_stats()
+        acc["refine_iterations"] = it
+        acc["refine_max_correction"] = em
+        lam_mixed = lam.clone()
+    del work
+    torch.cuda.empty_cache()
+
+    # ---- the FP64 form on the same matrix (the comparison the metric names)
+    fp64 = None
+    if mixed and args.fp64_compare > 0:
+        o64 = sk.Options(mode=sk.SKEW_MODE_FP64)
+        w64 = torch.empty(sk.workspace_size(n, nev, o64), dtype=torch.uint8, device=dev)
+        l64 = torch.empty(nev, dtype=torch.float64, device=dev)
+        Xr64, Xi64 = sk.fortran_empty(n, nev, dev), sk.fortran_empty(n, nev, dev)
+        times = []
+        for _ in range(args.fp64_compare):
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            code, st64 = sk.skew_eig_profile(A, nev, l64, Xr64, Xi64, w64, o64)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            if code != 0:
+                raise RuntimeError(f"FP64-form solve failed: {code}")
+            times.append(a0.elapsed_time(a1) / 1e3)
+        r64, o64n, _ = sk.metrics(A, l64, Xr64, Xi64, cols=cols)
+        fp64 = {"s": float(np.median(times)), "solves": len(times),
+                "resid_scaled": r64 * f / (n * eps * fro), "orth_scaled": o64n * f / (n * eps),
+                "max_lambda_diff_vs_mixed_rel": float(((l64 - lam_mixed).abs().max() / l64.abs().max()).item()),
+                "stages_ms": {k: round(v, 3) for k, v in st64.items()},
+                "speedup_mixed_over_fp64": float(np.median(times)) / (ms / 1e3)}
+        del w64, Xr64, Xi64
+        torch.cuda.empty_cache()
 
     # ---- roofline of the dominant stage
     F = {"band_reduce": 4.0 / 3.0 * n ** 3, "qtrd": 4.0 * n * n * nev, "qband": 4.0 * n * n * nev,
          "chase": 12.0 * 64 * 64 * (n * n / (2 * 64))}
+    if mixed:
+        # refinement: 4 FP64-accurate products of order n per iteration
+        F["refine"] = 4 * 2.0 * n ** 3 * max(1, acc.get("refine_iterations", 1))
     kern = {"band_reduce": "panel_qr_kernel + skew SYMM/rank-2k gemm_kernel/lower_tiles_kernel",
             "qtrd": "qtrd_kernel (1 launch per solve)", "qband": "gemm_kernel (3 per panel)",
-            "chase": "chase_kernel (1 launch per solve)"}
+            "chase": "chase_kernel (1 launch per solve)",
+            "refine": "ozaki_gemm_kernel (FP64-accurate digit-slice products; 4 per iteration)"}
     top = max(F, key=lambda k: stage_ms[k])
     achieved = F[top] / (stage_ms[top] * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -252,8 +296,9 @@ def run_ours(args, ws, rank, local):
         barrier(ws)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            oc = opts.c()
             code = L.skew_eig_host(n, sk._ptr(hA), n, nev, sk._ptr(hl), sk._ptr(hZr), sk._ptr(hZi),
-                                   sk._stream(stream))
+                                   sk.ctypes.byref(oc), sk._stream(stream))
             if code != 0:
                 raise RuntimeError(f"host solve failed: {code}")
         torch.cuda.synchronize()
@@ -273,13 +318,17 @@ def run_ours(args, ws, rank, local):
         out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": f"BSE-shaped skew n={n} nev={nev}, FP64 form (all steps FP64)",
-                          "n": n, "nev": nev, "band": 64, "form": "fp64",
+               "config": {"workload": (f"BSE-shaped skew n={n} nev={nev}, " +
+                                       ("mixed form (reduction contractions as FP64-accurate BF16 digit-slice "
+                                        "tensor-core products, Q_band BF16x6, Q_trd FP32, FP64 panels/chase/"
+                                        "tridiagonal) + FP64 refinement" if mixed else
+                                        "FP64 form (all steps FP64)")),
+                          "n": n, "nev": nev, "band": 64, "form": args.form,
                           "l2": "inputs larger than L2 (A = %.1f GB)" % (8 * n * n / 1e9),
                           "parallelism": "replicas" if ws > 1 else "single"},
                "tflops_nominal": total_F / (ms * 1e-3) / 1e12,
                "stages_ms": {k: round(v, 3) for k, v in stage_ms.items()},
-               "accuracy": acc, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "accuracy": acc, "fp64_form": fp64, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(out), flush=True)
 

@@ -54,22 +54,38 @@ extern "C" {
 
 typedef enum {
     SKEW_MODE_FP64 = 0,            /* every step in FP64 */
-    SKEW_MODE_MIXED_BF16X3 = 1,    /* dense contractions as BF16x3 splits on tcgen05 */
-    SKEW_MODE_MIXED_INT8 = 2       /* INT8 Ozaki splits: tcgen05 kind::i8 is not
+    SKEW_MODE_MIXED_BF16X3 = 1,    /* dense contractions (skew SYMM, rank-2k update,
+                                      Q_band) as BF16x3 splits on tcgen05, Q_trd in
+                                      FP32; reflectors, chase and tridiagonal solve
+                                      in FP64; then, when n is even and nev = n/2,
+                                      FP64 eigenpair refinement (Ogita-Aishima
+                                      through -iA) with FP64-accurate tensor-core
+                                      products (skew_gemm_f64acc) */
+    SKEW_MODE_MIXED_INT8 = 2,      /* INT8 Ozaki splits: tcgen05 kind::i8 is not
                                       available on sm_103a -> SKEW_ERR_UNSUPPORTED */
+    SKEW_MODE_MIXED_BF16X6 = 3,    /* as BF16X3 with three BF16 planes per operand
+                                      (hi, mid, lo) and the six products of order
+                                      <= 2: about FP32 accuracy */
+    SKEW_MODE_MIXED_REFINED = 4    /* the reduction's contractions (skew SYMM,
+                                      rank-2k update) as FP64-accurate BF16
+                                      digit-slice products on tcgen05, Q_band in
+                                      BF16x6, Q_trd in FP32, then the FP64
+                                      refinement (n even, nev = n/2) */
 } skew_mode;
 
 /* Fault hooks (host-side injection for tests; never fault the GPU). */
 #define SKEW_FAULT_NOMEM 1         /* pretend the workspace allocation failed */
 #define SKEW_FAULT_INVIT_NOCONV 2  /* give inverse iteration zero iterations */
 #define SKEW_FAULT_TINY_WAIT 4     /* make device waits give up at once */
+#define SKEW_FAULT_NO_REFINE 8     /* mixed modes: skip the FP64 refinement */
 
 typedef struct {
     int mode;          /* skew_mode; default SKEW_MODE_FP64 */
     int band;          /* panel width = band width b, a multiple of 64; 0 -> 64 */
     int check_finite;  /* 1: scan A for NaN/Inf first (SKEW_ERR_NONFINITE) */
     int fault;         /* SKEW_FAULT_* bits, tests only; 0 in production */
-    int reserved[4];
+    int refine_iters;  /* mixed modes: maximum refinement iterations; 0 -> 6 */
+    int reserved[3];
 } skew_opts;
 
 /* Default options (FP64 mode, b = 64). */
@@ -107,18 +123,19 @@ int skew_eig_ex(int n, const double* A, int lda, int nev, double* lambda,
 
 /*
  * Full solve from HOST buffers (A, lambda, Z_re, Z_im in host memory, ideally
- * pinned).  Copies A in, solves, copies results out; synchronises `stream`.
- * Same argument numbering and return codes as skew_eig.
+ * pinned).  Copies A in, solves with `opts` (NULL = default), copies results
+ * out; synchronises `stream`.  Argument numbering as skew_eig with 8 opts,
+ * 9 stream.
  */
 int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda,
-                  double* Z_re, double* Z_im, void* stream);
+                  double* Z_re, double* Z_im, const skew_opts* opts, void* stream);
 
 /* Stages timed by skew_eig_profile (Algorithm 1, two-step form):
  * 0 ingest (copy of the strict lower triangle), 1 full-to-band reduction,
  * 2 band pack, 3 bulge chase, 4 tridiagonal solve (bisection + inverse
  * iteration), 5 D map, 6 Q_trd back-transform, 7 Q_band back-transform,
- * 8 output copy. */
-#define SKEW_NSTAGES 9
+ * 8 FP64 refinement (mixed modes), 9 output copy. */
+#define SKEW_NSTAGES 10
 
 /*
  * skew_eig_ex plus CUDA events between the stages above, recorded on
@@ -144,6 +161,68 @@ size_t skew_metrics_ws(int n, int nev, int ncols);
 int skew_eig_metrics(int n, const double* A, int lda, int nev, const double* lambda,
                      const double* Z_re, const double* Z_im, int ldz, const int* cols,
                      int ncols, double* out3, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Mixed-precision dense contraction on the tensor cores (tcgen05, BF16
+ * inputs, FP32 accumulation in TMEM), the primitive of the mixed form:
+ *   C = alpha * A B^T + beta * C            (lower == 0)
+ *   C[lower 128-tiles] += alpha * A B^T, diagonal set to 0   (lower == 1, M == N)
+ * with every FP64 operand split into hi = bf16(x), lo = bf16(x - hi) and the
+ * product taken as hi*hi + lo*hi + hi*lo (relative error about 2^-16 per
+ * product plus K * 2^-24 from the FP32 sums).  Not in the paper.
+ * A is M x K with element (i, k) at A[i*a_rs + k*a_ks], B is N x K with
+ * (j, k) at B[j*b_rs + k*b_ks] (device, FP64); C is column-major FP64, ld
+ * ldc.  Workspace >= skew_gemm_bf16x3_ws(M, N, K) bytes (the BF16 planes).
+ * planes = 3 splits into hi, mid, lo and keeps the six products of order
+ * <= 2 (BF16x6, about 2^-24 relative).
+ * Arguments: 1 M, 2 N, 3 K >= 1, 13 ldc >= M, 14 lower, 15 planes (2 or 3).
+ */
+size_t skew_gemm_bf16x3_ws(int M, int N, int K);
+int skew_gemm_bf16x3(int M, int N, int K, double alpha, const double* A,
+                     long long a_rs, long long a_ks, const double* B, long long b_rs,
+                     long long b_ks, double beta, double* C, int ldc, int lower,
+                     int planes, void* ws, size_t ws_bytes, int* d_status, void* stream);
+
+/*
+ * FP64-accurate product on the BF16 tensor cores, the primitive of the
+ * eigenpair refinement of the mixed form:  C = alpha * A B^T + beta * C.
+ * Each row of A and of B is scaled by a power of two and cut into 8 digit
+ * slices of 7 bits (integers BF16 holds exactly); slice products of equal
+ * order are summed exactly in FP32 over K chunks of 128 and folded in
+ * double-float (about 48 bits), so the error is a few units of 2^-48 times
+ * the row-max products, independent of cancellation.  Not in the paper.
+ * Layouts and argument numbering as skew_gemm_bf16x3 (no lower mode).
+ */
+size_t skew_gemm_f64acc_ws(int M, int N, int K);
+int skew_gemm_f64acc(int M, int N, int K, double alpha, const double* A,
+                     long long a_rs, long long a_ks, const double* B, long long b_rs,
+                     long long b_ks, double beta, double* C, int ldc,
+                     void* ws, size_t ws_bytes, int* d_status, void* stream);
+
+/*
+ * FP64 eigenpair refinement on its own (the last stage of the mixed modes):
+ * given approximate lambda (n/2) and Z_re / Z_im (n x n/2, ld ldz, device)
+ * of skew A (n even), run at most `iters` Ogita-Aishima iterations through
+ * H = -iA with FP64-accurate tensor-core products and overwrite them.
+ * Synchronises `stream` once per iteration (convergence test).  Workspace
+ * >= skew_refine_ws(n) bytes.  Not in the paper.
+ * Arguments: 1 n (even, >= 2), 2 A, 3 lda, 4 lambda, 5/6 Z_re/Z_im, 7 ldz,
+ * 8 iters >= 1.
+ */
+size_t skew_refine_ws(int n);
+int skew_refine(int n, const double* A, int lda, double* lambda, double* Z_re,
+                double* Z_im, int ldz, int iters, void* ws, size_t ws_bytes,
+                int* d_status, void* stream);
+
+/* Statistics of the most recent refinement in this process (diagnostics):
+ * returns the number of iterations; emax[i] = largest first-order correction
+ * |E_jk| of iteration i, nclose[i] = pairs not separated enough for it
+ * (up to cap entries each, either pointer may be NULL). */
+int skew_refine_stats(double* emax, int* nclose, int cap);
+/* Same run: rnorm[i] = ||I - Z^H Z||_F seen by iteration i before its update,
+ * where[i] = location of the largest correction (row | column << 20 |
+ * block << 40, block 0 = Z^H Z part, 1 = conjugate part). */
+int skew_refine_trace(double* rnorm, long long* where, int cap);
 
 /* Number of CUDA kernels this library has launched in this process
  * (diagnostics; counts host-side launch calls). */

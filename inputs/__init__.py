@@ -121,28 +121,27 @@ def tridiagonal_skew(alpha: np.ndarray) -> np.ndarray:
 
 
 def bse_device(n: int, seed: int = 3, device="cuda"):
-    """``bse(n, seed)`` built on the GPU (same random draws, FP64 Cholesky and
-    product through torch), for orders where the host build is slow.
-    Returns a column-major (Fortran-strided) float64 CUDA tensor."""
+    """``bse(n, seed)`` with the final product on the GPU: the same random
+    draws, M and its Cholesky factor on the host (numpy/LAPACK), K = L^T (J L)
+    as one FP64 matmul on the device.  Returns a column-major
+    (Fortran-strided) float64 CUDA tensor."""
     import torch
     if n % 2:
         raise ValueError("bse_device() needs even n")
     h = n // 2
     rng = np.random.default_rng(seed)
-    G = torch.from_numpy(rng.standard_normal((h, h))).to(device)
-    d = torch.from_numpy(rng.uniform(2.0, 20.0, size=h)).to(device)
-    Ad = torch.diag(d) + 0.05 * 0.5 * (G + G.T) / np.sqrt(h)
+    G = rng.standard_normal((h, h))
+    Ad = np.diag(rng.uniform(2.0, 20.0, size=h)) + 0.05 * 0.5 * (G + G.T) / np.sqrt(h)
     del G
-    G2 = torch.from_numpy(rng.standard_normal((h, h))).to(device)
+    G2 = rng.standard_normal((h, h))
     B = 0.02 * 0.5 * (G2 + G2.T) / np.sqrt(h)
     del G2
-    M = torch.cat([torch.cat([Ad, B], 1), torch.cat([B, Ad], 1)], 0)
+    M = np.block([[Ad, B], [B, Ad]])
     del Ad, B
-    L = torch.linalg.cholesky(M)
+    L = torch.from_numpy(np.linalg.cholesky(M)).to(device)
     del M
     JL = torch.cat([L[h:], -L[:h]], 0)          # J L with J = [[0, I], [-I, 0]]
     K = L.T @ JL
     del JL, L
     K = 0.5 * (K - K.T)
-    # column-major copy
     return K.T.contiguous().T

@@ -30,10 +30,13 @@ SKEW_ERR_LAUNCH = 2007
 SKEW_MODE_FP64 = 0
 SKEW_MODE_MIXED_BF16X3 = 1
 SKEW_MODE_MIXED_INT8 = 2
+SKEW_MODE_MIXED_BF16X6 = 3
+SKEW_MODE_MIXED_REFINED = 4
 
 SKEW_FAULT_NOMEM = 1
 SKEW_FAULT_INVIT_NOCONV = 2
 SKEW_FAULT_TINY_WAIT = 4
+SKEW_FAULT_NO_REFINE = 8
 
 # every entry point the header declares: name -> (restype, argtypes)
 _i, _d, _p, _sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
@@ -43,11 +46,21 @@ SIGNATURES = {
     "skew_eig": (_i, [_i, _p, _i, _i, _p, _p, _p, _p]),
     "skew_eig_workspace_size": (_sz, [_i, _i, _p]),
     "skew_eig_ex": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
-    "skew_eig_host": (_i, [_i, _p, _i, _i, _p, _p, _p, _p]),
+    "skew_eig_host": (_i, [_i, _p, _i, _i, _p, _p, _p, _p, _p]),
     "skew_eig_profile": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
     "skew_metrics_ws": (_sz, [_i, _i, _i]),
     "skew_eig_metrics": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _i, _p, _p, _sz, _p]),
     "skew_launch_count": (ctypes.c_longlong, []),
+    "skew_refine_stats": (_i, [_p, _p, _i]),
+    "skew_refine_ws": (_sz, [_i]),
+    "skew_refine": (_i, [_i, _p, _i, _p, _p, _p, _i, _i, _p, _sz, _p, _p]),
+    "skew_refine_trace": (_i, [_p, _p, _i]),
+    "skew_gemm_bf16x3_ws": (_sz, [_i, _i, _i]),
+    "skew_gemm_f64acc_ws": (_sz, [_i, _i, _i]),
+    "skew_gemm_f64acc": (_i, [_i, _i, _i, _d, _p, ctypes.c_longlong, ctypes.c_longlong, _p, ctypes.c_longlong,
+                              ctypes.c_longlong, _d, _p, _i, _p, _sz, _p, _p]),
+    "skew_gemm_bf16x3": (_i, [_i, _i, _i, _d, _p, ctypes.c_longlong, ctypes.c_longlong, _p, ctypes.c_longlong,
+                              ctypes.c_longlong, _d, _p, _i, _i, _i, _p, _sz, _p, _p]),
     "skew_band_reduce_ws": (_sz, [_i, _i]),
     "skew_band_reduce": (_i, [_i, _p, _i, _i, _p, _p, _sz, _p, _p]),
     "skew_band_pack": (_i, [_i, _i, _p, _i, _p, _i, _p]),
@@ -66,7 +79,7 @@ SIGNATURES = {
 
 class skew_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("band", ctypes.c_int), ("check_finite", ctypes.c_int),
-                ("fault", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("fault", ctypes.c_int), ("refine_iters", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -144,11 +157,13 @@ class Options:
     band: int = 64
     check_finite: int = 0
     fault: int = 0
+    refine_iters: int = 0
 
     def c(self):
         o = skew_opts()
         lib().skew_opts_default(ctypes.byref(o))
         o.mode, o.band, o.check_finite, o.fault = self.mode, self.band, self.check_finite, self.fault
+        o.refine_iters = self.refine_iters
         return o
 
 
@@ -181,7 +196,7 @@ def skew_eig_ex(A, nev: int, lam, Zr, Zi, workspace, d_info, opts: Options | Non
                              _stream(stream))
 
 
-STAGES = ["ingest", "band_reduce", "band_pack", "chase", "tridiag", "dmap", "qtrd", "qband", "output"]
+STAGES = ["ingest", "band_reduce", "band_pack", "chase", "tridiag", "dmap", "qtrd", "qband", "refine", "output"]
 
 
 def skew_eig_profile(A, nev: int, lam, Zr, Zi, workspace, opts: Options | None = None, stream=None):
@@ -217,11 +232,76 @@ def metrics(A, lam, Zr, Zi, cols=None, stream=None):
     return float(out[0]), float(out[1]), float(out[2])
 
 
+def gemm_bf16x3(A, B, C=None, alpha=1.0, beta=0.0, lower=False, planes=2, stream=None):
+    """C = alpha * A @ B.T + beta * C on the tensor cores with BF16x3 splits
+    (A: M x K, B: N x K float64 CUDA tensors of any strides; C Fortran-strided,
+    returned).  lower=True: only the lower 128-tiles, C += alpha A B^T with a
+    zero diagonal."""
+    torch = _torch()
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = fortran_empty(M, N, A.device)
+        C.zero_()
+    ws = _ws(lib().skew_gemm_bf16x3_ws(M, N, K), A.device)
+    st = _status(A.device)
+    code = lib().skew_gemm_bf16x3(M, N, K, alpha, _ptr(A), A.stride(0), A.stride(1), _ptr(B), B.stride(0),
+                                  B.stride(1), beta, _ptr(C), _ld(C), 1 if lower else 0, planes, _ptr(ws), ws.numel(),
+                                  _ptr(st), _stream(stream))
+    _check(code, "skew_gemm_bf16x3")
+    return C, st
+
+
+def gemm_f64acc(A, B, C=None, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha * A @ B.T + beta * C to FP64 accuracy on the BF16 tensor cores
+    (exact digit slices).  A: M x K, B: N x K float64 CUDA tensors."""
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = fortran_empty(M, N, A.device)
+        C.zero_()
+    ws = _ws(lib().skew_gemm_f64acc_ws(M, N, K), A.device)
+    st = _status(A.device)
+    code = lib().skew_gemm_f64acc(M, N, K, alpha, _ptr(A), A.stride(0), A.stride(1), _ptr(B), B.stride(0),
+                                  B.stride(1), beta, _ptr(C), _ld(C), _ptr(ws), ws.numel(), _ptr(st), _stream(stream))
+    _check(code, "skew_gemm_f64acc")
+    return C, st
+
+
+def refine_stats():
+    """(iterations, [emax per iteration], [nclose per iteration]) of the most
+    recent refinement in this process."""
+    em = (ctypes.c_double * 8)()
+    nc = (ctypes.c_int * 8)()
+    it = lib().skew_refine_stats(em, nc, 8)
+    return it, [float(x) for x in em[:it]], [int(x) for x in nc[:it]]
+
+
+def refine(A, lam, Zr, Zi, iters=6, stream=None):
+    """FP64 refinement of (lam, Zr + i Zi) in place (n even, nev = n/2)."""
+    A = _as_device_f64(A)
+    n = A.shape[0]
+    ws = _ws(lib().skew_refine_ws(n), A.device)
+    st = _status(A.device)
+    code = lib().skew_refine(n, _ptr(A), _ld(A), _ptr(lam), _ptr(Zr), _ptr(Zi), _ld(Zr), iters, _ptr(ws),
+                             ws.numel(), _ptr(st), _stream(stream))
+    _check(code, "skew_refine")
+    return lam, Zr, Zi
+
+
+def refine_trace():
+    rn = (ctypes.c_double * 8)()
+    wh = (ctypes.c_longlong * 8)()
+    it = lib().skew_refine_trace(rn, wh, 8)
+    locs = [(int(w) & 0xFFFFF, (int(w) >> 20) & 0xFFFFF, (int(w) >> 40) & 1) for w in wh[:it]]
+    return [float(x) for x in rn[:it]], locs
+
+
 def launch_count() -> int:
     return int(lib().skew_launch_count())
 
 
-def skew_eig_host(A, nev: int, vectors: bool = True, stream=None):
+def skew_eig_host(A, nev: int, vectors: bool = True, opts: Options | None = None, stream=None):
     """Solve from host (ideally pinned) float64 tensors; returns host tensors."""
     torch = _torch()
     A = fortran(A.to(torch.float64))
@@ -230,7 +310,9 @@ def skew_eig_host(A, nev: int, vectors: bool = True, stream=None):
     lam = torch.empty(max(nev, 1), dtype=torch.float64, pin_memory=pin)
     Zr = torch.empty((nev, n), dtype=torch.float64, pin_memory=pin).t() if vectors else None
     Zi = torch.empty((nev, n), dtype=torch.float64, pin_memory=pin).t() if vectors else None
-    code = lib().skew_eig_host(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), _stream(stream))
+    o = (opts or Options()).c()
+    code = lib().skew_eig_host(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), ctypes.byref(o),
+                               _stream(stream))
     _check(code, "skew_eig_host")
     return lam[:nev], Zr, Zi
 

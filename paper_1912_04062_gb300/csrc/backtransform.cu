@@ -32,13 +32,21 @@ constexpr int QT = 256;
 
 __host__ __device__ inline int qsteps(int n, int b, int s) { return (s <= n - 3) ? 1 + (n - 3 - s) / b : 0; }
 
-// Thread t: column c = t / 4 of the slab, row phase q = t % 4 (rows 4i + q of
-// the reflector).  The four threads of a column are lanes of one warp, so a
-// reflector needs only warp shuffles and __syncwarp.
+// Thread t: column c = t / 4 of the slab, row phase q = t % 4.  The thread
+// keeps window rows 4u + q (u < 32) of its column in registers for the whole
+// block; the block's ell reflectors (v zero-padded to b, tau) are staged once
+// in shared memory.  Reflector s touches window rows off..off+b-1 with
+// off = s - s0; the loop over off is unrolled, so every register index is a
+// compile-time constant.  The four threads of a column are lanes of one warp:
+// a reflector costs two shuffles and no block barrier.
+template <typename T>
 __global__ void __launch_bounds__(QT)
-qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ tautrd, double* __restrict__ Z,
+qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ tautrd, T* __restrict__ Z,
             int ldz, int ncols, int slab) {
-    extern __shared__ double zw[];  // QLD x 64
+    extern __shared__ __align__(16) unsigned char qtrd_raw[];
+    T* zw = reinterpret_cast<T*>(qtrd_raw);  // QLD x 64 staging of the window
+    T* vs = zw + QLD * 64;                   // QELL x QB reflectors of the block
+    T* ts = vs + QELL * QB;                  // QELL taus
     const int nsw = n - 2;
     const int c0 = blockIdx.x * slab;
     const int nc = min(slab, ncols - c0);
@@ -55,27 +63,113 @@ qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ t
             const int top = s0 + 1 + k * QB;
             if (top >= n) break;
             const int H = min(QH, n - top);
+            // stage the reflectors (zero when sweep s has no step k) and the window
+            for (int e = t; e < QELL * QB; e += QT) {
+                const int sl = e / QB, i = e % QB, s = s0 + sl;
+                T v = 0;
+                if (s < s1 && k < qsteps(n, QB, s)) v = (T)Vtrd[((size_t)k * nsw + s) * QB + i];
+                vs[e] = v;
+            }
+            for (int sl = t; sl < QELL; sl += QT) {
+                const int s = s0 + sl;
+                ts[sl] = (s < s1 && k < qsteps(n, QB, s)) ? (T)tautrd[(size_t)k * nsw + s] : (T)0;
+            }
+            for (int e = t; e < H * nc; e += QT) {
+                int i = e % H, cc = e / H;
+                zw[cc * QLD + i] = Z[(size_t)(c0 + cc) * ldz + top + i];
+            }
+            __syncthreads();
+            T zr[32];
+            const T* zc = zw + c * QLD;
+#pragma unroll
+            for (int u = 0; u < 32; u++) {
+                const int r = 4 * u + q;
+                zr[u] = (r < H) ? zc[r] : (T)0;
+            }
+#pragma unroll
+            for (int off = QELL - 1; off >= 0; off--) {
+                const T tau = ts[off];
+                if (tau == (T)0) continue;
+                const T* v = vs + off * QB;
+                T a = 0;
+#pragma unroll
+                for (int u = 0; u < 32; u++) {
+                    if (4 * u + 3 < off || 4 * u > off + QB - 1) continue;
+                    const int i = 4 * u + q - off;
+                    if (i >= 0 && i < QB) a = fma(v[i], zr[u], a);
+                }
+                a += __shfl_xor_sync(0xffffffffu, a, 1);
+                a += __shfl_xor_sync(0xffffffffu, a, 2);
+                a *= tau;
+#pragma unroll
+                for (int u = 0; u < 32; u++) {
+                    if (4 * u + 3 < off || 4 * u > off + QB - 1) continue;
+                    const int i = 4 * u + q - off;
+                    if (i >= 0 && i < QB) zr[u] = fma(-a, v[i], zr[u]);
+                }
+            }
+            T* zcw = zw + c * QLD;
+#pragma unroll
+            for (int u = 0; u < 32; u++) {
+                const int r = 4 * u + q;
+                if (r < H) zcw[r] = zr[u];
+            }
+            __syncthreads();
+            for (int e = t; e < H * nc; e += QT) {
+                int i = e % H, cc = e / H;
+                Z[(size_t)(c0 + cc) * ldz + top + i] = zw[cc * QLD + i];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// FP64 variant: the window stays in shared memory (ld QLD, conflict-free for
+// doubles); thread (c, q) owns rows 4i + q of column c for each reflector.  On
+// this part the FP64 pipe is the limit, and the shared-memory form keeps it
+// busier than the register-resident one.
+template <typename T>
+__global__ void __launch_bounds__(QT)
+qtrd_smem_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ tautrd, T* __restrict__ Z,
+                 int ldz, int ncols, int slab) {
+    extern __shared__ __align__(16) unsigned char qtrd_raw[];
+    T* zw = reinterpret_cast<T*>(qtrd_raw);  // QLD x 64
+    const int nsw = n - 2;
+    const int c0 = blockIdx.x * slab;
+    const int nc = min(slab, ncols - c0);
+    if (nc <= 0) return;
+    const int t = threadIdx.x;
+    const int c = t >> 2, q = t & 3;
+    const int ngroups = (nsw + QELL - 1) / QELL;
+    for (int g = ngroups - 1; g >= 0; g--) {
+        const int s0 = g * QELL, s1 = min(nsw, s0 + QELL);
+        const int kmax = qsteps(n, QB, s0);
+        for (int k = 0; k < kmax; k++) {
+            const int top = s0 + 1 + k * QB;
+            if (top >= n) break;
+            const int H = min(QH, n - top);
             for (int e = t; e < H * nc; e += QT) {
                 int i = e % H, cc = e / H;
                 zw[cc * QLD + i] = Z[(size_t)(c0 + cc) * ldz + top + i];
             }
             __syncthreads();
             {
-                double* zc = zw + c * QLD;
+                T* zc = zw + c * QLD;
                 for (int s = s1 - 1; s >= s0; s--) {
                     if (k >= qsteps(n, QB, s)) continue;
                     const size_t vi = (size_t)k * nsw + s;
-                    const double tau = tautrd[vi];
-                    if (tau == 0.0) continue;
+                    const double taud = tautrd[vi];
+                    if (taud == 0.0) continue;
+                    const T tau = (T)taud;
                     const double* v = Vtrd + vi * QB;
                     const int off = s - s0;
                     const int lim = min(QB, H - off);
-                    double vr[QB / 4];
-                    double a = 0.0;
+                    T vr[QB / 4];
+                    T a = 0;
 #pragma unroll
                     for (int ii = 0; ii < QB / 4; ii++) {
                         int i = 4 * ii + q;
-                        vr[ii] = (i < lim) ? __ldg(v + i) : 0.0;
+                        vr[ii] = (i < lim) ? (T)__ldg(v + i) : (T)0;
                         if (i < lim) a = fma(vr[ii], zc[off + i], a);
                     }
                     a += __shfl_xor_sync(0xffffffffu, a, 1);
@@ -111,10 +205,9 @@ QbandWs carve_qband(Carve& cv, int n, int b, int k) {
     return w;
 }
 
-}  // namespace
-
-cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, double* Z, int ldz,
-                       int k) {
+template <typename T>
+cudaError_t apply_qtrd_t(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, T* Z, int ldz,
+                         int k) {
     if (b != QB) return cudaErrorInvalidValue;
     if (n < 3 || k <= 0) return cudaSuccess;
     // slab width so that the CTA count fills the GPU in whole waves
@@ -127,11 +220,30 @@ cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd, const 
     }
     if (slab < 8) slab = (k < 8) ? k : 8;
     const int grid = (k + slab - 1) / slab;
-    const size_t smem = sizeof(double) * (size_t)QLD * 64;
-    cudaFuncSetAttribute(qtrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    qtrd_kernel<<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
+    if (sizeof(T) == sizeof(double)) {
+        const size_t smem = sizeof(T) * (size_t)QLD * 64;
+        cudaFuncSetAttribute(qtrd_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        qtrd_smem_kernel<T><<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
+        count_launch();
+        return cudaGetLastError();
+    }
+    const size_t smem = sizeof(T) * ((size_t)QLD * 64 + (size_t)QELL * QB + QELL);
+    cudaFuncSetAttribute(qtrd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    qtrd_kernel<T><<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
     count_launch();
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, double* Z, int ldz,
+                       int k) {
+    return apply_qtrd_t<double>(st, n, b, Vtrd, tautrd, Z, ldz, k);
+}
+
+cudaError_t apply_qtrd_f32(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, float* Z, int ldz,
+                           int k) {
+    return apply_qtrd_t<float>(st, n, b, Vtrd, tautrd, Z, ldz, k);
 }
 
 size_t qband_ws(int n, int b, int k) {
@@ -155,6 +267,40 @@ int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw, const d
         if (gemm(st, true, false, b, k, m, 1.0, w.V, n, Zo, ldz, 0.0, w.Y, b) != cudaSuccess) return SKEW_ERR_CUDA;
         if (gemm(st, false, false, b, k, b, 1.0, Tp, b, w.Y, b, 0.0, w.Y2, b) != cudaSuccess) return SKEW_ERR_CUDA;
         if (gemm(st, false, false, m, k, b, -1.0, w.V, n, w.Y2, b, 1.0, Zo, ldz) != cudaSuccess) return SKEW_ERR_CUDA;
+    }
+    return 0;
+}
+
+// Mixed form: Q_band with the two contractions on the tensor cores (BF16x3):
+// Y^T = Z[o:, :]^T V_p, then Z[o:, :] -= (V_p T_p) Y, V_p T_p in FP64.
+size_t qband_mixed_ws(int n, int b, int k, int planes) {
+    size_t g1 = split_gemm_ws(k, b, n, planes), g2 = split_gemm_ws(n, k, b, planes);
+    return align_up(sizeof(double) * (size_t)n * b) * 2 + align_up(sizeof(double) * (size_t)k * b) +
+           (g1 > g2 ? g1 : g2) + 256;
+}
+
+int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz,
+                      int k, void* ws, size_t ws_bytes, int* status, int planes) {
+    const int P = num_panels(n, b);
+    if (P == 0 || k <= 0) return 0;
+    Carve cv(ws, ws_bytes);
+    double* V = cv.take<double>((size_t)n * b);
+    double* VT = cv.take<double>((size_t)n * b);
+    double* Yt = cv.take<double>((size_t)k * b);
+    size_t g1 = split_gemm_ws(k, b, n, planes), g2 = split_gemm_ws(n, k, b, planes);
+    size_t gsz = g1 > g2 ? g1 : g2;
+    void* gws = cv.take<char>(gsz);
+    if (!cv.ok) return SKEW_ERR_WORKSPACE;
+    for (int p = P - 1; p >= 0; p--) {
+        const int o = (p + 1) * b, m = n - o;
+        const double* Tp = Tfac + (size_t)p * b * b;
+        double* Zo = Z + o;
+        if (panel_v(st, n, b, p, W, ldw, V, n) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (gemm(st, false, false, m, b, b, 1.0, V, n, Tp, b, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
+        int rc = split_gemm(st, k, b, m, 1.0, Zo, ldz, 1, 0, V, n, 1, 0.0, Yt, k, 0, gws, gsz, status, planes);
+        if (rc) return rc;
+        rc = split_gemm(st, m, k, b, -1.0, VT, 1, n, 0, Yt, 1, k, 1.0, Zo, ldz, 0, gws, gsz, status, planes);
+        if (rc) return rc;
     }
     return 0;
 }

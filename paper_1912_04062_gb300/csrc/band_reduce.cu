@@ -238,9 +238,22 @@ ReduceWs carve_reduce(Carve& cv, int n, int b) {
 
 int num_panels(int n, int b) { return (n - 2 >= b) ? (n - 2) / b : 0; }
 
-size_t band_reduce_ws(int n, int b) {
+size_t mixed_gemm_ws(int n, int b, int planes) {
+    size_t g1, g2;
+    if (planes == REDUCE_F64ACC) {
+        g1 = ozaki_gemm_ws(n, b, n);
+        g2 = ozaki_gemm_ws(n, n, 2 * b);
+    } else {
+        g1 = split_gemm_ws(n, b, n, planes);
+        g2 = split_gemm_ws(n, n, 2 * b, planes);
+    }
+    return g1 > g2 ? g1 : g2;
+}
+
+size_t band_reduce_ws(int n, int b, int planes) {
     Carve cv(nullptr, ~size_t(0));
     carve_reduce(cv, n, b);
+    if (planes) cv.take<char>(mixed_gemm_ws(n, b, planes));
     return cv.off + 256;
 }
 
@@ -253,12 +266,15 @@ cudaError_t panel_v(cudaStream_t st, int n, int b, int p, const double* W, int l
 }
 
 int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac, void* ws,
-                size_t ws_bytes, int* d_status) {
+                size_t ws_bytes, int* d_status, int planes) {
+    const bool mixed = planes > 0;
     if (b <= 0 || b % 64 != 0 || b > 128) return SKEW_ERR_UNSUPPORTED;
     const int P = num_panels(n, b);
     if (P == 0) return 0;
     Carve cv(ws, ws_bytes);
     ReduceWs w = carve_reduce(cv, n, b);
+    const size_t gsz = mixed ? mixed_gemm_ws(n, b, planes) : 0;
+    void* gws = mixed ? cv.take<char>(gsz) : nullptr;
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
 
     int dev = 0, max_smem = 0;
@@ -295,7 +311,17 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         tfactor_kernel<<<1, 128, sizeof(double) * (b * b + b), st>>>(b, taup, w.G, Tp);
         count_launch();
         // ---- a3: P = A22 V (skew, lower triangle only)
-        if (skew_symm(st, m, b, A22, ldw, w.V, n, w.Pm, n) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (planes == REDUCE_F64ACC) {
+            int rc = ozaki_gemm(st, m, b, m, 1.0, A22, 0, ldw, 1.0, w.V, n, 1, 1.0, 0.0, w.Pm, n, gws, gsz, d_status,
+                                1);
+            if (rc) return rc;
+        } else if (mixed) {
+            int rc = split_gemm(st, m, b, m, 1.0, A22, 0, ldw, 1, w.V, n, 1, 0.0, w.Pm, n, 0, gws, gsz, d_status,
+                                planes);
+            if (rc) return rc;
+        } else if (skew_symm(st, m, b, A22, ldw, w.V, n, w.Pm, n) != cudaSuccess) {
+            return SKEW_ERR_CUDA;
+        }
         // ---- a4: Y = P T; C = T^T (V^T Y); W = Y - V C / 2
         if (gemm(st, false, false, m, b, b, 1.0, w.Pm, n, Tp, b, 0.0, w.Y, n) != cudaSuccess) return SKEW_ERR_CUDA;
         if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.Y, n, 0.0, w.C1, b) != cudaSuccess) return SKEW_ERR_CUDA;
@@ -304,7 +330,18 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         // ---- a5: A22 += [V W][W -V]^T (lower tiles)
         concat_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, w.V, w.Y, n, w.X2, w.Y2);
         count_launch();
-        if (gemm_lower_tiles(st, m, 2 * b, w.X2, n, w.Y2, n, A22, ldw) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (planes == REDUCE_F64ACC) {
+            // all tiles (the upper triangle of W is never read); diagonal ~0
+            int rc = ozaki_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 1.0, w.Y2, 1, n, 1.0, 1.0, A22, ldw, gws, gsz,
+                                d_status, 0);
+            if (rc) return rc;
+        } else if (mixed) {
+            int rc = split_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 0, w.Y2, 1, n, 1.0, A22, ldw, 1, gws, gsz, d_status,
+                                planes);
+            if (rc) return rc;
+        } else if (gemm_lower_tiles(st, m, 2 * b, w.X2, n, w.Y2, n, A22, ldw) != cudaSuccess) {
+            return SKEW_ERR_CUDA;
+        }
     }
     return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
 }

@@ -212,7 +212,7 @@ int pick_split(int tiles, int K, int requested) {
     if (requested > 0) return requested;
     const int target = 2 * device_sms();
     int s = 1;
-    while (tiles * s < target && K / (s * 2) >= 256) s *= 2;
+    while (tiles * s < target && K / (s * 2) >= 64) s *= 2;
     return s;
 }
 

@@ -31,9 +31,13 @@ cudaError_t gemm_lower_tiles(cudaStream_t st, int m, int k, const double* X, int
                              const double* Y, int ldy, double* C, int ldc);
 
 // ---- band_reduce.cu --------------------------------------------------------
-size_t band_reduce_ws(int n, int b);
+// planes > 0: the skew SYMM and the rank-2k update run as split-BF16 tensor-core
+// GEMMs with that many planes per operand (2: BF16x3, 3: BF16x6); planes ==
+// REDUCE_F64ACC: as FP64-accurate digit-slice tensor-core products.
+constexpr int REDUCE_F64ACC = 8;
+size_t band_reduce_ws(int n, int b, int planes = 0);
 int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
-                void* ws, size_t ws_bytes, int* d_status);
+                void* ws, size_t ws_bytes, int* d_status, int planes = 0);
 cudaError_t band_pack(cudaStream_t st, int n, int b, const double* W, int ldw,
                       double* AB, int ldab);
 // Explicit V (m x b, ld ldv) of panel p from the reduced W.
@@ -63,9 +67,50 @@ cudaError_t dmap_colmajor(cudaStream_t st, int n, int k, const double* Q, int ld
 // ---- backtransform.cu -------------------------------------------------------
 cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd,
                        const double* tautrd, double* Z, int ldz, int k);
+cudaError_t apply_qtrd_f32(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, float* Z,
+                           int ldz, int k);
 size_t qband_ws(int n, int b, int k);
+size_t qband_mixed_ws(int n, int b, int k, int planes);
+int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz,
+                      int k, void* ws, size_t ws_bytes, int* status, int planes);
 int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw,
                 const double* Tfac, double* Z, int ldz, int k, void* ws, size_t ws_bytes);
+
+// ---- umma_gemm.cu (tcgen05 BF16x3) ------------------------------------------
+// C = alpha * split3(A) split3(B)^T + beta * C (FP64 C, column-major, ldc) with
+// A[i,k] = A[i*a_rs + k*a_ks] (or the skew matrix of a lower triangle stored
+// column-major with ld a_ks when a_skew), B[j,k] = B[j*b_rs + k*b_ks];
+// lower: only the lower 128-tiles of C (M == N), C += alpha D, zero diagonal.
+// nplanes = 2: BF16x3 (hi*hi + lo*hi + hi*lo); nplanes = 3: BF16x6 (the six
+// products of order <= 2 of hi, mid, lo).
+size_t split_gemm_ws(int M, int N, int K, int nplanes = 3);
+int split_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, long long a_rs, long long a_ks,
+               int a_skew, const double* B, long long b_rs, long long b_ks, double beta, double* C, long long ldc,
+               int lower, void* ws, size_t ws_bytes, int* status, int nplanes = 3);
+
+// ---- ozaki_gemm.cu (FP64-accurate product from exact BF16 digit slices) -------
+// C = alpha * (sa A)(sb B)^T + beta * C, A[i,k] = A[i*a_rs + k*a_ks],
+// B[j,k] = B[j*b_rs + k*b_ks], C column-major.
+size_t ozaki_gemm_ws(int M, int N, int K);
+// a_skew: A is the skew matrix of the strict lower triangle stored column-major
+// with leading dimension a_ks (a_rs unused).
+int ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, long long a_rs, long long a_ks,
+               double sa, const double* B, long long b_rs, long long b_ks, double sb, double beta, double* C,
+               long long ldc, void* ws, size_t ws_bytes, int* status, int a_skew = 0);
+
+// ---- refine.cu (FP64 eigenpair refinement, mixed form) ---------------------------
+struct RefineInfo {
+    int iterations;
+    double emax[8];   // largest |E_ij| over separated pairs, per iteration
+    int nclose[8];    // pairs not separated (E_ij = R_ij / 2), per iteration
+    double rnorm[8];  // ||R||_F over the Z^H Z block before each update
+    long long where[8];  // location of the largest correction: i | j << 20 | block << 40
+};
+size_t refine_ws(int n);
+// M = [X Y] (n x n, ld n) and lambda (n/2) refined in place; n even.
+int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, double* M, int maxit, void* ws,
+           size_t ws_bytes, int* status, RefineInfo* info);
+RefineInfo& last_refine_info();
 
 // ---- metrics.cu -------------------------------------------------------------
 size_t metrics_ws(int n, int nev, int s);

@@ -55,17 +55,21 @@ inline int grid_for(size_t total) {
 
 struct Plan {
     int n, nev, b, P, K, nsw;
-    bool vectors;
+    bool vectors, mixed;
+    int planes;       // split-BF16 planes of the mixed back-transforms (0 in the FP64 form)
+    int reduce_prec;  // band reduction: 0 FP64, 2/3 split planes, REDUCE_F64ACC digit slices
     size_t ldab;
     // carved pointers
     double *W, *Tfac, *AB, *Vtrd, *tautrd, *alpha, *Qi, *Z;
+    float* Z32;
     int* status;
-    void *ws_reduce, *ws_chase, *ws_tri, *ws_qband;
-    size_t sz_reduce, sz_chase, sz_tri, sz_qband;
+    void *ws_reduce, *ws_chase, *ws_tri, *ws_qband, *ws_refine;
+    size_t sz_reduce, sz_chase, sz_tri, sz_qband, sz_refine;
+    bool refine;  // mixed form with a complete basis (n even, nev = n/2)
 };
 
-bool carve_plan(Plan& p, void* base, size_t cap) {
-    Carve cv(base, cap);
+// One carve-up routine serves both sizing (base == nullptr) and placement.
+bool carve_plan(Plan& p, Carve& cv) {
     const size_t n = (size_t)p.n, b = (size_t)p.b;
     const size_t nn = n ? n : 1;
     p.status = cv.take<int>(16);
@@ -80,14 +84,18 @@ bool carve_plan(Plan& p, void* base, size_t cap) {
     const size_t ne = (size_t)(p.nev ? p.nev : 1);
     p.Qi = p.vectors ? cv.take<double>(nn * ne) : nullptr;
     p.Z = p.vectors ? cv.take<double>(nn * 2 * ne) : nullptr;
-    p.sz_reduce = band_reduce_ws(p.n, p.b);
+    p.Z32 = (p.vectors && p.mixed) ? cv.take<float>(nn * 2 * ne) : nullptr;
+    p.sz_reduce = band_reduce_ws(p.n, p.b, p.reduce_prec);
     p.ws_reduce = cv.take<char>(p.sz_reduce);
     p.sz_chase = chase_ws(p.n, p.b);
     p.ws_chase = cv.take<char>(p.sz_chase);
     p.sz_tri = tridiag_ws(p.n, p.nev);
     p.ws_tri = cv.take<char>(p.sz_tri);
-    p.sz_qband = p.vectors ? qband_ws(p.n, p.b, 2 * p.nev) : 0;
+    p.sz_qband = p.vectors ? (p.mixed ? qband_mixed_ws(p.n, p.b, 2 * p.nev, p.planes) : qband_ws(p.n, p.b, 2 * p.nev))
+                           : 0;
     p.ws_qband = p.vectors ? cv.take<char>(p.sz_qband) : nullptr;
+    p.sz_refine = p.refine ? refine_ws(p.n) : 0;
+    p.ws_refine = p.refine ? cv.take<char>(p.sz_refine) : nullptr;
     return cv.ok;
 }
 
@@ -100,32 +108,29 @@ Plan make_plan(int n, int nev, const skew_opts* o, bool vectors) {
     p.K = chase_steps(n, p.b);
     p.nsw = n - 2;
     p.vectors = vectors;
+    p.mixed = o && (o->mode == SKEW_MODE_MIXED_BF16X3 || o->mode == SKEW_MODE_MIXED_BF16X6 ||
+                    o->mode == SKEW_MODE_MIXED_REFINED);
+    p.planes = !p.mixed ? 0 : (o->mode == SKEW_MODE_MIXED_BF16X3 ? 2 : 3);
+    // the reduction's contractions in the refined mode are FP64-accurate
+    p.reduce_prec = !p.mixed ? 0 : (o->mode == SKEW_MODE_MIXED_REFINED ? REDUCE_F64ACC : p.planes);
+    p.refine = p.mixed && vectors && n % 2 == 0 && n >= 2 && nev == n / 2 && !(o->fault & SKEW_FAULT_NO_REFINE);
     return p;
 }
 
 size_t plan_bytes(int n, int nev, const skew_opts* o, bool vectors) {
     Plan p = make_plan(n, nev, o, vectors);
     Carve cv(nullptr, ~size_t(0));
-    // replicate carve_plan with a null base to size it
-    const size_t nn = n ? (size_t)n : 1, b = (size_t)p.b;
-    cv.take<int>(16);
-    cv.take<double>(nn * nn);
-    cv.take<double>((size_t)(p.P ? p.P : 1) * b * b);
-    cv.take<double>((2 * b + 1) * nn);
-    const size_t nsw = (size_t)(p.nsw > 0 ? p.nsw : 1), K = (size_t)(p.K > 0 ? p.K : 1);
-    cv.take<double>(K * nsw * b);
-    cv.take<double>(K * nsw);
-    cv.take<double>(nn);
-    const size_t ne = (size_t)(nev ? nev : 1);
-    if (vectors) {
-        cv.take<double>(nn * ne);
-        cv.take<double>(nn * 2 * ne);
-    }
-    cv.take<char>(band_reduce_ws(n, p.b));
-    cv.take<char>(chase_ws(n, p.b));
-    cv.take<char>(tridiag_ws(n, nev));
-    if (vectors) cv.take<char>(qband_ws(n, p.b, 2 * nev));
+    carve_plan(p, cv);
     return cv.off + 256;
+}
+
+__global__ void f64_to_f32_kernel(size_t count, const double* __restrict__ x, float* __restrict__ y) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        y[e] = (float)x[e];
+}
+__global__ void f32_to_f64_kernel(size_t count, const float* __restrict__ x, double* __restrict__ y) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        y[e] = (double)x[e];
 }
 
 int check_args(int n, const void* A, int lda, int nev, const void* lambda, const void* Zre, const void* Zim) {
@@ -151,8 +156,11 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     const bool vectors = (Zre != nullptr);
     Plan p = make_plan(n, nev, o, vectors);
     if (p.b != 64) return SKEW_ERR_UNSUPPORTED;
-    if (o && o->mode != SKEW_MODE_FP64) return SKEW_ERR_UNSUPPORTED;
-    if (!carve_plan(p, ws, ws_bytes)) return SKEW_ERR_WORKSPACE;
+    if (o && o->mode != SKEW_MODE_FP64 && !p.mixed) return SKEW_ERR_UNSUPPORTED;
+    {
+        Carve cv(ws, ws_bytes);
+        if (!carve_plan(p, cv)) return SKEW_ERR_WORKSPACE;
+    }
     const int maxit = (o && (o->fault & SKEW_FAULT_INVIT_NOCONV)) ? 0 : 5;
 
     mark(0);
@@ -161,7 +169,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     copy_lower_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(n, A, lda, p.W, n, o ? o->check_finite : 0, p.status);
     count_launch();
     mark(1);
-    int rc = band_reduce(st, n, p.W, n, p.b, p.Tfac, p.ws_reduce, p.sz_reduce, p.status);
+    int rc = band_reduce(st, n, p.W, n, p.b, p.Tfac, p.ws_reduce, p.sz_reduce, p.status, p.reduce_prec);
     if (rc) return rc;
     mark(2);
     if (band_pack(st, n, p.b, p.W, n, p.AB, (int)p.ldab) != cudaSuccess) return SKEW_ERR_CUDA;
@@ -179,13 +187,31 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
             return SKEW_ERR_CUDA;
     }
     mark(6);
-    if (vectors && apply_qtrd(st, n, p.b, p.Vtrd, p.tautrd, p.Z, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
+    if (vectors && !p.mixed) {
+        if (apply_qtrd(st, n, p.b, p.Vtrd, p.tautrd, p.Z, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
+    } else if (vectors) {
+        // mixed form: Q_trd in FP32 arithmetic (reflectors from the FP64 chase)
+        const size_t cnt = (size_t)n * 2 * nev;
+        f64_to_f32_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z, p.Z32);
+        count_launch();
+        if (apply_qtrd_f32(st, n, p.b, p.Vtrd, p.tautrd, p.Z32, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
+        f32_to_f64_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z32, p.Z);
+        count_launch();
+    }
     mark(7);
     if (vectors) {
-        rc = apply_qband(st, n, p.b, p.W, n, p.Tfac, p.Z, n, 2 * nev, p.ws_qband, p.sz_qband);
+        rc = p.mixed ? apply_qband_mixed(st, n, p.b, p.W, n, p.Tfac, p.Z, n, 2 * nev, p.ws_qband, p.sz_qband, p.status,
+                                         p.planes)
+                     : apply_qband(st, n, p.b, p.W, n, p.Tfac, p.Z, n, 2 * nev, p.ws_qband, p.sz_qband);
         if (rc) return rc;
     }
     mark(8);
+    if (p.refine) {
+        const int iters = (o && o->refine_iters > 0) ? o->refine_iters : 6;
+        rc = refine(st, n, A, lda, lambda, p.Z, iters, p.ws_refine, p.sz_refine, p.status, &last_refine_info());
+        if (rc) return rc;
+    }
+    mark(9);
     if (vectors) {
         split_z_kernel<<<grid_for((size_t)n * nev), 256, 0, st>>>(n, nev, p.Z, n, Zre, Zim, ldz);
         count_launch();
@@ -194,7 +220,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
         store_status_kernel<<<1, 32, 0, st>>>(p.status, d_info);
         count_launch();
     }
-    mark(9);
+    mark(10);
     return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
 }
 
@@ -203,6 +229,10 @@ std::atomic<long long> g_launches{0};
 }  // namespace
 
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+RefineInfo& last_refine_info() {
+    static RefineInfo info{};
+    return info;
+}
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 }  // namespace sk
@@ -283,14 +313,15 @@ int skew_eig(int n, const double* A, int lda, int nev, double* lambda, double* Z
 }
 
 int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda, double* Z_re, double* Z_im,
-                  void* stream) {
+                  const skew_opts* opts, void* stream) {
     int rc = check_args(n, A, lda, nev, lambda, Z_re, Z_im);
     if (rc) return rc;
     if (n == 0 || nev == 0) return 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool vectors = Z_re != nullptr;
     const size_t nn = (size_t)n;
-    size_t bytes = plan_bytes(n, nev, nullptr, vectors);
+    if (opts && opts->mode == SKEW_MODE_MIXED_INT8) return SKEW_ERR_UNSUPPORTED;
+    size_t bytes = plan_bytes(n, nev, opts, vectors);
     size_t io = align_up(sizeof(double) * nn * n) + align_up(sizeof(double) * nev) +
                 (vectors ? 2 * align_up(sizeof(double) * nn * nev) : 0) + 256;
     char* base = nullptr;
@@ -308,7 +339,7 @@ int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda, doub
     if (cudaMemcpy2DAsync(dA, sizeof(double) * nn, A, sizeof(double) * (size_t)lda, sizeof(double) * nn, nn,
                           cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = SKEW_ERR_CUDA;
-    if (!rc) rc = run_solve(st, n, dA, n, nev, dl, dzr, dzi, n, nullptr, base, bytes - 256, d_info);
+    if (!rc) rc = run_solve(st, n, dA, n, nev, dl, dzr, dzi, n, opts, base, bytes - 256, d_info);
     if (!rc) {
         if (cudaMemcpyAsync(lambda, dl, sizeof(double) * nev, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
         if (vectors) {
@@ -351,6 +382,39 @@ int skew_eig_profile(int n, const double* A, int lda, int nev, double* lambda, d
     return rc ? rc : info;
 }
 
+size_t skew_refine_ws(int n) { return refine_ws(n) + align_up(sizeof(double) * (size_t)n * n) + 256; }
+
+int skew_refine(int n, const double* A, int lda, double* lambda, double* Z_re, double* Z_im, int ldz, int iters,
+                void* ws, size_t ws_bytes, int* d_status, void* stream) {
+    if (n < 2 || n % 2) return -1;
+    if (!A) return -2;
+    if (lda < n) return -3;
+    if (!lambda) return -4;
+    if (!Z_re || !Z_im) return -5;
+    if (ldz < n) return -7;
+    if (iters < 1) return -8;
+    const int m = n / 2;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Carve cv(ws, ws_bytes);
+    double* M = cv.take<double>((size_t)n * n);
+    size_t rb = refine_ws(n);
+    void* rws = cv.take<char>(rb);
+    if (!cv.ok) return SKEW_ERR_WORKSPACE;
+    if (cudaMemcpy2DAsync(M, sizeof(double) * n, Z_re, sizeof(double) * ldz, sizeof(double) * n, m,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpy2DAsync(M + (size_t)n * m, sizeof(double) * n, Z_im, sizeof(double) * ldz, sizeof(double) * n, m,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SKEW_ERR_CUDA;
+    int rc = refine(st, n, A, lda, lambda, M, iters, rws, rb, d_status, &last_refine_info());
+    if (rc) return rc;
+    if (cudaMemcpy2DAsync(Z_re, sizeof(double) * ldz, M, sizeof(double) * n, sizeof(double) * n, m,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpy2DAsync(Z_im, sizeof(double) * ldz, M + (size_t)n * m, sizeof(double) * n, sizeof(double) * n, m,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SKEW_ERR_CUDA;
+    return 0;
+}
+
 size_t skew_metrics_ws(int n, int nev, int ncols) { return metrics_ws(n, nev, ncols > 0 ? ncols : 1); }
 
 int skew_eig_metrics(int n, const double* A, int lda, int nev, const double* lambda, const double* Z_re,
@@ -369,6 +433,24 @@ int skew_eig_metrics(int n, const double* A, int lda, int nev, const double* lam
 }
 
 long long skew_launch_count(void) { return launch_count(); }
+
+int skew_refine_stats(double* emax, int* nclose, int cap) {
+    const RefineInfo& r = last_refine_info();
+    for (int i = 0; i < cap && i < 8; i++) {
+        if (emax) emax[i] = r.emax[i];
+        if (nclose) nclose[i] = r.nclose[i];
+    }
+    return r.iterations;
+}
+
+int skew_refine_trace(double* rnorm, long long* where, int cap) {
+    const RefineInfo& r = last_refine_info();
+    for (int i = 0; i < cap && i < 8; i++) {
+        if (rnorm) rnorm[i] = r.rnorm[i];
+        if (where) where[i] = r.where[i];
+    }
+    return r.iterations;
+}
 
 // ---------------------------------------------------------------- stages
 size_t skew_band_reduce_ws(int n, int b) { return band_reduce_ws(n, b); }
