@@ -67,10 +67,12 @@ typedef enum {
                                       (hi, mid, lo) and the six products of order
                                       <= 2: about FP32 accuracy */
     SKEW_MODE_MIXED_REFINED = 4    /* the reduction's contractions (skew SYMM,
-                                      rank-2k update) as FP64-accurate BF16
-                                      digit-slice products on tcgen05, Q_band in
-                                      BF16x6, Q_trd in FP32, then the FP64
-                                      refinement (n even, nev = n/2) */
+                                      rank-2k update) and Q_band as FP64-accurate
+                                      BF16 digit-slice products on tcgen05, Q_trd
+                                      in FP32, then the FP64 refinement (n even,
+                                      nev = n/2).  Without such a complete basis
+                                      (nev < n/2, odd n) nothing is refined and
+                                      Q_trd runs in FP64 */
 } skew_mode;
 
 /* Fault hooks (host-side injection for tests; never fault the GPU). */
@@ -84,8 +86,11 @@ typedef struct {
     int band;          /* panel width = band width b, a multiple of 64; 0 -> 64 */
     int check_finite;  /* 1: scan A for NaN/Inf first (SKEW_ERR_NONFINITE) */
     int fault;         /* SKEW_FAULT_* bits, tests only; 0 in production */
-    int refine_iters;  /* mixed modes: maximum refinement iterations; 0 -> 6 */
-    int reserved[3];
+    int refine_iters;  /* mixed modes: maximum refinement iterations (1..8); 0 -> 8 */
+    int refine_rho;    /* mixed modes: a pair of eigenvalues gets the first-order
+                          correction when it asks for a rotation below 1/refine_rho,
+                          else it joins a Rayleigh-Ritz cluster; 0 -> 1024 */
+    int reserved[2];
 } skew_opts;
 
 /* Default options (FP64 mode, b = 64). */
@@ -93,6 +98,11 @@ void skew_opts_default(skew_opts* opts);
 
 /* Human-readable text for a return code. Never NULL. */
 const char* skew_eig_strerror(int code);
+
+/* Name of the CUDA error behind the most recent SKEW_ERR_CUDA return of this
+ * process (e.g. "cudaErrorLaunchOutOfResources"), or "none".  Static string;
+ * never NULL. */
+const char* skew_last_cuda_error(void);
 
 /*
  * Full solve, device buffers.  Eigenvalues lambda[0..nev-1] (descending,
@@ -188,15 +198,24 @@ int skew_gemm_bf16x3(int M, int N, int K, double alpha, const double* A,
  * eigenpair refinement of the mixed form:  C = alpha * A B^T + beta * C.
  * Each row of A and of B is scaled by a power of two and cut into 8 digit
  * slices of 7 bits (integers BF16 holds exactly); slice products of equal
- * order are summed exactly in FP32 over K chunks of 128 and folded in
+ * order are summed exactly in FP32 over K groups of 256 and folded in
  * double-float (about 48 bits), so the error is a few units of 2^-48 times
  * the row-max products, independent of cancellation.  Not in the paper.
  * Layouts and argument numbering as skew_gemm_bf16x3 (no lower mode).
+ * skew_gemm_f64acc_ex adds: slices (1..8; the products of slice pairs of
+ * order < slices are kept, error about 2^-7 slices of the row-max products,
+ * -14 otherwise) and lower (1: only the 128 x 64 output tiles that reach or
+ * lie below the diagonal are written, the others are left untouched; -15
+ * otherwise).  Workspace: skew_gemm_f64acc_ws(M, N, K).
  */
 size_t skew_gemm_f64acc_ws(int M, int N, int K);
 int skew_gemm_f64acc(int M, int N, int K, double alpha, const double* A,
                      long long a_rs, long long a_ks, const double* B, long long b_rs,
                      long long b_ks, double beta, double* C, int ldc,
+                     void* ws, size_t ws_bytes, int* d_status, void* stream);
+int skew_gemm_f64acc_ex(int M, int N, int K, double alpha, const double* A,
+                     long long a_rs, long long a_ks, const double* B, long long b_rs,
+                     long long b_ks, double beta, double* C, int ldc, int slices, int lower,
                      void* ws, size_t ws_bytes, int* d_status, void* stream);
 
 /*
@@ -223,10 +242,29 @@ int skew_refine_stats(double* emax, int* nclose, int cap);
  * where[i] = location of the largest correction (row | column << 20 |
  * block << 40, block 0 = Z^H Z part, 1 = conjugate part). */
 int skew_refine_trace(double* rnorm, long long* where, int cap);
+/* Same run: digit slices (1..8; 8 = FP64-accurate) of iteration i's Gram and
+ * projection products (slices[i]) and of its update product (uslices[i]). */
+int skew_refine_slices(int* slices, int* uslices, int cap);
 
 /* Number of CUDA kernels this library has launched in this process
  * (diagnostics; counts host-side launch calls). */
 long long skew_launch_count(void);
+
+/* Kernel timing (diagnostics).  skew_kernel_timing(1) clears the record and
+ * from then on brackets every launch of the tensor-core product kernels with
+ * CUDA events on the stream the launch goes to (adds two event records per
+ * launch, at most 16384 launches are recorded); skew_kernel_timing(0) stops.
+ * Not thread-safe: one solving thread per process while it is on.
+ * skew_kernel_timing_read sums, over the recorded launches of one kind, the
+ * event-measured time (*ms), the algorithmic flops (*flops: 2 M N K per kept
+ * slice or plane product, over the outputs the launch writes) and the launch
+ * count; it waits for the recorded events.  Returns 0, -1 for an unknown
+ * kind, or SKEW_ERR_CUDA. */
+#define SKEW_KERNEL_OZAKI 0 /* FP64-accurate digit-slice product (ozaki_gemm_kernel) */
+#define SKEW_KERNEL_SPLIT 1 /* BF16x3 / BF16x6 split product (umma_gemm_kernel) */
+#define SKEW_KERNEL_OZAKI_REFINE 2 /* ozaki_gemm_kernel inside the refinement (n x n x n) */
+int skew_kernel_timing(int enable);
+int skew_kernel_timing_read(int kind, double* ms, double* flops, long long* launches);
 
 /* ------------------------------------------------------------------------
  * Stage entry points (the steps of Algorithm 1 one at a time; used by the

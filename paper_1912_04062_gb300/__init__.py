@@ -43,6 +43,7 @@ _i, _d, _p, _sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_
 SIGNATURES = {
     "skew_opts_default": (None, [_p]),
     "skew_eig_strerror": (ctypes.c_char_p, [_i]),
+    "skew_last_cuda_error": (ctypes.c_char_p, []),
     "skew_eig": (_i, [_i, _p, _i, _i, _p, _p, _p, _p]),
     "skew_eig_workspace_size": (_sz, [_i, _i, _p]),
     "skew_eig_ex": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
@@ -55,10 +56,15 @@ SIGNATURES = {
     "skew_refine_ws": (_sz, [_i]),
     "skew_refine": (_i, [_i, _p, _i, _p, _p, _p, _i, _i, _p, _sz, _p, _p]),
     "skew_refine_trace": (_i, [_p, _p, _i]),
+    "skew_refine_slices": (_i, [_p, _p, _i]),
+    "skew_kernel_timing": (_i, [_i]),
+    "skew_kernel_timing_read": (_i, [_i, _p, _p, _p]),
     "skew_gemm_bf16x3_ws": (_sz, [_i, _i, _i]),
     "skew_gemm_f64acc_ws": (_sz, [_i, _i, _i]),
     "skew_gemm_f64acc": (_i, [_i, _i, _i, _d, _p, ctypes.c_longlong, ctypes.c_longlong, _p, ctypes.c_longlong,
                               ctypes.c_longlong, _d, _p, _i, _p, _sz, _p, _p]),
+    "skew_gemm_f64acc_ex": (_i, [_i, _i, _i, _d, _p, ctypes.c_longlong, ctypes.c_longlong, _p, ctypes.c_longlong,
+                                 ctypes.c_longlong, _d, _p, _i, _i, _i, _p, _sz, _p, _p]),
     "skew_gemm_bf16x3": (_i, [_i, _i, _i, _d, _p, ctypes.c_longlong, ctypes.c_longlong, _p, ctypes.c_longlong,
                               ctypes.c_longlong, _d, _p, _i, _i, _i, _p, _sz, _p, _p]),
     "skew_band_reduce_ws": (_sz, [_i, _i]),
@@ -79,7 +85,8 @@ SIGNATURES = {
 
 class skew_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("band", ctypes.c_int), ("check_finite", ctypes.c_int),
-                ("fault", ctypes.c_int), ("refine_iters", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("fault", ctypes.c_int), ("refine_iters", ctypes.c_int), ("refine_rho", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -105,6 +112,8 @@ class SkewError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         self.code = code
         msg = lib().skew_eig_strerror(code).decode()
+        if code == SKEW_ERR_CUDA:
+            msg += " [" + lib().skew_last_cuda_error().decode() + "]"
         super().__init__(f"{where}: {msg} (code {code})")
 
 
@@ -158,12 +167,14 @@ class Options:
     check_finite: int = 0
     fault: int = 0
     refine_iters: int = 0
+    refine_rho: int = 0
 
     def c(self):
         o = skew_opts()
         lib().skew_opts_default(ctypes.byref(o))
         o.mode, o.band, o.check_finite, o.fault = self.mode, self.band, self.check_finite, self.fault
         o.refine_iters = self.refine_iters
+        o.refine_rho = self.refine_rho
         return o
 
 
@@ -252,9 +263,11 @@ def gemm_bf16x3(A, B, C=None, alpha=1.0, beta=0.0, lower=False, planes=2, stream
     return C, st
 
 
-def gemm_f64acc(A, B, C=None, alpha=1.0, beta=0.0, stream=None):
+def gemm_f64acc(A, B, C=None, alpha=1.0, beta=0.0, slices=8, lower=False, stream=None):
     """C = alpha * A @ B.T + beta * C to FP64 accuracy on the BF16 tensor cores
-    (exact digit slices).  A: M x K, B: N x K float64 CUDA tensors."""
+    (exact digit slices).  A: M x K, B: N x K float64 CUDA tensors.  slices < 8
+    keeps fewer digit-slice products (error about 2^-7 slices); lower writes
+    only the output tiles on or below the diagonal."""
     M, K = A.shape
     N = B.shape[0]
     if C is None:
@@ -262,8 +275,14 @@ def gemm_f64acc(A, B, C=None, alpha=1.0, beta=0.0, stream=None):
         C.zero_()
     ws = _ws(lib().skew_gemm_f64acc_ws(M, N, K), A.device)
     st = _status(A.device)
-    code = lib().skew_gemm_f64acc(M, N, K, alpha, _ptr(A), A.stride(0), A.stride(1), _ptr(B), B.stride(0),
-                                  B.stride(1), beta, _ptr(C), _ld(C), _ptr(ws), ws.numel(), _ptr(st), _stream(stream))
+    if slices == 8 and not lower:
+        code = lib().skew_gemm_f64acc(M, N, K, alpha, _ptr(A), A.stride(0), A.stride(1), _ptr(B), B.stride(0),
+                                      B.stride(1), beta, _ptr(C), _ld(C), _ptr(ws), ws.numel(), _ptr(st),
+                                      _stream(stream))
+    else:
+        code = lib().skew_gemm_f64acc_ex(M, N, K, alpha, _ptr(A), A.stride(0), A.stride(1), _ptr(B), B.stride(0),
+                                         B.stride(1), beta, _ptr(C), _ld(C), int(slices), 1 if lower else 0,
+                                         _ptr(ws), ws.numel(), _ptr(st), _stream(stream))
     _check(code, "skew_gemm_f64acc")
     return C, st
 
@@ -295,6 +314,36 @@ def refine_trace():
     it = lib().skew_refine_trace(rn, wh, 8)
     locs = [(int(w) & 0xFFFFF, (int(w) >> 20) & 0xFFFFF, (int(w) >> 40) & 1) for w in wh[:it]]
     return [float(x) for x in rn[:it]], locs
+
+
+def refine_slices():
+    """([Gram/projection slices per iteration], [update slices per iteration])
+    of the most recent refinement in this process (8 = FP64-accurate)."""
+    sl = (ctypes.c_int * 8)()
+    su = (ctypes.c_int * 8)()
+    it = lib().skew_refine_slices(sl, su, 8)
+    return [int(x) for x in sl[:it]], [int(x) for x in su[:it]]
+
+
+SKEW_KERNEL_OZAKI = 0
+SKEW_KERNEL_SPLIT = 1
+SKEW_KERNEL_OZAKI_REFINE = 2
+
+
+def kernel_timing(enable: bool) -> None:
+    """Switch per-launch event timing of the tensor-core product kernels on
+    (clearing the record) or off."""
+    lib().skew_kernel_timing(1 if enable else 0)
+
+
+def kernel_timing_read(kind: int):
+    """(total ms, algorithmic flops, launches) recorded for one kernel kind."""
+    ms = ctypes.c_double()
+    fl = ctypes.c_double()
+    k = ctypes.c_longlong()
+    code = lib().skew_kernel_timing_read(kind, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(k))
+    _check(code, "skew_kernel_timing_read")
+    return ms.value, fl.value, k.value
 
 
 def launch_count() -> int:

@@ -271,12 +271,25 @@ int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw, const d
     return 0;
 }
 
-// Mixed form: Q_band with the two contractions on the tensor cores (BF16x3):
+// Mixed form: Q_band with the two contractions on the tensor cores:
 // Y^T = Z[o:, :]^T V_p, then Z[o:, :] -= (V_p T_p) Y, V_p T_p in FP64.
+// planes: 2 / 3 (BF16x3 / BF16x6 split products) or REDUCE_F64ACC
+// (FP64-accurate digit-slice products)
+static size_t qband_gemm_ws(int n, int b, int k, int planes) {
+    size_t g1, g2;
+    if (planes == REDUCE_F64ACC) {
+        g1 = ozaki_gemm_ws(k, b, n);
+        g2 = ozaki_gemm_ws(n, k, b);
+    } else {
+        g1 = split_gemm_ws(k, b, n, planes);
+        g2 = split_gemm_ws(n, k, b, planes);
+    }
+    return g1 > g2 ? g1 : g2;
+}
+
 size_t qband_mixed_ws(int n, int b, int k, int planes) {
-    size_t g1 = split_gemm_ws(k, b, n, planes), g2 = split_gemm_ws(n, k, b, planes);
     return align_up(sizeof(double) * (size_t)n * b) * 2 + align_up(sizeof(double) * (size_t)k * b) +
-           (g1 > g2 ? g1 : g2) + 256;
+           qband_gemm_ws(n, b, k, planes) + 256;
 }
 
 int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz,
@@ -287,8 +300,7 @@ int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, c
     double* V = cv.take<double>((size_t)n * b);
     double* VT = cv.take<double>((size_t)n * b);
     double* Yt = cv.take<double>((size_t)k * b);
-    size_t g1 = split_gemm_ws(k, b, n, planes), g2 = split_gemm_ws(n, k, b, planes);
-    size_t gsz = g1 > g2 ? g1 : g2;
+    const size_t gsz = qband_gemm_ws(n, b, k, planes);
     void* gws = cv.take<char>(gsz);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
     for (int p = P - 1; p >= 0; p--) {
@@ -297,9 +309,17 @@ int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, c
         double* Zo = Z + o;
         if (panel_v(st, n, b, p, W, ldw, V, n) != cudaSuccess) return SKEW_ERR_CUDA;
         if (gemm(st, false, false, m, b, b, 1.0, V, n, Tp, b, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
-        int rc = split_gemm(st, k, b, m, 1.0, Zo, ldz, 1, 0, V, n, 1, 0.0, Yt, k, 0, gws, gsz, status, planes);
-        if (rc) return rc;
-        rc = split_gemm(st, m, k, b, -1.0, VT, 1, n, 0, Yt, 1, k, 1.0, Zo, ldz, 0, gws, gsz, status, planes);
+        // Yt = Z_o^T V (k x b), then Z_o -= (V T) Yt^T
+        int rc;
+        if (planes == REDUCE_F64ACC) {
+            rc = ozaki_gemm(st, k, b, m, 1.0, Zo, ldz, 1, 1.0, V, n, 1, 1.0, 0.0, Yt, k, gws, gsz, status);
+            if (rc) return rc;
+            rc = ozaki_gemm(st, m, k, b, -1.0, VT, 1, n, 1.0, Yt, 1, k, 1.0, 1.0, Zo, ldz, gws, gsz, status);
+        } else {
+            rc = split_gemm(st, k, b, m, 1.0, Zo, ldz, 1, 0, V, n, 1, 0.0, Yt, k, 0, gws, gsz, status, planes);
+            if (rc) return rc;
+            rc = split_gemm(st, m, k, b, -1.0, VT, 1, n, 0, Yt, 1, k, 1.0, Zo, ldz, 0, gws, gsz, status, planes);
+        }
         if (rc) return rc;
     }
     return 0;

@@ -331,9 +331,9 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         concat_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, w.V, w.Y, n, w.X2, w.Y2);
         count_launch();
         if (planes == REDUCE_F64ACC) {
-            // all tiles (the upper triangle of W is never read); diagonal ~0
+            // tiles on or below the diagonal (the upper triangle of W is never read)
             int rc = ozaki_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 1.0, w.Y2, 1, n, 1.0, 1.0, A22, ldw, gws, gsz,
-                                d_status, 0);
+                                d_status, 0, 8, 1);
             if (rc) return rc;
         } else if (mixed) {
             int rc = split_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 0, w.Y2, 1, n, 1.0, A22, ldw, 1, gws, gsz, d_status,

@@ -93,10 +93,13 @@ int split_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double*
 // B[j,k] = B[j*b_rs + k*b_ks], C column-major.
 size_t ozaki_gemm_ws(int M, int N, int K);
 // a_skew: A is the skew matrix of the strict lower triangle stored column-major
-// with leading dimension a_ks (a_rs unused).
+// with leading dimension a_ks (a_rs unused).  slices (1..8): digit slices kept,
+// accuracy about 2^-7 slices relative to |a_r|max |b_c|max per term.  lower:
+// only 128 x 64 tiles that reach the diagonal or lie below it are written.
 int ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, long long a_rs, long long a_ks,
                double sa, const double* B, long long b_rs, long long b_ks, double sb, double beta, double* C,
-               long long ldc, void* ws, size_t ws_bytes, int* status, int a_skew = 0);
+               long long ldc, void* ws, size_t ws_bytes, int* status, int a_skew = 0, int slices = 8,
+               int lower = 0);
 
 // ---- refine.cu (FP64 eigenpair refinement, mixed form) ---------------------------
 struct RefineInfo {
@@ -105,11 +108,15 @@ struct RefineInfo {
     int nclose[8];    // pairs not separated (E_ij = R_ij / 2), per iteration
     double rnorm[8];  // ||R||_F over the Z^H Z block before each update
     long long where[8];  // location of the largest correction: i | j << 20 | block << 40
+    int slices[8];       // digit slices of the Gram and projection products
+    int uslices[8];      // digit slices of the update product
 };
 size_t refine_ws(int n);
 // M = [X Y] (n x n, ld n) and lambda (n/2) refined in place; n even.
+// rho: separation factor of the first-order correction (pairs whose
+// correction would exceed 1/rho go to Rayleigh-Ritz clusters)
 int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, double* M, int maxit, void* ws,
-           size_t ws_bytes, int* status, RefineInfo* info);
+           size_t ws_bytes, int* status, RefineInfo* info, double rho = 1024.0);
 RefineInfo& last_refine_info();
 
 // ---- metrics.cu -------------------------------------------------------------
@@ -121,6 +128,22 @@ int metrics(cudaStream_t st, int n, const double* A, int lda, int nev, const dou
 // Host-side count of kernel launches issued by this library (diagnostics).
 void count_launch(int k = 1);
 long long launch_count();
+// Records the name of a failed CUDA call (for skew_last_cuda_error) and
+// returns SKEW_ERR_CUDA; cuda_ok(e) is cuda_fail(e) unless e == cudaSuccess.
+int cuda_fail(cudaError_t e);
+inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? 0 : cuda_fail(e); }
+// Kernel timing (diagnostics): when switched on, kt_begin / kt_end bracket a
+// launch with CUDA events on its stream and record its algorithmic flops.
+enum { KT_OZAKI = 0, KT_SPLIT = 1, KT_OZAKI_REFINE = 2, KT_KINDS = 3 };
+// kind recorded for ozaki_gemm launches (the refinement sets KT_OZAKI_REFINE
+// for its n x n x n products while it runs)
+extern int g_kt_ozaki_kind;
+int kt_begin(cudaStream_t st);
+void kt_end(cudaStream_t st, int slot, int kind, double flops);
+// elements (r, c) of an M x N result with c <= r (the lower triangle)
+inline double lower_count(double M, double N) {
+    return N <= M ? N * (N + 1) / 2 + (M - N) * N : M * (M + 1) / 2;
+}
 int device_sms();
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 

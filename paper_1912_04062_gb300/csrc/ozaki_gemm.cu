@@ -13,18 +13,25 @@
 // x = 2^e_r * sum_i d_i 2^-7(i+1) + O(2^(e_r - 56)).
 //
 // Product.  C[r][c] = 2^(e_r + f_c - 14) * sum_L 2^-7L T_L[r][c] with
-// T_L = sum_{i+j=L} D_i E_j^T.  Levels L = 0..7 are kept (36 slice pairs);
-// the dropped ones are below 2^-63 of |a_r|max |b_c|max per term.  Over a K
-// chunk of 128 each T_L is a sum of at most 8 * 128 products of size <= 2^14,
-// below 2^24: FP32 accumulation in TMEM is exact.  Each chunk's eight level
-// accumulators (8 x 64 TMEM columns) are folded into a double-float (two FP32)
-// running sum per output, which carries about 48 bits.
+// T_L = sum_{i+j=L} D_i E_j^T over the kept levels L < s (s = 8: 36 slice
+// pairs, the dropped ones below 2^-63 of |a_r|max |b_c|max per term; fewer
+// slices give a cheaper product accurate to about 2^-7s).  The level sums are
+// taken over K groups of 256: level 0 is a sum of 256 products of size
+// <= 2^14, level L >= 1 of 256 (L + 3) 2^12-sized terms (two pairs with a
+// leading digit, |d_0| <= 128), both below 2^24, so FP32 accumulation in TMEM
+// is exact.  After each group the level accumulators (s x 64 TMEM columns)
+// are folded into a double-float (two FP32) running sum per output, which
+// carries about 48 bits.
 //
-// Kernel: 128 x 64 output tile per CTA, 192 threads: warps 0-3 drain TMEM
-// (lanes 32w.. = rows) and accumulate; warp 4 issues TMA loads (all eight B
-// digit slices of the chunk stay resident, A slices stream through two
-// stages); warp 5 issues the MMAs.  TMEM holds one chunk, so the MMAs of chunk
-// c+1 start once the epilogue has drained chunk c.
+// Kernel: 128 x 64 output tile per CTA, 320 threads: warps 0-7 drain TMEM
+// (warp w: lanes 32 (w & 3).. = rows, columns 32 (w >> 2)..) and accumulate;
+// warp 8 issues TMA loads (the B digit
+// slices of a 128-wide K chunk stay resident, A slices stream through two
+// stages); warp 9 issues the MMAs.  TMEM holds one group of two chunks, so the
+// MMAs of the next group start once the epilogue has drained the last one.
+// With `lower` set, tiles wholly above the diagonal (every column index above
+// every row index) are skipped: for symmetric or skew results whose upper
+// triangle is not read.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -43,19 +50,25 @@ namespace {
 
 constexpr int OM = 128;      // tile rows
 constexpr int ON = 64;       // tile columns
-constexpr int OKC = 128;     // K per chunk (two 64-wide swizzle atoms)
+constexpr int OKC = 128;     // K per chunk (two 64-wide swizzle atoms; the last chunk may hold one)
+constexpr int OKA = 64;      // K per swizzle atom; K is padded to a multiple of it
 constexpr int SL = 8;        // digit slices per operand
-constexpr int OT = 192;      // threads per CTA
+constexpr int OT = 320;      // threads per CTA: 8 epilogue warps, TMA warp, MMA warp
+constexpr int OEPI = 256;    // epilogue threads
 
 struct OzParams {
     int M, N, nchunks;
+    int katoms;              // 64-wide K atoms in all (the last chunk holds one when odd)
     int Mp, Np;              // padded row counts of the slice planes
+    int mt, nt;              // output tiles along M and N
     const int* ea;           // row exponents of A (M)
     const int* eb;           // row exponents of B (N)
     double alpha, beta;
     double* C;
     long long ldc;
     int* status;
+    int s;                   // digit slices kept (levels L < s)
+    int lower;               // skip tiles above the diagonal
 };
 
 struct OzSmem {
@@ -114,7 +127,9 @@ SK_DEV void df_add_df(float& hi, float& lo, float xh, float xl) {
     hi = h;
 }
 
-__global__ void __launch_bounds__(OT, 1)
+// 10 warps: a sub-partition hosts up to 3 of them in its 16K registers, so at
+// most 168 registers per thread
+__global__ void __maxnreg__(168)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams p) {
     extern __shared__ unsigned char oz_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) &
@@ -131,8 +146,17 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 8);
     __shared__ int s_bi, s_bc, s_ai, s_ac;  // B chunks / A stages issued and consumed
 
-    const int m0 = blockIdx.x * OM, n0 = blockIdx.y * ON;
+    // tile order: groups of GM tile rows, column-major inside a group, so that
+    // the CTAs resident at one time share few distinct A and B rows (one wave
+    // of 152 covers about 8 x 19 tiles, whose operands L2 holds as the CTAs
+    // step through K together)
+    constexpr int GM = 8;
+    const int t = blockIdx.x, grp_size = GM * p.nt, first_m = (t / grp_size) * GM;
+    const int gm = (p.mt - first_m) < GM ? (p.mt - first_m) : GM;
+    const int m0 = (first_m + (t % grp_size) % gm) * OM, n0 = ((t % grp_size) / gm) * ON;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (p.lower && n0 >= m0 + OM) return;  // whole CTA, before any barrier or TMEM use
+    const int S = p.s;
 
     if (threadIdx.x == 0) {
         mbar_init(bfull, 1);
@@ -142,14 +166,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         mbar_init(&aempty[0], 1);
         mbar_init(&aempty[1], 1);
         mbar_init(tfull, 1);
-        mbar_init(tempty, 128);
+        mbar_init(tempty, OEPI);
         fence_mbar_init();
         fence_proxy_async_smem();
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
         s_bi = s_bc = s_ai = s_ac = 0;
     }
-    if (warp == 4) {
+    if (warp == 8) {
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     }
@@ -159,23 +183,24 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     const uint32_t tmem = *tmem_slot;
     const int nch = p.nchunks;
 
-    if (warp == 4) {
+    if (warp == 8) {
         if (lane == 0) {
             // ---- TMA producer
             bool ok = true;
             int bi = 0, ai = 0;
             for (int c = 0; c < nch && ok; c++) {
                 if (!(ok = mbar_wait(bfree, ((uint32_t)c & 1u) ^ 1u, p.status))) break;
-                mbar_arrive_expect_tx(bfull, OzSmem::B_BYTES);
-                for (int j = 0; j < SL; j++)
-                    for (int a = 0; a < 2; a++)
+                const int na = min(2, p.katoms - 2 * c);  // atoms in this chunk
+                mbar_arrive_expect_tx(bfull, (uint32_t)(S * na) * OzSmem::B_ATOM);
+                for (int j = 0; j < S; j++)
+                    for (int a = 0; a < na; a++)
                         tma_load_2d(sB + (j * 2 + a) * OzSmem::B_ATOM, &tmB, bfull, c * OKC + a * 64, j * p.Np + n0);
                 bi++;
-                for (int i = 0; i < SL; i++) {
-                    const int it = c * SL + i, s = it & 1;
+                for (int i = 0; i < S; i++) {
+                    const int it = c * S + i, s = it & 1;
                     if (!(ok = mbar_wait(&aempty[s], ((uint32_t)(it >> 1) & 1u) ^ 1u, p.status))) break;
-                    mbar_arrive_expect_tx(&afull[s], OzSmem::A_STAGE);
-                    for (int a = 0; a < 2; a++)
+                    mbar_arrive_expect_tx(&afull[s], (uint32_t)na * OzSmem::A_ATOM);
+                    for (int a = 0; a < na; a++)
                         tma_load_2d(sA + s * OzSmem::A_STAGE + a * OzSmem::A_ATOM, &tmA, &afull[s],
                                     c * OKC + a * 64, i * p.Mp + m0);
                     ai++;
@@ -184,66 +209,91 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             s_bi = bi;
             s_ai = ai;
         }
-    } else if (warp == 5) {
+    } else if (warp == 9) {
         if (lane == 0) {
             // ---- MMA issuer: level L accumulates in TMEM columns [64 L, 64 L + 64)
             constexpr uint32_t idesc = umma_idesc_bf16(OM, ON);
             bool ok = true;
             int bc = 0, ac = 0;
             for (int c = 0; c < nch && ok; c++) {
-                if (!(ok = mbar_wait(tempty, ((uint32_t)c & 1u) ^ 1u, p.status))) break;
-                tc_fence_after();
+                const bool first = (c & 1) == 0;  // first chunk of a 256-wide K group
+                if (first) {
+                    if (!(ok = mbar_wait(tempty, ((uint32_t)(c >> 1) & 1u) ^ 1u, p.status))) break;
+                    tc_fence_after();
+                }
                 if (!(ok = mbar_wait(bfull, (uint32_t)c & 1u, p.status))) break;
                 bc++;
                 tc_fence_after();
-                for (int i = 0; i < SL; i++) {
-                    const int it = c * SL + i, s = it & 1;
+                const int nkk = 4 * min(2, p.katoms - 2 * c);  // 16-wide K steps in this chunk
+                for (int i = 0; i < S; i++) {
+                    const int it = c * S + i, s = it & 1;
                     if (!(ok = mbar_wait(&afull[s], (uint32_t)(it >> 1) & 1u, p.status))) break;
                     ac++;
                     tc_fence_after();
-                    for (int j = 0; i + j < SL; j++) {
+                    for (int j = 0; i + j < S; j++) {
                         const uint32_t dcol = tmem + (uint32_t)((i + j) * ON);
 #pragma unroll
                         for (int kk = 0; kk < OKC / 16; kk++) {
+                            if (kk >= nkk) break;
                             const int a = kk >> 2, k4 = kk & 3;
                             const uint64_t ad =
                                 umma_desc_sw128(smem_u32(sA + s * OzSmem::A_STAGE + a * OzSmem::A_ATOM)) + 2 * k4;
                             const uint64_t bd = umma_desc_sw128(smem_u32(sB + (j * 2 + a) * OzSmem::B_ATOM)) + 2 * k4;
-                            // level L is first written by the pair (0, L) at kk = 0
-                            umma_bf16(dcol, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                            // level L is first written by the pair (0, L) at kk = 0 of a group
+                            umma_bf16(dcol, ad, bd, idesc, (!first || i > 0 || kk > 0) ? 1u : 0u);
                         }
                     }
                     umma_commit(&aempty[s]);
                 }
                 umma_commit(bfree);
-                umma_commit(tfull);
+                if (!first || c == nch - 1) umma_commit(tfull);
             }
             s_bc = bc;
             s_ac = ac;
         }
     } else {
-        // ---- epilogue warps 0-3: row m0 + 32 w + lane
-        float ah[ON], al[ON];
+        // ---- epilogue warps 0-7: row m0 + 32 (w & 3) + lane, columns n0 + 32 (w >> 2) + [0, 32)
+        constexpr int EC = ON / 2;
+        const int quad = warp & 3, half = warp >> 2;
+        float ah[EC], al[EC];
 #pragma unroll
-        for (int q = 0; q < ON; q++) { ah[q] = 0.f; al[q] = 0.f; }
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int q = 0; q < EC; q++) { ah[q] = 0.f; al[q] = 0.f; }
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * EC);
         bool ok = true;
-        for (int c = 0; c < nch; c++) {
-            ok = mbar_wait(tfull, (uint32_t)c & 1u, p.status);
+        const int ngroups = (nch + 1) / 2;
+        for (int grp = 0; grp < ngroups; grp++) {
+            ok = mbar_wait(tfull, (uint32_t)grp & 1u, p.status);
             tc_fence_after();
             if (!ok) break;
 #pragma unroll
-            for (int g = 0; g < ON / 16; g++) {
+            for (int g = 0; g < EC / 16; g++) {
                 float sh[16], sl[16];
 #pragma unroll
                 for (int q = 0; q < 16; q++) { sh[q] = 0.f; sl[q] = 0.f; }
+                // levels from the smallest up, three TMEM loads in flight per wait
 #pragma unroll 1
-                for (int L = SL - 1; L >= 0; L--) {
-                    float v[16];
-                    tmem_ld16(lane_base + (uint32_t)(L * ON + g * 16), v);
-                    const float sc = __int_as_float((127 - 7 * L) << 23);  // 2^-7L
+                for (int top = S - 1; top >= 0; top -= 3) {
+                    uint32_t v0[16], v1[16], v2[16];
+                    const uint32_t col = lane_base + (uint32_t)(g * 16);
+                    tmem_ld16_async(col + (uint32_t)(top * ON), v0);
+                    if (top >= 1) tmem_ld16_async(col + (uint32_t)((top - 1) * ON), v1);
+                    if (top >= 2) tmem_ld16_async(col + (uint32_t)((top - 2) * ON), v2);
+                    tmem_wait_ld16(v0);
+                    tmem_after_wait16(v1);
+                    tmem_after_wait16(v2);
+                    float sc = __int_as_float((127 - 7 * top) << 23);  // 2^-7L
 #pragma unroll
-                    for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], v[q] * sc);
+                    for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], __uint_as_float(v0[q]) * sc);
+                    if (top >= 1) {
+                        sc *= 128.f;
+#pragma unroll
+                        for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], __uint_as_float(v1[q]) * sc);
+                    }
+                    if (top >= 2) {
+                        sc *= 128.f;
+#pragma unroll
+                        for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], __uint_as_float(v2[q]) * sc);
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < 16; q++) df_add_df(ah[g * 16 + q], al[g * 16 + q], sh[q], sl[q]);
@@ -251,12 +301,12 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             tc_fence_before();
             mbar_arrive(tempty);
         }
-        const int row = m0 + warp * 32 + lane;
+        const int row = m0 + quad * 32 + lane;
         if (ok && row < p.M) {
             const int er = p.ea[row];
 #pragma unroll
-            for (int q = 0; q < ON; q++) {
-                const int col = n0 + q;
+            for (int q = 0; q < EC; q++) {
+                const int col = n0 + half * EC + q;
                 if (col >= p.N) continue;
                 const double val = ldexp((double)ah[q] + (double)al[q], er + p.eb[col] - 14);
                 double* dst = p.C + (long long)col * p.ldc + row;
@@ -268,12 +318,12 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     __syncthreads();
     // after a timeout, let loads that were issued but never consumed land
     // before the shared memory is released (capped as well)
-    if (threadIdx.x == 128) {
+    if (threadIdx.x == 256) {
         for (int c = s_bc; c < s_bi; c++) mbar_wait(bfull, (uint32_t)c & 1u, p.status, 1u << 16);
         for (int it = s_ac; it < s_ai; it++) mbar_wait(&afull[it & 1], (uint32_t)(it >> 1) & 1u, p.status, 1u << 16);
     }
     __syncthreads();
-    if (warp == 4) tmem_dealloc(tmem, 512);
+    if (warp == 8) tmem_dealloc(tmem, 512);
 }
 
 // Row exponents when rows are contiguous in memory (sr == 1): one thread per
@@ -442,7 +492,7 @@ inline int gridn(long long total) {
 }  // namespace
 
 size_t ozaki_gemm_ws(int M, int N, int K) {
-    const long long Kp = rup(K > 0 ? K : 1, OKC), Mp = rup(M > 0 ? M : 1, OM), Np = rup(N > 0 ? N : 1, ON);
+    const long long Kp = rup(K > 0 ? K : 1, OKA), Mp = rup(M > 0 ? M : 1, OM), Np = rup(N > 0 ? N : 1, ON);
     return align_up((size_t)(SL * Mp * Kp * 2)) + align_up((size_t)(SL * Np * Kp * 2)) + align_up(sizeof(int) * Mp) +
            align_up(sizeof(int) * Np) + align_up(sizeof(unsigned long long) * Mp) + 256;
 }
@@ -450,10 +500,10 @@ size_t ozaki_gemm_ws(int M, int N, int K) {
 // C = alpha * (sa A)(sb B)^T + beta C, A[i,k] = A[i*a_rs + k*a_ks], B[j,k] = B[j*b_rs + k*b_ks].
 int ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, long long a_rs, long long a_ks,
                double sa, const double* B, long long b_rs, long long b_ks, double sb, double beta, double* C,
-               long long ldc, void* ws, size_t ws_bytes, int* status, int a_skew) {
+               long long ldc, void* ws, size_t ws_bytes, int* status, int a_skew, int slices, int lower) {
     if (M <= 0 || N <= 0) return 0;
-    if (K <= 0) return SKEW_ERR_UNSUPPORTED;
-    const long long Kp = rup(K, OKC), Mp = rup(M, OM), Np = rup(N, ON);
+    if (K <= 0 || slices < 1 || slices > SL) return SKEW_ERR_UNSUPPORTED;
+    const long long Kp = rup(K, OKA), Mp = rup(M, OM), Np = rup(N, ON);
     Carve cv(ws, ws_bytes);
     __nv_bfloat16* Ad = cv.take<__nv_bfloat16>((size_t)(SL * Mp * Kp));
     __nv_bfloat16* Bd = cv.take<__nv_bfloat16>((size_t)(SL * Np * Kp));
@@ -495,7 +545,8 @@ int ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double*
     OzParams p{};
     p.M = M;
     p.N = N;
-    p.nchunks = (int)(Kp / OKC);
+    p.katoms = (int)(Kp / OKA);
+    p.nchunks = (p.katoms + 1) / 2;
     p.Mp = (int)Mp;
     p.Np = (int)Np;
     p.ea = ea;
@@ -505,11 +556,20 @@ int ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double*
     p.C = C;
     p.ldc = ldc;
     p.status = status;
+    p.s = slices;
+    p.lower = lower;
     const size_t smem = OzSmem::bytes();
     cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    ozaki_gemm_kernel<<<dim3((unsigned)(Mp / OM), (unsigned)(Np / ON)), OT, smem, st>>>(ta, tb, p);
+    p.mt = (int)(Mp / OM);
+    p.nt = (int)(Np / ON);
+    // algorithmic work: the kept slice pairs over the outputs written
+    const double pairs = slices * (slices + 1) / 2.0;
+    const double outs = lower ? lower_count(M, N) : (double)M * N;
+    const int kt = kt_begin(st);
+    ozaki_gemm_kernel<<<(unsigned)(p.mt * p.nt), OT, smem, st>>>(ta, tb, p);
+    kt_end(st, kt, g_kt_ozaki_kind, 2.0 * pairs * outs * K);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
+    return cuda_ok(cudaGetLastError());
 }
 
 }  // namespace sk
@@ -524,5 +584,18 @@ extern "C" int skew_gemm_f64acc(int M, int N, int K, double alpha, const double*
     if (K < 1) return -3;
     if (ldc < (M > 1 ? M : 1)) return -13;
     return sk::ozaki_gemm(static_cast<cudaStream_t>(stream), M, N, K, alpha, A, a_rs, a_ks, 1.0, B, b_rs, b_ks, 1.0,
-                          beta, C, ldc, ws, ws_bytes, d_status, 0);
+                          beta, C, ldc, ws, ws_bytes, d_status, 0, 8, 0);
+}
+
+extern "C" int skew_gemm_f64acc_ex(int M, int N, int K, double alpha, const double* A, long long a_rs, long long a_ks,
+                                   const double* B, long long b_rs, long long b_ks, double beta, double* C, int ldc,
+                                   int slices, int lower, void* ws, size_t ws_bytes, int* d_status, void* stream) {
+    if (M < 0) return -1;
+    if (N < 0) return -2;
+    if (K < 1) return -3;
+    if (ldc < (M > 1 ? M : 1)) return -13;
+    if (slices < 1 || slices > 8) return -14;
+    if (lower != 0 && lower != 1) return -15;
+    return sk::ozaki_gemm(static_cast<cudaStream_t>(stream), M, N, K, alpha, A, a_rs, a_ks, 1.0, B, b_rs, b_ks, 1.0,
+                          beta, C, ldc, ws, ws_bytes, d_status, 0, slices, lower);
 }

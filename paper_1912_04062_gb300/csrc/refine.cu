@@ -21,7 +21,8 @@
 // and the update is one real product M <- M + M U,
 //   U = [[Er + Fr, Ei + Fi], [Fi - Ei, Er - Fr]]   (E11 = Er + i Ei, E21 = Fr + i Fi).
 // A pair counts as separated when the first-order rotation it asks for is
-// small: |lambda~_j - lambda~_i| > max(tau, 64 (|S_ij| + |lambda~_j| |R_ij|)).
+// small: |lambda~_j - lambda~_i| > max(tau, rho (|S_ij| + |lambda~_j| |R_ij|)),
+// rho = 1024 by default.
 // Runs of neighbours that are not separated form clusters; each cluster gets
 // a Rayleigh-Ritz rotation from its FP64-accurate Gram and projection blocks
 // (after Ogita and Aishima's treatment of clustered eigenvalues, 2019), and
@@ -64,23 +65,13 @@ __global__ void skew_full_kernel(int n, const double* __restrict__ A, int lda, d
     }
 }
 
-// lambda~_i = Sg_ii / G_ii = (T_XY - T_YX)_ii / (XX + YY)_ii
-__global__ void refine_lambda_kernel(int m, int n, const double* __restrict__ Wg, const double* __restrict__ T,
-                                     double* __restrict__ lt) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const long long ld = n;
-    const double g = Wg[i + i * ld] + Wg[(m + i) + (m + i) * ld];
-    const double s = T[i + (m + i) * ld] - T[(m + i) + i * ld];  // 2 x skew part of T_XY(i, i)
-    lt[i] = s / g;
-}
-
 struct RefineScalars {
     unsigned long long emax_bits;  // max |E| over off-diagonal separated pairs (as double bits)
     unsigned int nclose;           // pairs neither separated nor inside one cluster
     double lmax;
     double rnorm2;                 // sum |R~_ij|^2 over the E11 block (orthogonality before the update)
-    unsigned long long where;      // (max |E| bits << 32 truncated) packed location of the max: i | j << 20 | blk << 40
+    unsigned long long where;      // packed location of the max: i | j << 20 | blk << 40
+    unsigned long long umax_bits;  // max |U_ij| of the update (as double bits)
 };
 
 constexpr int KC = 16;  // largest cluster handled by Rayleigh-Ritz
@@ -94,20 +85,30 @@ SK_DEV cplx cadd(cplx a, cplx b) { return {a.r + b.r, a.i + b.i}; }
 SK_DEV cplx csub(cplx a, cplx b) { return {a.r - b.r, a.i - b.i}; }
 SK_DEV cplx cscale(cplx a, double s) { return {a.r * s, a.i * s}; }
 
-// Blocks of Zh^H Zh and Zh^H H Zh at (i, j) (see the header comment), from
-// the exactly symmetric part of Wg and the exactly skew part of T: the
-// products carry rounding errors that break the symmetry slightly, and the
-// correction's orthogonality identity E_ij + conj(E_ji) = R_ij holds only for
-// an exactly Hermitian S and G.
+// Blocks of Zh^H Zh and Zh^H H Zh at (i, j) (see the header comment).  Wg
+// and T are formed on their lower triangle only and read as exactly symmetric
+// and exactly skew: the correction's orthogonality identity
+// E_ij + conj(E_ji) = R_ij holds only for an exactly Hermitian S and G.
 struct Blocks {
     cplx G, F, Sg, Sf;
 };
 SK_DEV double wsym(const double* __restrict__ Wg, long long ld, int a, int b) {
-    return 0.5 * (Wg[a + b * ld] + Wg[b + a * ld]);
+    return a >= b ? Wg[a + b * ld] : Wg[b + a * ld];
 }
 SK_DEV double tskew(const double* __restrict__ T, long long ld, int a, int b) {
-    return 0.5 * (T[a + b * ld] - T[b + a * ld]);
+    return a > b ? T[a + b * ld] : (a < b ? -T[b + a * ld] : 0.0);
 }
+// lambda~_i = Sg_ii / G_ii = (T_XY - T_YX)_ii / (XX + YY)_ii
+__global__ void refine_lambda_kernel(int m, int n, const double* __restrict__ Wg, const double* __restrict__ T,
+                                     double* __restrict__ lt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const long long ld = n;
+    const double g = Wg[i + i * ld] + Wg[(m + i) + (m + i) * ld];
+    const double s = 2.0 * tskew(T, ld, i, m + i);  // (T_XY - T_YX)(i, i)
+    lt[i] = s / g;
+}
+
 SK_DEV Blocks blocks(int i, int j, int m, long long ld, const double* __restrict__ Wg, const double* __restrict__ T) {
     const double XX = wsym(Wg, ld, i, j), YY = wsym(Wg, ld, m + i, m + j);
     const double XY = wsym(Wg, ld, i, m + j), YX = wsym(Wg, ld, m + i, j);
@@ -122,24 +123,23 @@ SK_DEV Blocks blocks(int i, int j, int m, long long ld, const double* __restrict
 }
 
 // first-order rotation the pair (i, j) asks for is small enough for the
-// correction formula: |l_j - l_i| > max(tau, RHO (|Sg_ij| + |l_j| |R_ij|))
-constexpr double RHO = 64.0;
-SK_DEV bool separated(double li, double lj, cplx Sg, cplx R, double tau) {
-    const double need = RHO * (hypot(Sg.r, Sg.i) + fabs(lj) * hypot(R.r, R.i));
+// correction formula: |l_j - l_i| > max(tau, rho (|Sg_ij| + |l_j| |R_ij|))
+SK_DEV bool separated(double li, double lj, cplx Sg, cplx R, double tau, double rho) {
+    const double need = rho * (hypot(Sg.r, Sg.i) + fabs(lj) * hypot(R.r, R.i));
     return fabs(lj - li) > fmax(tau, need);
 }
 
 // close[i] = 1 when the neighbours i and i+1 (eigenvalues sorted descending)
 // are not separated
 __global__ void refine_close_kernel(int m, int n, const double* __restrict__ Wg, const double* __restrict__ T,
-                                    const double* __restrict__ lt, double tau, int* __restrict__ close) {
+                                    const double* __restrict__ lt, double tau, double rho, int* __restrict__ close) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     int c = 0;
     if (i + 1 < m) {
         const Blocks b = blocks(i, i + 1, m, n, Wg, T);
         const cplx R = {-b.G.r, -b.G.i};
-        c = !separated(lt[i], lt[i + 1], b.Sg, R, tau);
+        c = !separated(lt[i], lt[i + 1], b.Sg, R, tau, rho);
     }
     close[i] = c;
 }
@@ -301,8 +301,8 @@ SK_DEV int basis_of(int i, int m, const int* __restrict__ cid, const double* __r
 // m x m planes of Et (E~11 real, imag, E~21 real, imag).
 __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg, const double* __restrict__ T,
                                      const double* __restrict__ lt, const int* __restrict__ cid,
-                                     const double* __restrict__ Vc, double tau, double* __restrict__ Et,
-                                     RefineScalars* sc) {
+                                     const double* __restrict__ Vc, double tau, double rho,
+                                     double* __restrict__ Et, RefineScalars* sc) {
     const long long ld = n, mm = (long long)m * m;
     double emax = 0.0, rn2 = 0.0;
     unsigned int close = 0;
@@ -330,7 +330,7 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
         const cplx R = {(i == j ? 1.0 : 0.0) - G.r, -G.i};
         cplx E11, E21;
         rn2 += R.r * R.r + R.i * R.i;
-        if (i != j && !same && separated(li, lj, Sg, R, tau)) {
+        if (i != j && !same && separated(li, lj, Sg, R, tau, rho)) {
             const double d = lj - li;
             E11 = {(Sg.r + lj * R.r) / d, (Sg.i + lj * R.i) / d};
             const double a = hypot(E11.r, E11.i);
@@ -341,7 +341,7 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
         }
         const cplx num = {Sf.r - lj * F.r, Sf.i - lj * F.i};
         const double d2 = lj + li;
-        if (fabs(d2) > fmax(tau, RHO * (hypot(Sf.r, Sf.i) + fabs(lj) * hypot(F.r, F.i)))) {
+        if (fabs(d2) > fmax(tau, rho * (hypot(Sf.r, Sf.i) + fabs(lj) * hypot(F.r, F.i)))) {
             E21 = cscale(num, 1.0 / d2);
             const double a = hypot(E21.r, E21.i);
             if (a > emax) {
@@ -376,8 +376,9 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
 // E11 = B - I + B E~11 and E21 = conj(B) E~21 (the conjugate partners rotate
 // by conj(B)); then U = [[Er + Fr, Ei + Fi], [Fi - Ei, Er - Fr]].
 __global__ void refine_u_kernel(int m, const int* __restrict__ cid, const double* __restrict__ Vc,
-                                const double* __restrict__ Et, double* __restrict__ U) {
+                                const double* __restrict__ Et, double* __restrict__ U, RefineScalars* sc) {
     const long long mm = (long long)m * m, ldu = 2LL * m;
+    double umax = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mm;
          e += (long long)gridDim.x * blockDim.x) {
         const int q = (int)(e % m), j = (int)(e / m);
@@ -407,7 +408,12 @@ __global__ void refine_u_kernel(int m, const int* __restrict__ cid, const double
         U[q + (m + j) * ldu] = E11.i + E21.i;
         U[(m + q) + j * ldu] = E21.i - E11.i;
         U[(m + q) + (m + j) * ldu] = E11.r - E21.r;
+        umax = fmax(umax, fmax(fmax(fabs(E11.r + E21.r), fabs(E11.i + E21.i)),
+                               fmax(fabs(E21.i - E11.i), fabs(E11.r - E21.r))));
     }
+    for (int o = 16; o > 0; o >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+    if ((threadIdx.x & 31) == 0 && umax > 0.0)
+        atomicMax(&sc->umax_bits, (unsigned long long)__double_as_longlong(umax));
 }
 
 __global__ void refine_reset_kernel(RefineScalars* sc) {
@@ -416,6 +422,7 @@ __global__ void refine_reset_kernel(RefineScalars* sc) {
         sc->nclose = 0u;
         sc->rnorm2 = 0.0;
         sc->where = 0ULL;
+        sc->umax_bits = 0ULL;
     }
 }
 
@@ -474,7 +481,7 @@ size_t refine_ws(int n) {
 }
 
 int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, double* M, int maxit, void* ws,
-           size_t ws_bytes, int* status, RefineInfo* info) {
+           size_t ws_bytes, int* status, RefineInfo* info, double rho) {
     if (n % 2 || n < 2) return SKEW_ERR_UNSUPPORTED;
     const int m = n / 2;
     Carve cv(ws, ws_bytes);
@@ -484,45 +491,71 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
     count_launch();
     if (info) {
         info->iterations = 0;
-        for (int k = 0; k < 8; k++) { info->emax[k] = 0.0; info->nclose[k] = 0; }
+        for (int k = 0; k < 8; k++) {
+            info->emax[k] = 0.0;
+            info->nclose[k] = info->slices[k] = info->uslices[k] = 0;
+        }
     }
+    struct KindScope {  // products of this loop are timed as their own kind
+        KindScope() { g_kt_ozaki_kind = KT_OZAKI_REFINE; }
+        ~KindScope() { g_kt_ozaki_kind = KT_OZAKI; }
+    } kind_scope;
     const long long ldn = n;
     for (int it = 0; it < maxit; it++) {
-        // Wg = M^T M, AM = S M, T = M^T (S M): FP64-accurate tensor-core products
-        int rc = ozaki_gemm(st, n, n, n, 1.0, M, ldn, 1, 1.0, M, ldn, 1, 1.0, 0.0, w.Wg, ldn, w.oz, w.oz_bytes, status, 0);
+        // The Gram and projection products keep all eight digit slices: an
+        // error delta in Wg or T enters E_ij as delta / (l_j - l_i), and dense
+        // spectra have gaps far below any bound on the correction, so a
+        // cheaper product stalls the iteration instead of speeding it up.
+        const int sl = 8;
+        // Wg = M^T M (symmetric), AM = S M, T = M^T (S M) (skew): FP64-accurate
+        // tensor-core products, Wg and T on their lower triangle
+        int rc = ozaki_gemm(st, n, n, n, 1.0, M, ldn, 1, 1.0, M, ldn, 1, 1.0, 0.0, w.Wg, ldn, w.oz, w.oz_bytes, status,
+                            0, sl, 1);
         if (rc) return rc;
         // row r of S is minus column r of S (skew), read contiguously
-        rc = ozaki_gemm(st, n, n, n, 1.0, w.S, ldn, 1, -1.0, M, ldn, 1, 1.0, 0.0, w.AM, ldn, w.oz, w.oz_bytes, status, 0);
+        rc = ozaki_gemm(st, n, n, n, 1.0, w.S, ldn, 1, -1.0, M, ldn, 1, 1.0, 0.0, w.AM, ldn, w.oz, w.oz_bytes, status,
+                        0, sl, 0);
         if (rc) return rc;
-        rc = ozaki_gemm(st, n, n, n, 1.0, M, ldn, 1, 1.0, w.AM, ldn, 1, 1.0, 0.0, w.T, ldn, w.oz, w.oz_bytes, status, 0);
+        rc = ozaki_gemm(st, n, n, n, 1.0, M, ldn, 1, 1.0, w.AM, ldn, 1, 1.0, 0.0, w.T, ldn, w.oz, w.oz_bytes, status,
+                        0, sl, 1);
         if (rc) return rc;
         refine_lambda_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt);
         refine_reset_kernel<<<1, 32, 0, st>>>(w.sc);
         lmax_kernel<<<1, 1024, 0, st>>>(m, w.lt, &w.sc->lmax);
         count_launch(3);
         double lmax = 0.0;
-        if (cudaMemcpyAsync(&lmax, &w.sc->lmax, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return SKEW_ERR_CUDA;
+        if (const cudaError_t e = cudaMemcpyAsync(&lmax, &w.sc->lmax, sizeof(double), cudaMemcpyDeviceToHost, st))
+            return cuda_fail(e);
+        if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
         const double tau = 64.0 * n * DBL_EPSILON * lmax;
-        refine_close_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt, tau, w.close);
+        refine_close_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt, tau, rho, w.close);
         refine_rr_kernel<<<m, 32, 0, st>>>(m, n, w.Wg, w.T, w.close, w.lt, w.cid, w.Vc, w.nbig);
         // E~ lives in the AM buffer (free once T is formed)
         refine_etilde_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, n, w.Wg, w.T, w.lt, w.cid, w.Vc, tau,
-                                                                      w.AM, w.sc);
-        refine_u_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, w.cid, w.Vc, w.AM, w.U);
+                                                                      rho, w.AM, w.sc);
+        refine_u_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, w.cid, w.Vc, w.AM, w.U, w.sc);
         count_launch(4);
-        // M <- M + M U (the product reads M's digit slices, taken before C is written)
-        rc = ozaki_gemm(st, n, n, n, 1.0, M, 1, ldn, 1.0, w.U, 2LL * m, 1, 1.0, 1.0, M, ldn, w.oz, w.oz_bytes, status, 0);
-        if (rc) return rc;
-        if (cudaMemcpyAsync(lambda, w.lt, sizeof(double) * m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return SKEW_ERR_CUDA;
         RefineScalars h{};
-        if (cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return SKEW_ERR_CUDA;
-        double emax;
+        if (const cudaError_t e = cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, st))
+            return cuda_fail(e);
+        if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
+        double emax, umax;
         std::memcpy(&emax, &h.emax_bits, sizeof(double));
+        std::memcpy(&umax, &h.umax_bits, sizeof(double));
+        // M <- M + M U: with |U| <= umax the product needs a relative error of
+        // about 2^-62 / umax (entries of M ~ n^-1/2, rows of length n), so
+        // fewer slices serve once the corrections are small
+        int su = 8;
+        if (umax > 0.0) {
+            su = (int)std::ceil((62.0 + std::log2(umax)) / 7.0);
+            su = su < 3 ? 3 : (su > 8 ? 8 : su);
+        }
+        // the product reads M's digit slices, taken before C is written
+        rc = ozaki_gemm(st, n, n, n, 1.0, M, 1, ldn, 1.0, w.U, 2LL * m, 1, 1.0, 1.0, M, ldn, w.oz, w.oz_bytes, status,
+                        0, su, 0);
+        if (rc) return rc;
+        if (const cudaError_t e = cudaMemcpyAsync(lambda, w.lt, sizeof(double) * m, cudaMemcpyDeviceToDevice, st))
+            return cuda_fail(e);
         if (info) {
             info->iterations = it + 1;
             if (it < 8) {
@@ -530,12 +563,15 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
                 info->nclose[it] = (int)h.nclose;
                 info->rnorm[it] = std::sqrt(h.rnorm2);
                 info->where[it] = (long long)h.where;
+                info->slices[it] = sl;
+                info->uslices[it] = su;
             }
         }
         // the next iteration would move the vectors by ~emax^2: stop once that
         // is below the FP64 level
         if (emax < 1e-8) break;
     }
+    if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
     return 0;
 }
 

@@ -2,6 +2,7 @@
 // workspace carve-up and the stage sequence of Algorithm 1 (two-step form) on
 // one stream.
 #include <atomic>
+#include <vector>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -56,8 +57,10 @@ inline int grid_for(size_t total) {
 struct Plan {
     int n, nev, b, P, K, nsw;
     bool vectors, mixed;
-    int planes;       // split-BF16 planes of the mixed back-transforms (0 in the FP64 form)
+    int planes;       // split-BF16 planes of the mixed form (0 in the FP64 form)
     int reduce_prec;  // band reduction: 0 FP64, 2/3 split planes, REDUCE_F64ACC digit slices
+    int qband_prec;   // mixed Q_band: 2/3 split planes or REDUCE_F64ACC digit slices
+    bool qtrd_f32;    // mixed Q_trd in FP32 arithmetic (else FP64)
     size_t ldab;
     // carved pointers
     double *W, *Tfac, *AB, *Vtrd, *tautrd, *alpha, *Qi, *Z;
@@ -84,14 +87,15 @@ bool carve_plan(Plan& p, Carve& cv) {
     const size_t ne = (size_t)(p.nev ? p.nev : 1);
     p.Qi = p.vectors ? cv.take<double>(nn * ne) : nullptr;
     p.Z = p.vectors ? cv.take<double>(nn * 2 * ne) : nullptr;
-    p.Z32 = (p.vectors && p.mixed) ? cv.take<float>(nn * 2 * ne) : nullptr;
+    p.Z32 = (p.vectors && p.qtrd_f32) ? cv.take<float>(nn * 2 * ne) : nullptr;
     p.sz_reduce = band_reduce_ws(p.n, p.b, p.reduce_prec);
     p.ws_reduce = cv.take<char>(p.sz_reduce);
     p.sz_chase = chase_ws(p.n, p.b);
     p.ws_chase = cv.take<char>(p.sz_chase);
     p.sz_tri = tridiag_ws(p.n, p.nev);
     p.ws_tri = cv.take<char>(p.sz_tri);
-    p.sz_qband = p.vectors ? (p.mixed ? qband_mixed_ws(p.n, p.b, 2 * p.nev, p.planes) : qband_ws(p.n, p.b, 2 * p.nev))
+    p.sz_qband = p.vectors ? (p.mixed ? qband_mixed_ws(p.n, p.b, 2 * p.nev, p.qband_prec)
+                                      : qband_ws(p.n, p.b, 2 * p.nev))
                            : 0;
     p.ws_qband = p.vectors ? cv.take<char>(p.sz_qband) : nullptr;
     p.sz_refine = p.refine ? refine_ws(p.n) : 0;
@@ -114,6 +118,14 @@ Plan make_plan(int n, int nev, const skew_opts* o, bool vectors) {
     // the reduction's contractions in the refined mode are FP64-accurate
     p.reduce_prec = !p.mixed ? 0 : (o->mode == SKEW_MODE_MIXED_REFINED ? REDUCE_F64ACC : p.planes);
     p.refine = p.mixed && vectors && n % 2 == 0 && n >= 2 && nev == n / 2 && !(o->fault & SKEW_FAULT_NO_REFINE);
+    // back-transforms: split products and FP32 Q_trd in the split modes; the
+    // refined mode takes Q_band as FP64-accurate digit-slice products (the
+    // refinement starts from vectors about 100x more orthogonal and saves an
+    // iteration) and Q_trd in FP32, or in FP64 when there is no complete
+    // basis to refine (nev < n/2, odd n)
+    const bool refined_mode = p.mixed && o->mode == SKEW_MODE_MIXED_REFINED;
+    p.qband_prec = !p.mixed ? 0 : (refined_mode ? REDUCE_F64ACC : p.planes);
+    p.qtrd_f32 = p.mixed && vectors && !(refined_mode && !p.refine);
     return p;
 }
 
@@ -162,6 +174,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
         if (!carve_plan(p, cv)) return SKEW_ERR_WORKSPACE;
     }
     const int maxit = (o && (o->fault & SKEW_FAULT_INVIT_NOCONV)) ? 0 : 5;
+    last_refine_info() = RefineInfo{};  // iterations = 0 unless this solve refines
 
     mark(0);
     zero_int_kernel<<<1, 32, 0, st>>>(p.status);
@@ -187,7 +200,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
             return SKEW_ERR_CUDA;
     }
     mark(6);
-    if (vectors && !p.mixed) {
+    if (vectors && !p.qtrd_f32) {
         if (apply_qtrd(st, n, p.b, p.Vtrd, p.tautrd, p.Z, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
     } else if (vectors) {
         // mixed form: Q_trd in FP32 arithmetic (reflectors from the FP64 chase)
@@ -201,14 +214,15 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     mark(7);
     if (vectors) {
         rc = p.mixed ? apply_qband_mixed(st, n, p.b, p.W, n, p.Tfac, p.Z, n, 2 * nev, p.ws_qband, p.sz_qband, p.status,
-                                         p.planes)
+                                         p.qband_prec)
                      : apply_qband(st, n, p.b, p.W, n, p.Tfac, p.Z, n, 2 * nev, p.ws_qband, p.sz_qband);
         if (rc) return rc;
     }
     mark(8);
     if (p.refine) {
-        const int iters = (o && o->refine_iters > 0) ? o->refine_iters : 6;
-        rc = refine(st, n, A, lda, lambda, p.Z, iters, p.ws_refine, p.sz_refine, p.status, &last_refine_info());
+        const int iters = (o && o->refine_iters > 0) ? (o->refine_iters < 8 ? o->refine_iters : 8) : 8;
+        const double rho = (o && o->refine_rho > 0) ? (double)o->refine_rho : 1024.0;
+        rc = refine(st, n, A, lda, lambda, p.Z, iters, p.ws_refine, p.sz_refine, p.status, &last_refine_info(), rho);
         if (rc) return rc;
     }
     mark(9);
@@ -221,7 +235,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
         count_launch();
     }
     mark(10);
-    return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
+    return cuda_ok(cudaGetLastError());
 }
 
 std::atomic<long long> g_launches{0};
@@ -234,6 +248,61 @@ RefineInfo& last_refine_info() {
     return info;
 }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+struct KtRec {
+    cudaEvent_t a, b;
+    int kind;
+    double flops;
+};
+struct KTimer {
+    bool on = false;
+    size_t used = 0;
+    std::vector<KtRec> recs;  // events are created on first use and reused
+};
+KTimer& ktimer() {
+    static KTimer t;
+    return t;
+}
+constexpr size_t KT_CAP = 16384;
+}  // namespace
+
+int g_kt_ozaki_kind = KT_OZAKI;
+
+namespace {
+std::atomic<const char*> g_last_cuda_error{"none"};
+}
+int cuda_fail(cudaError_t e) {
+    if (e != cudaSuccess) g_last_cuda_error.store(cudaGetErrorName(e), std::memory_order_relaxed);
+    return SKEW_ERR_CUDA;
+}
+
+int kt_begin(cudaStream_t st) {
+    KTimer& t = ktimer();
+    if (!t.on) return -1;
+    if (t.used == t.recs.size()) {
+        if (t.recs.size() >= KT_CAP) return -1;
+        KtRec r{};
+        if (cudaEventCreate(&r.a) != cudaSuccess) return -1;
+        if (cudaEventCreate(&r.b) != cudaSuccess) {
+            cudaEventDestroy(r.a);
+            return -1;
+        }
+        t.recs.push_back(r);
+    }
+    const int slot = (int)t.used;
+    if (cudaEventRecord(t.recs[slot].a, st) != cudaSuccess) return -1;
+    t.used++;
+    return slot;
+}
+
+void kt_end(cudaStream_t st, int slot, int kind, double flops) {
+    if (slot < 0) return;
+    KTimer& t = ktimer();
+    t.recs[slot].kind = kind;
+    t.recs[slot].flops = flops;
+    if (cudaEventRecord(t.recs[slot].b, st) != cudaSuccess) t.recs[slot].kind = -1;
+}
 
 }  // namespace sk
 
@@ -308,7 +377,7 @@ int skew_eig(int n, const double* A, int lda, int nev, double* lambda, double* Z
         if (cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
     }
     cudaFreeAsync(ws, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SKEW_ERR_CUDA;
+    if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
     return rc ? rc : info;
 }
 
@@ -349,7 +418,7 @@ int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda, doub
         if (cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
     }
     cudaFreeAsync(base, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SKEW_ERR_CUDA;
+    if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
     return rc ? rc : info;
 }
 
@@ -375,7 +444,7 @@ int skew_eig_profile(int n, const double* A, int lda, int nev, double* lambda, d
         d_info = static_cast<int*>(workspace);
         if (cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+    if (const cudaError_t e = cudaStreamSynchronize(st)) rc = cuda_fail(e);
     if (rc == 0)
         for (int i = 0; i < SKEW_NSTAGES; i++) cudaEventElapsedTime(&stage_ms[i], ev.ev[i], ev.ev[i + 1]);
     for (int i = 0; i <= SKEW_NSTAGES; i++) cudaEventDestroy(ev.ev[i]);
@@ -434,6 +503,36 @@ int skew_eig_metrics(int n, const double* A, int lda, int nev, const double* lam
 
 long long skew_launch_count(void) { return launch_count(); }
 
+const char* skew_last_cuda_error(void) { return g_last_cuda_error.load(std::memory_order_relaxed); }
+
+int skew_kernel_timing(int enable) {
+    KTimer& t = ktimer();
+    t.on = enable != 0;
+    t.used = 0;
+    return 0;
+}
+
+int skew_kernel_timing_read(int kind, double* ms, double* flops, long long* launches) {
+    if (kind < 0 || kind >= KT_KINDS) return -1;
+    KTimer& t = ktimer();
+    double tm = 0.0, fl = 0.0;
+    long long k = 0;
+    for (size_t i = 0; i < t.used; i++) {
+        const KtRec& r = t.recs[i];
+        if (r.kind != kind) continue;
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return SKEW_ERR_CUDA;
+        float e = 0.f;
+        if (cudaEventElapsedTime(&e, r.a, r.b) != cudaSuccess) return SKEW_ERR_CUDA;
+        tm += e;
+        fl += r.flops;
+        k++;
+    }
+    if (ms) *ms = tm;
+    if (flops) *flops = fl;
+    if (launches) *launches = k;
+    return 0;
+}
+
 int skew_refine_stats(double* emax, int* nclose, int cap) {
     const RefineInfo& r = last_refine_info();
     for (int i = 0; i < cap && i < 8; i++) {
@@ -448,6 +547,15 @@ int skew_refine_trace(double* rnorm, long long* where, int cap) {
     for (int i = 0; i < cap && i < 8; i++) {
         if (rnorm) rnorm[i] = r.rnorm[i];
         if (where) where[i] = r.where[i];
+    }
+    return r.iterations;
+}
+
+int skew_refine_slices(int* slices, int* uslices, int cap) {
+    const RefineInfo& r = last_refine_info();
+    for (int i = 0; i < cap && i < 8; i++) {
+        if (slices) slices[i] = r.slices[i];
+        if (uslices) uslices[i] = r.uslices[i];
     }
     return r.iterations;
 }

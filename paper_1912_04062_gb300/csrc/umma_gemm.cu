@@ -237,10 +237,13 @@ bool make_tmap(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
 inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
 
 template <int BN, int STAGES>
-cudaError_t launch(cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& tb, const UmmaParams& p, dim3 grid) {
+cudaError_t launch(cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& tb, const UmmaParams& p, dim3 grid,
+                   double flops) {
     const size_t smem = UmmaSmem<BN, STAGES>::bytes();
     cudaFuncSetAttribute(umma_gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int kt = kt_begin(st);
     umma_gemm_kernel<BN, STAGES><<<grid, UT, smem, st>>>(ta, tb, p);
+    kt_end(st, kt, KT_SPLIT, flops);
     count_launch();
     return cudaGetLastError();
 }
@@ -302,14 +305,16 @@ int split_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double*
     p.C = C;
     p.ldc = ldc;
     p.status = status;
+    // algorithmic work: the kept plane products over the outputs written
+    const double flops = 2.0 * p.nterms * (lower ? lower_count(M, N) : (double)M * N) * K;
     cudaError_t e;
     if (lower) {
         const long long T = Mp / UM;
-        e = launch<128, 3>(st, ta, tb, p, dim3((unsigned)(T * (T + 1) / 2)));
+        e = launch<128, 3>(st, ta, tb, p, dim3((unsigned)(T * (T + 1) / 2)), flops);
     } else if (BN == 64) {
-        e = launch<64, 4>(st, ta, tb, p, dim3((unsigned)(Mp / UM), (unsigned)(Np / 64)));
+        e = launch<64, 4>(st, ta, tb, p, dim3((unsigned)(Mp / UM), (unsigned)(Np / 64)), flops);
     } else {
-        e = launch<128, 3>(st, ta, tb, p, dim3((unsigned)(Mp / UM), (unsigned)(Np / 128)));
+        e = launch<128, 3>(st, ta, tb, p, dim3((unsigned)(Mp / UM), (unsigned)(Np / 128)), flops);
     }
     return e == cudaSuccess ? 0 : SKEW_ERR_CUDA;
 }

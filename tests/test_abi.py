@@ -73,3 +73,31 @@ def test_workspace_size_grows(sk):
     # dominant terms: W (n^2), chase reflectors (~n^2), interleaved LU (4 n nev)
     n = 4096
     assert sizes[2] >= 8 * (2 * n * n)
+
+
+def test_f64acc_ex_argument_checks_are_host_side(sk):
+    L = sk.lib()
+    nul = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+
+    def call(M=8, N=8, K=8, ldc=8, slices=8, lower=0):
+        return L.skew_gemm_f64acc_ex(M, N, K, 1.0, fake, 8, 1, fake, 8, 1, 0.0, fake, ldc, slices, lower,
+                                     fake, 1 << 20, fake, nul)
+    assert call(M=-1) == -1
+    assert call(N=-1) == -2
+    assert call(K=0) == -3
+    assert call(ldc=7) == -13
+    assert call(slices=0) == -14
+    assert call(slices=9) == -14
+    assert call(lower=2) == -15
+    # the error-name query is available without a failure
+    assert L.skew_last_cuda_error()
+
+
+def test_kernel_timing_switch_is_host_side(sk):
+    L = sk.lib()
+    assert L.skew_kernel_timing(1) == 0
+    ms, fl, k = sk.kernel_timing_read(sk.SKEW_KERNEL_OZAKI)
+    assert (ms, fl, k) == (0.0, 0.0, 0)
+    assert L.skew_kernel_timing_read(7, None, None, None) == -1
+    assert L.skew_kernel_timing(0) == 0

@@ -156,6 +156,48 @@ def test_gemm_f64acc_matches_fp64(M, N, K):
     assert np.all(err <= 2.0 ** -45 * scale + K * 2.0 ** -54 * rmax + 2 * K * eps * scale)
 
 
+@pytest.mark.parametrize("slices", [3, 5, 6, 7])
+def test_gemm_f64acc_fewer_slices(slices):
+    # keeping the slice pairs of order < s: error about 2^-7s of the row-max
+    # products (digit truncation of both operands plus the dropped pairs)
+    import torch
+    import paper_1912_04062_gb300 as sk
+    rng = np.random.default_rng(100 + slices)
+    M, N, K = 200, 130, 700
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-4, 4, (M, 1)))
+    B = rng.standard_normal((N, K))
+    C, st = sk.gemm_f64acc(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), slices=slices)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    rmax = np.abs(A).max(1)[:, None] * np.abs(B).max(1)[None, :]
+    err = np.abs(C.cpu().numpy() - A @ B.T)
+    assert np.all(err <= (slices + 2) * K * 2.0 ** (-7 * slices) * rmax)
+    # and it does get coarser with fewer slices (not silently full precision)
+    if slices <= 5:
+        assert np.max(err / rmax) > 2.0 ** (-7 * slices - 14)
+
+
+def test_gemm_f64acc_lower_tiles():
+    import torch
+    import paper_1912_04062_gb300 as sk
+    rng = np.random.default_rng(9)
+    n, K = 300, 257
+    X = rng.standard_normal((n, K))
+    C0 = rng.standard_normal((n, n))
+    dC = sk.fortran(torch.from_numpy(C0).cuda())
+    C, st = sk.gemm_f64acc(torch.from_numpy(X).cuda(), torch.from_numpy(X).cuda(), dC, beta=1.0, lower=True)
+    torch.cuda.synchronize()
+    C = C.cpu().numpy()
+    ref = C0 + X @ X.T
+    for r0 in range(0, n, 128):
+        for c0 in range(0, n, 64):
+            blk = (slice(r0, min(n, r0 + 128)), slice(c0, min(n, c0 + 64)))
+            if c0 >= r0 + 128:
+                assert np.array_equal(C[blk], C0[blk])       # above the diagonal: untouched
+            else:
+                assert np.max(np.abs(C[blk] - ref[blk])) <= 1e-12 * np.abs(ref).max()
+
+
 def test_gemm_f64acc_under_cancellation():
     # rows of B orthogonal to the rows of A: the exact product is tiny next to
     # |A||B|; a longdouble reference shows the result is FP64-accurate, far
@@ -203,9 +245,36 @@ def test_mixed_refined_meets_fp64_tolerances(n, kind, planes):
     assert np.max(np.abs(lam - lam_o)) <= 1e-12 * nrm2, (it, emax, nclose)
     m = oracle.scaled_metrics(A, lam, X, Y)
     assert m["resid"] <= 50 and m["orth"] <= 50, (m, it, emax, nclose)
-    # the loop ends on a correction below 1e-8, reached quadratically from the
-    # one before it (earlier steps may hand pairs over from Rayleigh-Ritz
-    # clusters to the first-order formula and need not shrink quadratically)
+    # the loop ends on a correction below 1e-8 from FP64-accurate products
+    # (all eight digit slices), reached quadratically from the step before it
+    # plus that step's product error (earlier steps use fewer slices, and may
+    # hand pairs over from Rayleigh-Ritz clusters to the first-order formula)
+    sl, su = sk.refine_slices()
+    assert len(sl) == it and sl[-1] == 8 and all(3 <= s <= 8 for s in sl + su)
     assert emax[-1] < 1e-8
     if len(emax) >= 2:
-        assert emax[-1] <= max(1e3 * emax[-2] ** 2, 1e-14)
+        prod_err = 0.0 if sl[-2] == 8 else 1e4 * 2.0 ** (-7 * sl[-2])
+        assert emax[-1] <= max(1e3 * emax[-2] ** 2, 1e-14, prod_err), (emax, sl)
+
+
+@pytest.mark.parametrize("n,nev,kind", [(512, 100, "prescribed"), (257, 128, "random"), (1024, 300, "bse")])
+def test_refined_mode_without_complete_basis(n, nev, kind):
+    # nev < n/2 or odd n: no basis to refine, so the refined mode runs
+    # FP64-accurate back-transforms (digit-slice Q_band, FP64 Q_trd) and must
+    # meet the FP64 bounds without refinement
+    import inputs
+    import oracle
+    import paper_1912_04062_gb300 as sk
+    if kind == "random":
+        A = inputs.random_skew(n, seed=41)
+    elif kind == "prescribed":
+        A, _ = inputs.prescribed(n, seed=4)
+    else:
+        A = inputs.bse(n, seed=5)
+    info, lam, X, Y = _mixed_solve(A, nev, sk.SKEW_MODE_MIXED_REFINED)
+    assert info == 0
+    assert sk.refine_stats()[0] == 0
+    lam_o, *_ = oracle.skew_eig(A, nev, vectors=False)
+    assert np.max(np.abs(lam - lam_o)) <= 1e-12 * float(lam_o.max())
+    m = oracle.scaled_metrics(A, lam, X, Y)
+    assert m["resid"] <= 50 and m["orth"] <= 50, m
