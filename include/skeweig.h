@@ -87,9 +87,10 @@ typedef struct {
     int check_finite;  /* 1: scan A for NaN/Inf first (SKEW_ERR_NONFINITE) */
     int fault;         /* SKEW_FAULT_* bits, tests only; 0 in production */
     int refine_iters;  /* mixed modes: maximum refinement iterations (1..8); 0 -> 8 */
-    int refine_rho;    /* mixed modes: a pair of eigenvalues gets the first-order
-                          correction when it asks for a rotation below 1/refine_rho,
-                          else it joins a Rayleigh-Ritz cluster; 0 -> 1024 */
+    int refine_rho;    /* mixed modes: neighbouring eigenvalues whose first-order
+                          correction would rotate by more than 1/refine_rho are
+                          refined together by Rayleigh-Ritz (clusters of up to 16);
+                          0 -> 1024 */
     int reserved[2];
 } skew_opts;
 
@@ -139,6 +140,36 @@ int skew_eig_ex(int n, const double* A, int lda, int nev, double* lambda,
  */
 int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda,
                   double* Z_re, double* Z_im, const skew_opts* opts, void* stream);
+
+/*
+ * Batched solve: `count` independent problems, each as in skew_eig (matrix b:
+ * order n[b], device A[b] with leading dimension lda[b], nev[b] eigenpairs
+ * into device lambda[b], Z_re[b], Z_im[b] of leading dimension n[b]).  The
+ * size arrays and the pointer arrays are host arrays; Z_re == Z_im == NULL
+ * (the arrays) or Z_re[b] == Z_im[b] == NULL (one matrix) asks for
+ * eigenvalues only.  Orders 2..160 are solved together, one CTA per matrix
+ * (matrix in shared memory, unblocked Householder tridiagonalisation, then one
+ * bisection and one inverse-iteration launch for all matrices, then one
+ * back-transform launch), always in FP64; larger orders run the two-step solve
+ * of skew_eig_ex one after another in `opts`' mode.  Not in the paper (it
+ * solves one matrix per run).
+ * Asynchronous on `stream`.  skew_eig_batched allocates its workspace with
+ * cudaMallocAsync / cudaFreeAsync on the stream and reports no per-matrix
+ * status; skew_eig_batched_ex takes a caller workspace of at least
+ * skew_eig_batched_workspace_size(count, n, nev, opts) bytes and a device
+ * array d_info[count] (may be NULL) that receives 0 or 1000 + j per matrix.
+ * Returns 0, -1 (count < 0), -k for the first invalid per-matrix argument
+ * (2 n, 3 A, 4 lda, 5 nev, 6 lambda, 7 Z), SKEW_ERR_WORKSPACE, SKEW_ERR_NOMEM,
+ * SKEW_ERR_UNSUPPORTED (INT8 mode) or SKEW_ERR_CUDA.
+ */
+size_t skew_eig_batched_workspace_size(int count, const int* n, const int* nev, const skew_opts* opts);
+int skew_eig_batched(int count, const int* n, const double* const* A, const int* lda, const int* nev,
+                     double* const* lambda, double* const* Z_re, double* const* Z_im,
+                     const skew_opts* opts, void* stream);
+int skew_eig_batched_ex(int count, const int* n, const double* const* A, const int* lda,
+                        const int* nev, double* const* lambda, double* const* Z_re,
+                        double* const* Z_im, const skew_opts* opts, void* workspace,
+                        size_t ws_bytes, int* d_info, void* stream);
 
 /* Stages timed by skew_eig_profile (Algorithm 1, two-step form):
  * 0 ingest (copy of the strict lower triangle), 1 full-to-band reduction,

@@ -48,6 +48,9 @@ SIGNATURES = {
     "skew_eig_workspace_size": (_sz, [_i, _i, _p]),
     "skew_eig_ex": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
     "skew_eig_host": (_i, [_i, _p, _i, _i, _p, _p, _p, _p, _p]),
+    "skew_eig_batched_workspace_size": (_sz, [_i, _p, _p, _p]),
+    "skew_eig_batched": (_i, [_i, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
+    "skew_eig_batched_ex": (_i, [_i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p, _p]),
     "skew_eig_profile": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
     "skew_metrics_ws": (_sz, [_i, _i, _i]),
     "skew_eig_metrics": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _i, _p, _p, _sz, _p]),
@@ -344,6 +347,63 @@ def kernel_timing_read(kind: int):
     code = lib().skew_kernel_timing_read(kind, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(k))
     _check(code, "skew_kernel_timing_read")
     return ms.value, fl.value, k.value
+
+
+def _batch_arrays(As, nevs, vectors):
+    torch = _torch()
+    count = len(As)
+    As = [_as_device_f64(A) for A in As]
+    ns = [int(A.shape[0]) for A in As]
+    lams = [torch.empty(max(nv, 1), dtype=torch.float64, device=A.device) for A, nv in zip(As, nevs)]
+    Zr = [fortran_empty(n, nv, A.device) if vectors else None for A, n, nv in zip(As, ns, nevs)]
+    Zi = [fortran_empty(n, nv, A.device) if vectors else None for A, n, nv in zip(As, ns, nevs)]
+    IA = ctypes.c_int * max(count, 1)
+    PA = ctypes.c_void_p * max(count, 1)
+    c_n = IA(*ns)
+    c_lda = IA(*[_ld(A) for A in As])
+    c_nev = IA(*[int(v) for v in nevs])
+    c_A = PA(*[A.data_ptr() for A in As])
+    c_l = PA(*[t.data_ptr() for t in lams])
+    c_zr = PA(*[z.data_ptr() for z in Zr]) if vectors else None
+    c_zi = PA(*[z.data_ptr() for z in Zi]) if vectors else None
+    return count, As, lams, Zr, Zi, (c_n, c_A, c_lda, c_nev, c_l, c_zr, c_zi)
+
+
+def skew_eig_batched(As, nevs, vectors: bool = True, opts: Options | None = None, stream=None, info=False):
+    """Solve many independent problems (list of float64 CUDA tensors A_b with
+    nev_b each).  Returns lists (lam_b, Zr_b, Zi_b) [and the per-matrix status
+    tensor when info=True]."""
+    torch = _torch()
+    count, As, lams, Zr, Zi, c = _batch_arrays(As, nevs, vectors)
+    c_n, c_A, c_lda, c_nev, c_l, c_zr, c_zi = c
+    o = (opts or Options()).c()
+    nbytes = int(lib().skew_eig_batched_workspace_size(count, c_n, c_nev, ctypes.byref(o)))
+    dev = As[0].device if As else torch.device("cuda")
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    d_info = torch.full((max(count, 1),), -1, dtype=torch.int32, device=dev)
+    code = lib().skew_eig_batched_ex(count, c_n, c_A, c_lda, c_nev, c_l, c_zr, c_zi, ctypes.byref(o), _ptr(ws),
+                                     ws.numel(), _ptr(d_info), _stream(stream))
+    _check(code, "skew_eig_batched_ex")
+    out = ([l[:nv] for l, nv in zip(lams, nevs)], Zr, Zi)
+    return out + (d_info[:count],) if info else out
+
+
+def shard_lpt(sizes, world: int):
+    """Partition batch members over `world` ranks by longest-processing-time on
+    n^3 cost (largest first, each to the least-loaded rank, ties to the lowest
+    rank).  Returns one sorted index list per rank; deterministic, so every
+    rank computes the same partition without communication."""
+    import heapq
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(sizes)), key=lambda i: (-int(sizes[i]) ** 3, i))
+    heap = [(0, r) for r in range(world)]
+    parts = [[] for _ in range(world)]
+    for i in order:
+        load, r = heapq.heappop(heap)
+        parts[r].append(i)
+        heapq.heappush(heap, (load + int(sizes[i]) ** 3, r))
+    return [sorted(p) for p in parts]
 
 
 def launch_count() -> int:

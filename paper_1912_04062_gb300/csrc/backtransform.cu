@@ -273,13 +273,20 @@ int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw, const d
 
 // Mixed form: Q_band with the two contractions on the tensor cores:
 // Y^T = Z[o:, :]^T V_p, then Z[o:, :] -= (V_p T_p) Y, V_p T_p in FP64.
-// planes: 2 / 3 (BF16x3 / BF16x6 split products) or REDUCE_F64ACC
-// (FP64-accurate digit-slice products)
+// planes: 2 / 3 (BF16x3 / BF16x6 split products, one panel per pass) or
+// REDUCE_F64ACC (FP64-accurate digit-slice products, QG panels per pass: the
+// product Q_p0 Q_p0+1 ... Q_p0+QG-1 is one compact WY block I - V T V^T with
+// V = [V_p0 ... V_p0+QG-1] and T built by the block form of the forward
+// recursion of Eq. 7, T_1..j = [[T_1..j-1, -T_1..j-1 (V_1..j-1^T V_j) T_j],
+// [0, T_j]], so Z is read and written once per QG panels and the update has
+// K = QG b)
+constexpr int QG = 4;
+
 static size_t qband_gemm_ws(int n, int b, int k, int planes) {
     size_t g1, g2;
     if (planes == REDUCE_F64ACC) {
-        g1 = ozaki_gemm_ws(k, b, n);
-        g2 = ozaki_gemm_ws(n, k, b);
+        g1 = ozaki_gemm_ws(k, QG * b, n);
+        g2 = ozaki_gemm_ws(n, k, QG * b);
     } else {
         g1 = split_gemm_ws(k, b, n, planes);
         g2 = split_gemm_ws(n, k, b, planes);
@@ -288,38 +295,85 @@ static size_t qband_gemm_ws(int n, int b, int k, int planes) {
 }
 
 size_t qband_mixed_ws(int n, int b, int k, int planes) {
-    return align_up(sizeof(double) * (size_t)n * b) * 2 + align_up(sizeof(double) * (size_t)k * b) +
-           qband_gemm_ws(n, b, k, planes) + 256;
+    const size_t w = (planes == REDUCE_F64ACC) ? (size_t)QG * b : (size_t)b;
+    return align_up(sizeof(double) * (size_t)n * w) * 2 + align_up(sizeof(double) * (size_t)k * w) +
+           3 * align_up(sizeof(double) * w * w) + qband_gemm_ws(n, b, k, planes) + 256;
 }
+
+namespace {
+// T of a panel group: the diagonal blocks are the panels' own T (b x b each),
+// everything else 0 (filled in afterwards).
+__global__ void tgroup_init_kernel(int g, int b, const double* __restrict__ Tp, double* __restrict__ Tg) {
+    const int gb = g * b;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gb * gb; e += gridDim.x * blockDim.x) {
+        const int r = e % gb, c = e / gb, jr = r / b, jc = c / b;
+        Tg[e] = (jr == jc) ? Tp[(size_t)jr * b * b + (r % b) + (size_t)(c % b) * b] : 0.0;
+    }
+}
+}  // namespace
 
 int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz,
                       int k, void* ws, size_t ws_bytes, int* status, int planes) {
     const int P = num_panels(n, b);
     if (P == 0 || k <= 0) return 0;
+    const bool acc = planes == REDUCE_F64ACC;
+    const int w = acc ? QG * b : b;
     Carve cv(ws, ws_bytes);
-    double* V = cv.take<double>((size_t)n * b);
-    double* VT = cv.take<double>((size_t)n * b);
-    double* Yt = cv.take<double>((size_t)k * b);
+    double* V = cv.take<double>((size_t)n * w);
+    double* VT = cv.take<double>((size_t)n * w);
+    double* Yt = cv.take<double>((size_t)k * w);
+    double* Tg = cv.take<double>((size_t)w * w);
+    double* G = cv.take<double>((size_t)w * w);
+    double* tmp = cv.take<double>((size_t)w * w);
     const size_t gsz = qband_gemm_ws(n, b, k, planes);
     void* gws = cv.take<char>(gsz);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
-    for (int p = P - 1; p >= 0; p--) {
-        const int o = (p + 1) * b, m = n - o;
-        const double* Tp = Tfac + (size_t)p * b * b;
-        double* Zo = Z + o;
-        if (panel_v(st, n, b, p, W, ldw, V, n) != cudaSuccess) return SKEW_ERR_CUDA;
-        if (gemm(st, false, false, m, b, b, 1.0, V, n, Tp, b, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
-        // Yt = Z_o^T V (k x b), then Z_o -= (V T) Yt^T
-        int rc;
-        if (planes == REDUCE_F64ACC) {
-            rc = ozaki_gemm(st, k, b, m, 1.0, Zo, ldz, 1, 1.0, V, n, 1, 1.0, 0.0, Yt, k, gws, gsz, status);
-            if (rc) return rc;
-            rc = ozaki_gemm(st, m, k, b, -1.0, VT, 1, n, 1.0, Yt, 1, k, 1.0, 1.0, Zo, ldz, gws, gsz, status);
-        } else {
-            rc = split_gemm(st, k, b, m, 1.0, Zo, ldz, 1, 0, V, n, 1, 0.0, Yt, k, 0, gws, gsz, status, planes);
+    if (!acc) {
+        for (int p = P - 1; p >= 0; p--) {
+            const int o = (p + 1) * b, m = n - o;
+            const double* Tp = Tfac + (size_t)p * b * b;
+            double* Zo = Z + o;
+            if (panel_v(st, n, b, p, W, ldw, V, n) != cudaSuccess) return SKEW_ERR_CUDA;
+            if (gemm(st, false, false, m, b, b, 1.0, V, n, Tp, b, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
+            // Yt = Z_o^T V (k x b), then Z_o -= (V T) Yt^T
+            int rc = split_gemm(st, k, b, m, 1.0, Zo, ldz, 1, 0, V, n, 1, 0.0, Yt, k, 0, gws, gsz, status, planes);
             if (rc) return rc;
             rc = split_gemm(st, m, k, b, -1.0, VT, 1, n, 0, Yt, 1, k, 1.0, Zo, ldz, 0, gws, gsz, status, planes);
+            if (rc) return rc;
         }
+        return 0;
+    }
+    for (int pe = P - 1; pe >= 0; pe -= QG) {
+        const int p0 = pe - QG + 1 > 0 ? pe - QG + 1 : 0, g = pe - p0 + 1, gb = g * b;
+        const int o = (p0 + 1) * b, m = n - o;
+        double* Zo = Z + o;
+        // V of the group (m x gb, ld n): panel p0 + j starts at row j b
+        if (cudaMemsetAsync(V, 0, sizeof(double) * (size_t)n * gb, st) != cudaSuccess) return SKEW_ERR_CUDA;
+        for (int j = 0; j < g; j++)
+            if (panel_v(st, n, b, p0 + j, W, ldw, V + (size_t)j * b * n + (size_t)j * b, n) != cudaSuccess)
+                return SKEW_ERR_CUDA;
+        // T of the group
+        tgroup_init_kernel<<<(gb * gb + 255) / 256, 256, 0, st>>>(g, b, Tfac + (size_t)p0 * b * b, Tg);
+        count_launch();
+        if (g > 1) {
+            if (gemm(st, true, false, gb, gb, m, 1.0, V, n, V, n, 0.0, G, gb) != cudaSuccess) return SKEW_ERR_CUDA;
+            for (int j = 1; j < g; j++) {
+                const int jb = j * b;
+                const double* Tj = Tfac + (size_t)(p0 + j) * b * b;
+                // tmp = (V_1..j-1^T V_j) T_j, then T[0:jb, jb:jb+b] = -T[0:jb, 0:jb] tmp
+                if (gemm(st, false, false, jb, b, b, 1.0, G + (size_t)jb * gb, gb, Tj, b, 0.0, tmp, gb) !=
+                    cudaSuccess)
+                    return SKEW_ERR_CUDA;
+                if (gemm(st, false, false, jb, b, jb, -1.0, Tg, gb, tmp, gb, 0.0, Tg + (size_t)jb * gb, gb) !=
+                    cudaSuccess)
+                    return SKEW_ERR_CUDA;
+            }
+        }
+        if (gemm(st, false, false, m, gb, gb, 1.0, V, n, Tg, gb, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
+        // Yt = Z_o^T V (k x gb), then Z_o -= (V T) Yt^T
+        int rc = ozaki_gemm(st, k, gb, m, 1.0, Zo, ldz, 1, 1.0, V, n, 1, 1.0, 0.0, Yt, k, gws, gsz, status);
+        if (rc) return rc;
+        rc = ozaki_gemm(st, m, k, gb, -1.0, VT, 1, n, 1.0, Yt, 1, k, 1.0, 1.0, Zo, ldz, gws, gsz, status);
         if (rc) return rc;
     }
     return 0;

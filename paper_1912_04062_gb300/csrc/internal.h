@@ -119,6 +119,19 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
            size_t ws_bytes, int* status, RefineInfo* info, double rho = 1024.0);
 RefineInfo& last_refine_info();
 
+// ---- batched.cu (many small independent solves) ------------------------------
+// Largest order of the one-CTA shared-memory path.
+constexpr int BATCH_SMALL_MAX = 160;
+struct BatchProblem {
+    int n, nev, lda;
+    const double* A;
+    double *lambda, *Zre, *Zim;  // Z: n x nev, leading dimension n; Zre == null: values only
+    int* info;                   // device status word of this matrix (may be null)
+};
+size_t batched_small_ws(int count, const BatchProblem* probs);
+// every n in [2, BATCH_SMALL_MAX]; FP64 throughout
+int batched_small(cudaStream_t st, int count, const BatchProblem* probs, void* ws, size_t ws_bytes, int maxit);
+
 // ---- metrics.cu -------------------------------------------------------------
 size_t metrics_ws(int n, int nev, int s);
 int metrics(cudaStream_t st, int n, const double* A, int lda, int nev, const double* lambda, const double* X,

@@ -21,9 +21,9 @@
 // and the update is one real product M <- M + M U,
 //   U = [[Er + Fr, Ei + Fi], [Fi - Ei, Er - Fr]]   (E11 = Er + i Ei, E21 = Fr + i Fi).
 // A pair counts as separated when the first-order rotation it asks for is
-// small: |lambda~_j - lambda~_i| > max(tau, rho (|S_ij| + |lambda~_j| |R_ij|)),
-// rho = 1024 by default.
-// Runs of neighbours that are not separated form clusters; each cluster gets
+// small: |lambda~_j - lambda~_i| > max(tau, rho (|S_ij| + |lambda~_j| |R_ij|)).
+// Runs of neighbours that are not separated for the cluster factor rho (1024
+// by default) form clusters; each cluster gets
 // a Rayleigh-Ritz rotation from its FP64-accurate Gram and projection blocks
 // (after Ogita and Aishima's treatment of clustered eigenvalues, 2019), and
 // the first-order terms coupling it to other columns rotate with it.
@@ -123,7 +123,11 @@ SK_DEV Blocks blocks(int i, int j, int m, long long ld, const double* __restrict
 }
 
 // first-order rotation the pair (i, j) asks for is small enough for the
-// correction formula: |l_j - l_i| > max(tau, rho (|Sg_ij| + |l_j| |R_ij|))
+// correction formula: |l_j - l_i| > max(tau, rho (|Sg_ij| + |l_j| |R_ij|)).
+// Neighbours closer than that for the cluster factor rho form Rayleigh-Ritz
+// clusters; every other pair takes the first-order formula when it asks for a
+// rotation below 1/RHO1 (else E_ij = R_ij / 2, left to the next iteration).
+constexpr double RHO1 = 64.0;
 SK_DEV bool separated(double li, double lj, cplx Sg, cplx R, double tau, double rho) {
     const double need = rho * (hypot(Sg.r, Sg.i) + fabs(lj) * hypot(R.r, R.i));
     return fabs(lj - li) > fmax(tau, need);
@@ -301,8 +305,8 @@ SK_DEV int basis_of(int i, int m, const int* __restrict__ cid, const double* __r
 // m x m planes of Et (E~11 real, imag, E~21 real, imag).
 __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg, const double* __restrict__ T,
                                      const double* __restrict__ lt, const int* __restrict__ cid,
-                                     const double* __restrict__ Vc, double tau, double rho,
-                                     double* __restrict__ Et, RefineScalars* sc) {
+                                     const double* __restrict__ Vc, double tau, double* __restrict__ Et,
+                                     RefineScalars* sc) {
     const long long ld = n, mm = (long long)m * m;
     double emax = 0.0, rn2 = 0.0;
     unsigned int close = 0;
@@ -330,7 +334,7 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
         const cplx R = {(i == j ? 1.0 : 0.0) - G.r, -G.i};
         cplx E11, E21;
         rn2 += R.r * R.r + R.i * R.i;
-        if (i != j && !same && separated(li, lj, Sg, R, tau, rho)) {
+        if (i != j && !same && separated(li, lj, Sg, R, tau, RHO1)) {
             const double d = lj - li;
             E11 = {(Sg.r + lj * R.r) / d, (Sg.i + lj * R.i) / d};
             const double a = hypot(E11.r, E11.i);
@@ -341,7 +345,7 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
         }
         const cplx num = {Sf.r - lj * F.r, Sf.i - lj * F.i};
         const double d2 = lj + li;
-        if (fabs(d2) > fmax(tau, rho * (hypot(Sf.r, Sf.i) + fabs(lj) * hypot(F.r, F.i)))) {
+        if (fabs(d2) > fmax(tau, RHO1 * (hypot(Sf.r, Sf.i) + fabs(lj) * hypot(F.r, F.i)))) {
             E21 = cscale(num, 1.0 / d2);
             const double a = hypot(E21.r, E21.i);
             if (a > emax) {
@@ -532,7 +536,7 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
         refine_rr_kernel<<<m, 32, 0, st>>>(m, n, w.Wg, w.T, w.close, w.lt, w.cid, w.Vc, w.nbig);
         // E~ lives in the AM buffer (free once T is formed)
         refine_etilde_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, n, w.Wg, w.T, w.lt, w.cid, w.Vc, tau,
-                                                                      rho, w.AM, w.sc);
+                                                                      w.AM, w.sc);
         refine_u_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, w.cid, w.Vc, w.AM, w.U, w.sc);
         count_launch(4);
         RefineScalars h{};

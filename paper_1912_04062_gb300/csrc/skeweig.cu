@@ -381,6 +381,129 @@ int skew_eig(int n, const double* A, int lda, int nev, double* lambda, double* Z
     return rc ? rc : info;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Argument check of a batch: -1 count, then the argument number of the
+// first invalid per-matrix entry (2 n, 3 A, 4 lda, 5 nev, 6 lambda, 7 Z).
+int batch_check(int count, const int* n, const double* const* A, const int* lda, const int* nev,
+                double* const* lambda, double* const* Zre, double* const* Zim, const skew_opts* opts) {
+    if (count < 0) return -1;
+    if (count == 0) return 0;
+    if (!n) return -2;
+    if (!A) return -3;
+    if (!lda) return -4;
+    if (!nev) return -5;
+    if (!lambda) return -6;
+    if ((Zre == nullptr) != (Zim == nullptr)) return -7;
+    for (int b = 0; b < count; b++) {
+        const int rc = check_args(n[b], A[b], lda[b], nev[b], lambda[b], Zre ? Zre[b] : nullptr,
+                                  Zim ? Zim[b] : nullptr);
+        if (rc) return rc - 1;  // -1 .. -6 -> -2 .. -7
+    }
+    if (opts && opts->mode == SKEW_MODE_MIXED_INT8) return SKEW_ERR_UNSUPPORTED;
+    return 0;
+}
+
+struct BatchPlan {
+    std::vector<BatchProblem> small;
+    std::vector<int> large;
+    size_t small_bytes, large_bytes;
+};
+
+BatchPlan plan_batch(int count, const int* n, const double* const* A, const int* lda, const int* nev,
+                     double* const* lambda, double* const* Zre, double* const* Zim, const skew_opts* opts,
+                     int* d_info) {
+    BatchPlan bp{};
+    bp.large_bytes = 0;
+    for (int b = 0; b < count; b++) {
+        const bool vec = Zre && Zre[b];
+        if (n[b] < 2 || nev[b] == 0) continue;
+        if (n[b] <= BATCH_SMALL_MAX) {
+            BatchProblem q{};
+            q.n = n[b];
+            q.nev = nev[b];
+            q.lda = lda[b];
+            q.A = A ? A[b] : nullptr;
+            q.lambda = lambda ? lambda[b] : nullptr;
+            q.Zre = vec ? Zre[b] : nullptr;
+            q.Zim = vec ? Zim[b] : nullptr;
+            q.info = d_info ? d_info + b : nullptr;
+            bp.small.push_back(q);
+        } else {
+            bp.large.push_back(b);
+            const size_t by = plan_bytes(n[b], nev[b], opts, vec);
+            bp.large_bytes = by > bp.large_bytes ? by : bp.large_bytes;
+        }
+    }
+    bp.small_bytes = bp.small.empty() ? 0 : batched_small_ws((int)bp.small.size(), bp.small.data());
+    return bp;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t skew_eig_batched_workspace_size(int count, const int* n, const int* nev, const skew_opts* opts) {
+    if (count <= 0 || !n || !nev) return 256;
+    // sizes only: pointers are not looked at; every matrix is taken with vectors
+    std::vector<double*> fake((size_t)count, reinterpret_cast<double*>(16));
+    std::vector<int> lda((size_t)count);
+    for (int b = 0; b < count; b++) lda[(size_t)b] = n[b] > 1 ? n[b] : 1;
+    BatchPlan bp = plan_batch(count, n, fake.data(), lda.data(), nev, fake.data(), fake.data(), fake.data(), opts,
+                              nullptr);
+    return align_up(bp.small_bytes) + align_up(bp.large_bytes) + 256;
+}
+
+int skew_eig_batched_ex(int count, const int* n, const double* const* A, const int* lda, const int* nev,
+                        double* const* lambda, double* const* Z_re, double* const* Z_im, const skew_opts* opts,
+                        void* workspace, size_t ws_bytes, int* d_info, void* stream) {
+    int rc = batch_check(count, n, A, lda, nev, lambda, Z_re, Z_im, opts);
+    if (rc) return rc;
+    if (count == 0) return 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (d_info) {
+        if (const cudaError_t e = cudaMemsetAsync(d_info, 0, sizeof(int) * (size_t)count, st)) return cuda_fail(e);
+    }
+    BatchPlan bp = plan_batch(count, n, A, lda, nev, lambda, Z_re, Z_im, opts, d_info);
+    const size_t need = align_up(bp.small_bytes) + align_up(bp.large_bytes);
+    if ((bp.small_bytes || bp.large_bytes) && (!workspace || ws_bytes < need)) return SKEW_ERR_WORKSPACE;
+    char* base = static_cast<char*>(workspace);
+    if (!bp.small.empty()) {
+        rc = batched_small(st, (int)bp.small.size(), bp.small.data(), base, bp.small_bytes, 5);
+        if (rc) return rc;
+    }
+    char* lws = base + align_up(bp.small_bytes);
+    for (int b : bp.large) {
+        const bool vec = Z_re && Z_re[b];
+        rc = run_solve(st, n[b], A[b], lda[b], nev[b], lambda[b], vec ? Z_re[b] : nullptr, vec ? Z_im[b] : nullptr,
+                       n[b], opts, lws, bp.large_bytes, d_info ? d_info + b : nullptr);
+        if (rc) return rc;
+    }
+    return cuda_ok(cudaGetLastError());
+}
+
+int skew_eig_batched(int count, const int* n, const double* const* A, const int* lda, const int* nev,
+                     double* const* lambda, double* const* Z_re, double* const* Z_im, const skew_opts* opts,
+                     void* stream) {
+    int rc = batch_check(count, n, A, lda, nev, lambda, Z_re, Z_im, opts);
+    if (rc) return rc;
+    if (count == 0) return 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BatchPlan bp = plan_batch(count, n, A, lda, nev, lambda, Z_re, Z_im, opts, nullptr);
+    const size_t need = align_up(bp.small_bytes) + align_up(bp.large_bytes);
+    if (need == 0) return 0;
+    void* ws = nullptr;
+    if (cudaMallocAsync(&ws, need, st) != cudaSuccess) {
+        cudaGetLastError();
+        return SKEW_ERR_NOMEM;
+    }
+    rc = skew_eig_batched_ex(count, n, A, lda, nev, lambda, Z_re, Z_im, opts, ws, need, nullptr, stream);
+    cudaFreeAsync(ws, st);
+    return rc;
+}
+
 int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda, double* Z_re, double* Z_im,
                   const skew_opts* opts, void* stream) {
     int rc = check_args(n, A, lda, nev, lambda, Z_re, Z_im);

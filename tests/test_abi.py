@@ -101,3 +101,25 @@ def test_kernel_timing_switch_is_host_side(sk):
     assert (ms, fl, k) == (0.0, 0.0, 0)
     assert L.skew_kernel_timing_read(7, None, None, None) == -1
     assert L.skew_kernel_timing(0) == 0
+
+
+def test_batched_argument_checks_are_host_side(sk):
+    L = sk.lib()
+    IA = ctypes.c_int * 2
+    PA = ctypes.c_void_p * 2
+    fake = PA(16, 16)
+    nul = ctypes.c_void_p(0)
+
+    def call(n=(4, 4), lda=(4, 4), nev=(1, 1), count=2, Zr=None, Zi=None):
+        return L.skew_eig_batched(count, IA(*n), fake, IA(*lda), IA(*nev), fake, Zr, Zi, None, nul)
+    assert call(count=-1) == -1
+    assert call(n=(4, -1)) == -2
+    assert call(lda=(4, 3)) == -4
+    assert call(nev=(1, 3)) == -5
+    assert call(Zr=fake, Zi=None) == -7
+    assert L.skew_eig_batched(0, None, None, None, None, None, None, None, None, nul) == 0
+    # workspace grows with the batch and covers the largest single solve
+    small = sk.lib().skew_eig_batched_workspace_size(2, IA(40, 100), IA(20, 50), None)
+    big = sk.lib().skew_eig_batched_workspace_size(2, IA(40, 400), IA(20, 200), None)
+    assert 0 < small < big
+    assert big >= sk.workspace_size(400, 200)
