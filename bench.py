@@ -234,9 +234,9 @@ def run_ours(args, ws, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = sk.launch_count() - l0
-    ktime = {k: sk.kernel_timing_read(v) for k, v in
-             (("ozaki_refine", sk.SKEW_KERNEL_OZAKI_REFINE), ("ozaki_reduce", sk.SKEW_KERNEL_OZAKI),
-              ("split", sk.SKEW_KERNEL_SPLIT))}
+    kinds = {name: sk.kernel_timing_read(i) for i, name in enumerate(sk.KERNEL_KINDS)}
+    ktime = {"ozaki_refine": kinds["ozaki_refine"], "ozaki_reduce": kinds["ozaki_product"],
+             "split": kinds["split_product"]}
     sk.kernel_timing(False)
     clocks = clk.stop()
     barrier(ws)
@@ -309,7 +309,7 @@ def run_ours(args, ws, rank, local):
         tms, tfl, tl = ktime[top]
         achieved = tfl / (tms * 1e-3) / 1e12
         name = {"ozaki_refine": "ozaki_gemm_kernel (refinement products, n x n x n)",
-                "ozaki_reduce": "ozaki_gemm_kernel (band-reduction products)",
+                "ozaki_reduce": "ozaki_gemm_kernel (band-reduction and Q_band products)",
                 "split": "umma_gemm_kernel (BF16 split products)"}[top]
         roof = {"bound": "tensor", "achieved": achieved, "peak": PEAKS["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "frac": achieved / PEAKS["bf16_tflops_sustained"],
@@ -369,6 +369,7 @@ def run_ours(args, ws, rank, local):
                           "l2": "inputs larger than L2 (A = %.1f GB)" % (8 * n * n / 1e9),
                           "parallelism": "replicas" if ws > 1 else "single"},
                "tflops_nominal": total_F / (ms * 1e-3) / 1e12,
+               "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kinds.items()},
                "stages_ms": {k: round(v, 3) for k, v in stage_ms.items()},
                "accuracy": acc, "fp64_form": fp64, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clocks}

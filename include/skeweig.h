@@ -282,18 +282,28 @@ int skew_refine_slices(int* slices, int* uslices, int cap);
 long long skew_launch_count(void);
 
 /* Kernel timing (diagnostics).  skew_kernel_timing(1) clears the record and
- * from then on brackets every launch of the tensor-core product kernels with
- * CUDA events on the stream the launch goes to (adds two event records per
- * launch, at most 16384 launches are recorded); skew_kernel_timing(0) stops.
+ * from then on brackets the library's launches (one record per launch or per
+ * group of launches of one kind) with CUDA events on the stream they go to
+ * (two event records each, at most 16384 records); skew_kernel_timing(0) stops.
  * Not thread-safe: one solving thread per process while it is on.
- * skew_kernel_timing_read sums, over the recorded launches of one kind, the
- * event-measured time (*ms), the algorithmic flops (*flops: 2 M N K per kept
- * slice or plane product, over the outputs the launch writes) and the launch
- * count; it waits for the recorded events.  Returns 0, -1 for an unknown
- * kind, or SKEW_ERR_CUDA. */
-#define SKEW_KERNEL_OZAKI 0 /* FP64-accurate digit-slice product (ozaki_gemm_kernel) */
-#define SKEW_KERNEL_SPLIT 1 /* BF16x3 / BF16x6 split product (umma_gemm_kernel) */
+ * skew_kernel_timing_read sums, over the records of one kind, the
+ * event-measured time (*ms), the algorithmic flops (*flops; for the two
+ * product kinds: 2 M N K per kept slice or plane product over the outputs the
+ * launch writes, 0 for the others) and the record count; it waits for the
+ * recorded events.  Returns 0, -1 for an unknown kind, or SKEW_ERR_CUDA. */
+#define SKEW_KERNEL_OZAKI 0        /* ozaki_gemm_kernel outside the refinement (reduction, Q_band) */
+#define SKEW_KERNEL_SPLIT 1        /* BF16x3 / BF16x6 split product (umma_gemm_kernel) */
 #define SKEW_KERNEL_OZAKI_REFINE 2 /* ozaki_gemm_kernel inside the refinement (n x n x n) */
+#define SKEW_KERNEL_SLICE_SPLIT 3  /* operand splitters (digit slices, BF16 planes) */
+#define SKEW_KERNEL_PANEL_QR 4     /* cooperative panel QR */
+#define SKEW_KERNEL_GEMM_F64 5     /* FP64 GEMM-type kernels (SYMM, rank-2k, W build, T, FP64 Q_band) */
+#define SKEW_KERNEL_CHASE 6        /* bulge chase */
+#define SKEW_KERNEL_BISECT 7       /* bisection */
+#define SKEW_KERNEL_INVIT 8        /* inverse iteration */
+#define SKEW_KERNEL_QTRD 9         /* Q_trd back-transform */
+#define SKEW_KERNEL_REFINE_AUX 10  /* O(n^2) kernels of the refinement */
+#define SKEW_KERNEL_OTHER 11       /* copies, conversions, D map, output */
+#define SKEW_KERNEL_KINDS 12
 int skew_kernel_timing(int enable);
 int skew_kernel_timing_read(int kind, double* ms, double* flops, long long* launches);
 

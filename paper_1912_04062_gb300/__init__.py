@@ -331,6 +331,17 @@ def refine_slices():
 SKEW_KERNEL_OZAKI = 0
 SKEW_KERNEL_SPLIT = 1
 SKEW_KERNEL_OZAKI_REFINE = 2
+SKEW_KERNEL_SLICE_SPLIT = 3
+SKEW_KERNEL_PANEL_QR = 4
+SKEW_KERNEL_GEMM_F64 = 5
+SKEW_KERNEL_CHASE = 6
+SKEW_KERNEL_BISECT = 7
+SKEW_KERNEL_INVIT = 8
+SKEW_KERNEL_QTRD = 9
+SKEW_KERNEL_REFINE_AUX = 10
+SKEW_KERNEL_OTHER = 11
+KERNEL_KINDS = ["ozaki_product", "split_product", "ozaki_refine", "slice_split", "panel_qr", "gemm_f64",
+                "chase", "bisect", "invit", "qtrd", "refine_aux", "other"]
 
 
 def kernel_timing(enable: bool) -> None:

@@ -223,12 +223,14 @@ cudaError_t apply_qtrd_t(cudaStream_t st, int n, int b, const double* Vtrd, cons
     if (sizeof(T) == sizeof(double)) {
         const size_t smem = sizeof(T) * (size_t)QLD * 64;
         cudaFuncSetAttribute(qtrd_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        KtScope kt(st, KT_QTRD);
         qtrd_smem_kernel<T><<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
         count_launch();
         return cudaGetLastError();
     }
     const size_t smem = sizeof(T) * ((size_t)QLD * 64 + (size_t)QELL * QB + QELL);
     cudaFuncSetAttribute(qtrd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    KtScope kt(st, KT_QTRD);
     qtrd_kernel<T><<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
     count_launch();
     return cudaGetLastError();
@@ -263,6 +265,7 @@ int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw, const d
         const int o = (p + 1) * b, m = n - o;
         const double* Tp = Tfac + (size_t)p * b * b;
         double* Zo = Z + o;
+        KtScope kt(st, KT_GEMM_F64);
         if (panel_v(st, n, b, p, W, ldw, w.V, n) != cudaSuccess) return SKEW_ERR_CUDA;
         if (gemm(st, true, false, b, k, m, 1.0, w.V, n, Zo, ldz, 0.0, w.Y, b) != cudaSuccess) return SKEW_ERR_CUDA;
         if (gemm(st, false, false, b, k, b, 1.0, Tp, b, w.Y, b, 0.0, w.Y2, b) != cudaSuccess) return SKEW_ERR_CUDA;
@@ -333,8 +336,11 @@ int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, c
             const int o = (p + 1) * b, m = n - o;
             const double* Tp = Tfac + (size_t)p * b * b;
             double* Zo = Z + o;
-            if (panel_v(st, n, b, p, W, ldw, V, n) != cudaSuccess) return SKEW_ERR_CUDA;
-            if (gemm(st, false, false, m, b, b, 1.0, V, n, Tp, b, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
+            {
+                KtScope kt(st, KT_GEMM_F64);
+                if (panel_v(st, n, b, p, W, ldw, V, n) != cudaSuccess) return SKEW_ERR_CUDA;
+                if (gemm(st, false, false, m, b, b, 1.0, V, n, Tp, b, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
+            }
             // Yt = Z_o^T V (k x b), then Z_o -= (V T) Yt^T
             int rc = split_gemm(st, k, b, m, 1.0, Zo, ldz, 1, 0, V, n, 1, 0.0, Yt, k, 0, gws, gsz, status, planes);
             if (rc) return rc;
@@ -347,29 +353,32 @@ int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, c
         const int p0 = pe - QG + 1 > 0 ? pe - QG + 1 : 0, g = pe - p0 + 1, gb = g * b;
         const int o = (p0 + 1) * b, m = n - o;
         double* Zo = Z + o;
-        // V of the group (m x gb, ld n): panel p0 + j starts at row j b
-        if (cudaMemsetAsync(V, 0, sizeof(double) * (size_t)n * gb, st) != cudaSuccess) return SKEW_ERR_CUDA;
-        for (int j = 0; j < g; j++)
-            if (panel_v(st, n, b, p0 + j, W, ldw, V + (size_t)j * b * n + (size_t)j * b, n) != cudaSuccess)
-                return SKEW_ERR_CUDA;
-        // T of the group
-        tgroup_init_kernel<<<(gb * gb + 255) / 256, 256, 0, st>>>(g, b, Tfac + (size_t)p0 * b * b, Tg);
-        count_launch();
-        if (g > 1) {
-            if (gemm(st, true, false, gb, gb, m, 1.0, V, n, V, n, 0.0, G, gb) != cudaSuccess) return SKEW_ERR_CUDA;
-            for (int j = 1; j < g; j++) {
-                const int jb = j * b;
-                const double* Tj = Tfac + (size_t)(p0 + j) * b * b;
-                // tmp = (V_1..j-1^T V_j) T_j, then T[0:jb, jb:jb+b] = -T[0:jb, 0:jb] tmp
-                if (gemm(st, false, false, jb, b, b, 1.0, G + (size_t)jb * gb, gb, Tj, b, 0.0, tmp, gb) !=
-                    cudaSuccess)
+        {
+            KtScope kt(st, KT_GEMM_F64);  // V, T and V T of the group
+            // V of the group (m x gb, ld n): panel p0 + j starts at row j b
+            if (cudaMemsetAsync(V, 0, sizeof(double) * (size_t)n * gb, st) != cudaSuccess) return SKEW_ERR_CUDA;
+            for (int j = 0; j < g; j++)
+                if (panel_v(st, n, b, p0 + j, W, ldw, V + (size_t)j * b * n + (size_t)j * b, n) != cudaSuccess)
                     return SKEW_ERR_CUDA;
-                if (gemm(st, false, false, jb, b, jb, -1.0, Tg, gb, tmp, gb, 0.0, Tg + (size_t)jb * gb, gb) !=
-                    cudaSuccess)
-                    return SKEW_ERR_CUDA;
+            // T of the group
+            tgroup_init_kernel<<<(gb * gb + 255) / 256, 256, 0, st>>>(g, b, Tfac + (size_t)p0 * b * b, Tg);
+            count_launch();
+            if (g > 1) {
+                if (gemm(st, true, false, gb, gb, m, 1.0, V, n, V, n, 0.0, G, gb) != cudaSuccess) return SKEW_ERR_CUDA;
+                for (int j = 1; j < g; j++) {
+                    const int jb = j * b;
+                    const double* Tj = Tfac + (size_t)(p0 + j) * b * b;
+                    // tmp = (V_1..j-1^T V_j) T_j, then T[0:jb, jb:jb+b] = -T[0:jb, 0:jb] tmp
+                    if (gemm(st, false, false, jb, b, b, 1.0, G + (size_t)jb * gb, gb, Tj, b, 0.0, tmp, gb) !=
+                        cudaSuccess)
+                        return SKEW_ERR_CUDA;
+                    if (gemm(st, false, false, jb, b, jb, -1.0, Tg, gb, tmp, gb, 0.0, Tg + (size_t)jb * gb, gb) !=
+                        cudaSuccess)
+                        return SKEW_ERR_CUDA;
+                }
             }
+            if (gemm(st, false, false, m, gb, gb, 1.0, V, n, Tg, gb, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
         }
-        if (gemm(st, false, false, m, gb, gb, 1.0, V, n, Tg, gb, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
         // Yt = Z_o^T V (k x gb), then Z_o -= (V T) Yt^T
         int rc = ozaki_gemm(st, k, gb, m, 1.0, Zo, ldz, 1, 1.0, V, n, 1, 1.0, 0.0, Yt, k, gws, gsz, status);
         if (rc) return rc;

@@ -300,16 +300,22 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         if (cudaMemsetAsync(w.bar, 0, sizeof(unsigned), st) != cudaSuccess) return SKEW_ERR_CUDA;
         int ldp = ldw, nbv = b, mm = m;
         void* args[] = {&mm, &nbv, &panel, &ldp, &taup, &w.part, &w.rowbuf, &w.bar, &d_status, &rpc};
-        if (cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st) !=
-            cudaSuccess)
-            return SKEW_ERR_LAUNCH;
+        {
+            KtScope kt(st, KT_PANEL_QR);
+            if (cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st) !=
+                cudaSuccess)
+                return SKEW_ERR_LAUNCH;
+        }
         count_launch();
         // ---- T factor (Eq. 7)
-        panel_v_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, panel, ldw, w.V, n);
-        count_launch();
-        if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.V, n, 0.0, w.G, b) != cudaSuccess) return SKEW_ERR_CUDA;
-        tfactor_kernel<<<1, 128, sizeof(double) * (b * b + b), st>>>(b, taup, w.G, Tp);
-        count_launch();
+        {
+            KtScope kt(st, KT_GEMM_F64);
+            panel_v_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, panel, ldw, w.V, n);
+            count_launch();
+            if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.V, n, 0.0, w.G, b) != cudaSuccess) return SKEW_ERR_CUDA;
+            tfactor_kernel<<<1, 128, sizeof(double) * (b * b + b), st>>>(b, taup, w.G, Tp);
+            count_launch();
+        }
         // ---- a3: P = A22 V (skew, lower triangle only)
         if (planes == REDUCE_F64ACC) {
             int rc = ozaki_gemm(st, m, b, m, 1.0, A22, 0, ldw, 1.0, w.V, n, 1, 1.0, 0.0, w.Pm, n, gws, gsz, d_status,
@@ -319,17 +325,22 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
             int rc = split_gemm(st, m, b, m, 1.0, A22, 0, ldw, 1, w.V, n, 1, 0.0, w.Pm, n, 0, gws, gsz, d_status,
                                 planes);
             if (rc) return rc;
-        } else if (skew_symm(st, m, b, A22, ldw, w.V, n, w.Pm, n) != cudaSuccess) {
-            return SKEW_ERR_CUDA;
+        } else {
+            KtScope kt(st, KT_GEMM_F64);
+            if (skew_symm(st, m, b, A22, ldw, w.V, n, w.Pm, n) != cudaSuccess) return SKEW_ERR_CUDA;
         }
-        // ---- a4: Y = P T; C = T^T (V^T Y); W = Y - V C / 2
-        if (gemm(st, false, false, m, b, b, 1.0, w.Pm, n, Tp, b, 0.0, w.Y, n) != cudaSuccess) return SKEW_ERR_CUDA;
-        if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.Y, n, 0.0, w.C1, b) != cudaSuccess) return SKEW_ERR_CUDA;
-        if (gemm(st, true, false, b, b, b, 1.0, Tp, b, w.C1, b, 0.0, w.C2, b) != cudaSuccess) return SKEW_ERR_CUDA;
-        if (gemm(st, false, false, m, b, b, -0.5, w.V, n, w.C2, b, 1.0, w.Y, n) != cudaSuccess) return SKEW_ERR_CUDA;
-        // ---- a5: A22 += [V W][W -V]^T (lower tiles)
-        concat_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, w.V, w.Y, n, w.X2, w.Y2);
-        count_launch();
+        {
+            // ---- a4: Y = P T; C = T^T (V^T Y); W = Y - V C / 2
+            KtScope kt(st, KT_GEMM_F64);
+            if (gemm(st, false, false, m, b, b, 1.0, w.Pm, n, Tp, b, 0.0, w.Y, n) != cudaSuccess) return SKEW_ERR_CUDA;
+            if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.Y, n, 0.0, w.C1, b) != cudaSuccess) return SKEW_ERR_CUDA;
+            if (gemm(st, true, false, b, b, b, 1.0, Tp, b, w.C1, b, 0.0, w.C2, b) != cudaSuccess) return SKEW_ERR_CUDA;
+            if (gemm(st, false, false, m, b, b, -0.5, w.V, n, w.C2, b, 1.0, w.Y, n) != cudaSuccess)
+                return SKEW_ERR_CUDA;
+            // ---- a5: A22 += [V W][W -V]^T (lower tiles)
+            concat_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, w.V, w.Y, n, w.X2, w.Y2);
+            count_launch();
+        }
         if (planes == REDUCE_F64ACC) {
             // tiles on or below the diagonal (the upper triangle of W is never read)
             int rc = ozaki_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 1.0, w.Y2, 1, n, 1.0, 1.0, A22, ldw, gws, gsz,
@@ -339,8 +350,9 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
             int rc = split_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 0, w.Y2, 1, n, 1.0, A22, ldw, 1, gws, gsz, d_status,
                                 planes);
             if (rc) return rc;
-        } else if (gemm_lower_tiles(st, m, 2 * b, w.X2, n, w.Y2, n, A22, ldw) != cudaSuccess) {
-            return SKEW_ERR_CUDA;
+        } else {
+            KtScope kt(st, KT_GEMM_F64);
+            if (gemm_lower_tiles(st, m, 2 * b, w.X2, n, w.Y2, n, A22, ldw) != cudaSuccess) return SKEW_ERR_CUDA;
         }
     }
     return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;

@@ -230,6 +230,7 @@ int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha, do
         int G = occ * device_sms();
         if (G > nsw) G = nsw;
         void* args[] = {&n, &AB, &ldab, &alpha, &Vtrd, &tautrd, &prog, &d_status};
+        KtScope kt(st, KT_CHASE);
         if (cudaLaunchCooperativeKernel((void*)chase_kernel, dim3(G), dim3(CH_THREADS), args, smem, st) != cudaSuccess)
             return SKEW_ERR_LAUNCH;
         count_launch();

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include "../../include/skeweig.h"
 
@@ -92,6 +93,19 @@ int split_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double*
 // C = alpha * (sa A)(sb B)^T + beta * C, A[i,k] = A[i*a_rs + k*a_ks],
 // B[j,k] = B[j*b_rs + k*b_ks], C column-major.
 size_t ozaki_gemm_ws(int M, int N, int K);
+// An operand cut into its 8 digit slices (planes of Rp x Kp BF16, row-major)
+// with per-row exponents; reusable across products.
+struct OzOperand {
+    __nv_bfloat16* d;
+    int* e;
+    int rows, K;
+    long long Rp, Kp;
+};
+size_t ozaki_operand_ws(int rows, int K);
+int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long rs, long long ks, double sgn, int skew,
+                void* ws, size_t ws_bytes, OzOperand* op);
+int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, double alpha, double beta, double* C,
+                   long long ldc, int* status, int slices = 8, int lower = 0);
 // a_skew: A is the skew matrix of the strict lower triangle stored column-major
 // with leading dimension a_ks (a_rs unused).  slices (1..8): digit slices kept,
 // accuracy about 2^-7 slices relative to |a_r|max |b_c|max per term.  lower:
@@ -147,12 +161,36 @@ int cuda_fail(cudaError_t e);
 inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? 0 : cuda_fail(e); }
 // Kernel timing (diagnostics): when switched on, kt_begin / kt_end bracket a
 // launch with CUDA events on its stream and record its algorithmic flops.
-enum { KT_OZAKI = 0, KT_SPLIT = 1, KT_OZAKI_REFINE = 2, KT_KINDS = 3 };
+enum {
+    KT_OZAKI = 0,         // digit-slice products outside the refinement
+    KT_SPLIT = 1,         // BF16 plane products (split modes)
+    KT_OZAKI_REFINE = 2,  // digit-slice products of the refinement
+    KT_SLICE_SPLIT = 3,   // operand splitters (digit slices, BF16 planes)
+    KT_PANEL_QR = 4,      // cooperative panel QR
+    KT_GEMM_F64 = 5,      // FP64 GEMM-type kernels (SYMM, rank-2k, W build, T factors, FP64 Q_band)
+    KT_CHASE = 6,         // bulge chase
+    KT_BISECT = 7,        // bisection
+    KT_INVIT = 8,         // inverse iteration
+    KT_QTRD = 9,          // Q_trd back-transform
+    KT_REFINE_AUX = 10,   // O(n^2) kernels of the refinement
+    KT_OTHER = 11,        // copies, conversions, D map, output
+    KT_KINDS = 12
+};
 // kind recorded for ozaki_gemm launches (the refinement sets KT_OZAKI_REFINE
 // for its n x n x n products while it runs)
 extern int g_kt_ozaki_kind;
 int kt_begin(cudaStream_t st);
 void kt_end(cudaStream_t st, int slot, int kind, double flops);
+// Brackets the launches issued in its lifetime as one timed record of `kind`.
+struct KtScope {
+    cudaStream_t st;
+    int slot, kind;
+    double flops;
+    KtScope(cudaStream_t s, int k, double f = 0.0) : st(s), slot(kt_begin(s)), kind(k), flops(f) {}
+    ~KtScope() { kt_end(st, slot, kind, flops); }
+    KtScope(const KtScope&) = delete;
+    KtScope& operator=(const KtScope&) = delete;
+};
 // elements (r, c) of an M x N result with c <= r (the lower triangle)
 inline double lower_count(double M, double N) {
     return N <= M ? N * (N + 1) / 2 + (M - N) * N : M * (M + 1) / 2;

@@ -25,10 +25,13 @@
 //
 // Kernel: 128 x 64 output tile per CTA, 320 threads: warps 0-7 drain TMEM
 // (warp w: lanes 32 (w & 3).. = rows, columns 32 (w >> 2)..) and accumulate;
-// warp 8 issues TMA loads (the B digit
-// slices of a 128-wide K chunk stay resident, A slices stream through two
-// stages); warp 9 issues the MMAs.  TMEM holds one group of two chunks, so the
-// MMAs of the next group start once the epilogue has drained the last one.
+// warp 8 issues TMA loads, warp 9 issues the MMAs.  K advances in chunks of 64
+// (one 128-byte swizzle atom).  All B digit slices of a chunk sit in one of two
+// buffers, so the next chunk's B loads while the current one is multiplied; A
+// digit slices stream through a ring of NA one-slice stages.  Within a chunk,
+// pass i multiplies A slice i with B slices 0 .. S-1-i.
+// TMEM holds one level group (4 chunks = 256 of K), so the MMAs of the next
+// group start once the epilogue has drained it.
 // With `lower` set, tiles wholly above the diagonal (every column index above
 // every row index) are skipped: for symmetric or skew results whose upper
 // triangle is not read.
@@ -50,15 +53,15 @@ namespace {
 
 constexpr int OM = 128;      // tile rows
 constexpr int ON = 64;       // tile columns
-constexpr int OKC = 128;     // K per chunk (two 64-wide swizzle atoms; the last chunk may hold one)
-constexpr int OKA = 64;      // K per swizzle atom; K is padded to a multiple of it
+constexpr int OKA = 64;      // K per chunk = one 64-wide swizzle atom; K is padded to a multiple of it
+constexpr int NA = 6;        // A stages (one digit slice of one chunk each)
+constexpr int GRP = 4;       // chunks per exact level group (256 of K)
 constexpr int SL = 8;        // digit slices per operand
 constexpr int OT = 320;      // threads per CTA: 8 epilogue warps, TMA warp, MMA warp
 constexpr int OEPI = 256;    // epilogue threads
 
 struct OzParams {
-    int M, N, nchunks;
-    int katoms;              // 64-wide K atoms in all (the last chunk holds one when odd)
+    int M, N, nchunks;       // nchunks: 64-wide K chunks
     int Mp, Np;              // padded row counts of the slice planes
     int mt, nt;              // output tiles along M and N
     const int* ea;           // row exponents of A (M)
@@ -72,11 +75,13 @@ struct OzParams {
 };
 
 struct OzSmem {
-    static constexpr uint32_t B_ATOM = ON * 128;          // 64 rows x 128 B
-    static constexpr uint32_t A_ATOM = OM * 128;          // 128 rows x 128 B
-    static constexpr uint32_t B_BYTES = SL * 2 * B_ATOM;  // all slices of a chunk
-    static constexpr uint32_t A_STAGE = 2 * A_ATOM;       // one slice of a chunk
-    static constexpr size_t bytes() { return 1024 + B_BYTES + 2 * A_STAGE + 8 * 10 + 16; }
+    static constexpr uint32_t B_ATOM = ON * 128;       // 64 rows x 128 B: one B slice of a chunk
+    static constexpr uint32_t A_ATOM = OM * 128;       // 128 rows x 128 B: one A slice of a chunk
+    static constexpr uint32_t B_SET = SL * B_ATOM;     // all B slices of a chunk (64 KB)
+    static constexpr uint32_t B_BYTES = 2 * B_SET;     // two chunks in flight
+    static constexpr uint32_t A_BYTES = NA * A_ATOM;   // 96 KB
+    static constexpr int NBAR = 4 + 2 * NA + 2;        // bfull/bfree per set, afull/aempty per stage, tfull, tempty
+    static constexpr size_t bytes() { return 1024 + B_BYTES + A_BYTES + 8 * NBAR + 16; }
 };
 
 // Digits of x 2^-e (|x| < 2^e) without FP64 arithmetic: the significand is
@@ -134,17 +139,18 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     extern __shared__ unsigned char oz_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) &
                                                          ~uintptr_t(1023));
-    unsigned char* sB = sm;                        // [slice][atom] 64 x 128 B
-    unsigned char* sA = sm + OzSmem::B_BYTES;      // [stage][atom] 128 x 128 B
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sA + 2 * OzSmem::A_STAGE);
-    uint64_t* bfull = bar + 0;
-    uint64_t* bfree = bar + 1;
-    uint64_t* afull = bar + 2;   // [2]
-    uint64_t* aempty = bar + 4;  // [2]
-    uint64_t* tfull = bar + 6;
-    uint64_t* tempty = bar + 7;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 8);
-    __shared__ int s_bi, s_bc, s_ai, s_ac;  // B chunks / A stages issued and consumed
+    unsigned char* sB = sm;                        // [set][slice] 64 x 128 B
+    unsigned char* sA = sm + OzSmem::B_BYTES;      // [stage] 128 x 128 B
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sA + OzSmem::A_BYTES);
+    uint64_t* bfull = bar;             // [2]
+    uint64_t* bfree = bar + 2;         // [2]
+    uint64_t* afull = bar + 4;         // [NA]
+    uint64_t* aempty = bar + 4 + NA;   // [NA]
+    uint64_t* tfull = bar + 4 + 2 * NA;
+    uint64_t* tempty = tfull + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 1);
+    // loads issued (producer) and consumed (MMA): B in chunks, A in slices
+    __shared__ int s_bi, s_bc, s_ai, s_ac;
 
     // tile order: groups of GM tile rows, column-major inside a group, so that
     // the CTAs resident at one time share few distinct A and B rows (one wave
@@ -159,12 +165,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     const int S = p.s;
 
     if (threadIdx.x == 0) {
-        mbar_init(bfull, 1);
-        mbar_init(bfree, 1);
-        mbar_init(&afull[0], 1);
-        mbar_init(&afull[1], 1);
-        mbar_init(&aempty[0], 1);
-        mbar_init(&aempty[1], 1);
+        for (int q = 0; q < 2; q++) {
+            mbar_init(&bfull[q], 1);
+            mbar_init(&bfree[q], 1);
+        }
+        for (int q = 0; q < NA; q++) {
+            mbar_init(&afull[q], 1);
+            mbar_init(&aempty[q], 1);
+        }
         mbar_init(tfull, 1);
         mbar_init(tempty, OEPI);
         fence_mbar_init();
@@ -185,24 +193,24 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 
     if (warp == 8) {
         if (lane == 0) {
-            // ---- TMA producer
+            // ---- TMA producer: per chunk, its B slices into buffer c & 1 (free
+            // once chunk c - 2 is multiplied), then its A slices (each waits
+            // for its ring stage)
             bool ok = true;
-            int bi = 0, ai = 0;
+            int ai = 0, bi = 0;
             for (int c = 0; c < nch && ok; c++) {
-                if (!(ok = mbar_wait(bfree, ((uint32_t)c & 1u) ^ 1u, p.status))) break;
-                const int na = min(2, p.katoms - 2 * c);  // atoms in this chunk
-                mbar_arrive_expect_tx(bfull, (uint32_t)(S * na) * OzSmem::B_ATOM);
+                const int q = c & 1;
+                if (!(ok = mbar_wait(&bfree[q], ((uint32_t)(c >> 1) & 1u) ^ 1u, p.status))) break;
+                mbar_arrive_expect_tx(&bfull[q], (uint32_t)S * OzSmem::B_ATOM);
                 for (int j = 0; j < S; j++)
-                    for (int a = 0; a < na; a++)
-                        tma_load_2d(sB + (j * 2 + a) * OzSmem::B_ATOM, &tmB, bfull, c * OKC + a * 64, j * p.Np + n0);
+                    tma_load_2d(sB + q * OzSmem::B_SET + j * OzSmem::B_ATOM, &tmB, &bfull[q], c * OKA,
+                                j * p.Np + n0);
                 bi++;
                 for (int i = 0; i < S; i++) {
-                    const int it = c * S + i, s = it & 1;
-                    if (!(ok = mbar_wait(&aempty[s], ((uint32_t)(it >> 1) & 1u) ^ 1u, p.status))) break;
-                    mbar_arrive_expect_tx(&afull[s], (uint32_t)na * OzSmem::A_ATOM);
-                    for (int a = 0; a < na; a++)
-                        tma_load_2d(sA + s * OzSmem::A_STAGE + a * OzSmem::A_ATOM, &tmA, &afull[s],
-                                    c * OKC + a * 64, i * p.Mp + m0);
+                    const int it = c * S + i, st = it % NA;
+                    if (!(ok = mbar_wait(&aempty[st], ((uint32_t)(it / NA) & 1u) ^ 1u, p.status))) break;
+                    mbar_arrive_expect_tx(&afull[st], OzSmem::A_ATOM);
+                    tma_load_2d(sA + st * OzSmem::A_ATOM, &tmA, &afull[st], c * OKA, i * p.Mp + m0);
                     ai++;
                 }
             }
@@ -214,39 +222,36 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             // ---- MMA issuer: level L accumulates in TMEM columns [64 L, 64 L + 64)
             constexpr uint32_t idesc = umma_idesc_bf16(OM, ON);
             bool ok = true;
-            int bc = 0, ac = 0;
+            int ac = 0, bc = 0;
             for (int c = 0; c < nch && ok; c++) {
-                const bool first = (c & 1) == 0;  // first chunk of a 256-wide K group
+                const bool first = (c % GRP) == 0;  // first chunk of a level group
                 if (first) {
-                    if (!(ok = mbar_wait(tempty, ((uint32_t)(c >> 1) & 1u) ^ 1u, p.status))) break;
+                    if (!(ok = mbar_wait(tempty, ((uint32_t)(c / GRP) & 1u) ^ 1u, p.status))) break;
                     tc_fence_after();
                 }
-                if (!(ok = mbar_wait(bfull, (uint32_t)c & 1u, p.status))) break;
+                const int q = c & 1;
+                if (!(ok = mbar_wait(&bfull[q], (uint32_t)(c >> 1) & 1u, p.status))) break;
                 bc++;
                 tc_fence_after();
-                const int nkk = 4 * min(2, p.katoms - 2 * c);  // 16-wide K steps in this chunk
                 for (int i = 0; i < S; i++) {
-                    const int it = c * S + i, s = it & 1;
-                    if (!(ok = mbar_wait(&afull[s], (uint32_t)(it >> 1) & 1u, p.status))) break;
+                    const int it = c * S + i, st = it % NA;
+                    if (!(ok = mbar_wait(&afull[st], (uint32_t)(it / NA) & 1u, p.status))) break;
                     ac++;
                     tc_fence_after();
+                    const uint64_t ad0 = umma_desc_sw128(smem_u32(sA + st * OzSmem::A_ATOM));
                     for (int j = 0; i + j < S; j++) {
                         const uint32_t dcol = tmem + (uint32_t)((i + j) * ON);
+                        const uint64_t bd0 = umma_desc_sw128(smem_u32(sB + q * OzSmem::B_SET + j * OzSmem::B_ATOM));
 #pragma unroll
-                        for (int kk = 0; kk < OKC / 16; kk++) {
-                            if (kk >= nkk) break;
-                            const int a = kk >> 2, k4 = kk & 3;
-                            const uint64_t ad =
-                                umma_desc_sw128(smem_u32(sA + s * OzSmem::A_STAGE + a * OzSmem::A_ATOM)) + 2 * k4;
-                            const uint64_t bd = umma_desc_sw128(smem_u32(sB + (j * 2 + a) * OzSmem::B_ATOM)) + 2 * k4;
+                        for (int kk = 0; kk < OKA / 16; kk++)
                             // level L is first written by the pair (0, L) at kk = 0 of a group
-                            umma_bf16(dcol, ad, bd, idesc, (!first || i > 0 || kk > 0) ? 1u : 0u);
-                        }
+                            umma_bf16(dcol, ad0 + 2 * kk, bd0 + 2 * kk, idesc, (!first || i > 0 || kk > 0) ? 1u : 0u);
                     }
-                    umma_commit(&aempty[s]);
+                    umma_commit(&aempty[st]);
                 }
-                umma_commit(bfree);
-                if (!first || c == nch - 1) umma_commit(tfull);
+                if (!ok) break;
+                umma_commit(&bfree[q]);
+                if (c % GRP == GRP - 1 || c == nch - 1) umma_commit(tfull);
             }
             s_bc = bc;
             s_ac = ac;
@@ -260,7 +265,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         for (int q = 0; q < EC; q++) { ah[q] = 0.f; al[q] = 0.f; }
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * EC);
         bool ok = true;
-        const int ngroups = (nch + 1) / 2;
+        const int ngroups = (nch + GRP - 1) / GRP;
         for (int grp = 0; grp < ngroups; grp++) {
             ok = mbar_wait(tfull, (uint32_t)grp & 1u, p.status);
             tc_fence_after();
@@ -319,23 +324,32 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     // after a timeout, let loads that were issued but never consumed land
     // before the shared memory is released (capped as well)
     if (threadIdx.x == 256) {
-        for (int c = s_bc; c < s_bi; c++) mbar_wait(bfull, (uint32_t)c & 1u, p.status, 1u << 16);
-        for (int it = s_ac; it < s_ai; it++) mbar_wait(&afull[it & 1], (uint32_t)(it >> 1) & 1u, p.status, 1u << 16);
+        for (int c = s_bc; c < s_bi; c++) mbar_wait(&bfull[c & 1], (uint32_t)(c >> 1) & 1u, p.status, 1u << 16);
+        for (int it = s_ac; it < s_ai; it++) mbar_wait(&afull[it % NA], (uint32_t)(it / NA) & 1u, p.status, 1u << 16);
     }
     __syncthreads();
     if (warp == 8) tmem_dealloc(tmem, 512);
 }
 
-// Row exponents when rows are contiguous in memory (sr == 1): one thread per
-// row walks k, so a warp reads 32 consecutive rows at each k.
-__global__ void oz_exp_cols_kernel(int rows, int K, const double* __restrict__ src, long long sk,
-                                   int* __restrict__ e) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-        double m = 0.0;
-        for (int k = 0; k < K; k++) m = fmax(m, fabs(src[r + (long long)k * sk]));
-        int ex = 0;
-        if (m > 0.0) frexp(m, &ex);
-        e[r] = ex;
+// Row maxima when rows are contiguous in memory (sr == 1): 32 rows x 256 k
+// per block, read along rows (coalesced); per-row maxima go to rowmax (ordered
+// bit patterns of non-negative doubles) with atomicMax.
+__global__ void oz_rowmax_cols_kernel(int rows, int K, const double* __restrict__ src, long long sk,
+                                      unsigned long long* __restrict__ rowmax) {
+    __shared__ double red[8][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int r = blockIdx.x * 32 + tx, k0 = blockIdx.y * 256;
+    double m = 0.0;
+    if (r < rows)
+        for (int kk = ty; kk < 256; kk += 8) {
+            const int k = k0 + kk;
+            if (k < K) m = fmax(m, fabs(src[r + (long long)k * sk]));
+        }
+    red[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0) {
+        for (int q = 1; q < 8; q++) m = fmax(m, red[q][tx]);
+        if (r < rows && m > 0.0) atomicMax(rowmax + r, (unsigned long long)__double_as_longlong(m));
     }
 }
 
@@ -491,66 +505,77 @@ inline int gridn(long long total) {
 
 }  // namespace
 
-size_t ozaki_gemm_ws(int M, int N, int K) {
-    const long long Kp = rup(K > 0 ? K : 1, OKA), Mp = rup(M > 0 ? M : 1, OM), Np = rup(N > 0 ? N : 1, ON);
-    return align_up((size_t)(SL * Mp * Kp * 2)) + align_up((size_t)(SL * Np * Kp * 2)) + align_up(sizeof(int) * Mp) +
-           align_up(sizeof(int) * Np) + align_up(sizeof(unsigned long long) * Mp) + 256;
+size_t ozaki_operand_ws(int rows, int K) {
+    const long long Kp = rup(K > 0 ? K : 1, OKA), Rp = rup(rows > 0 ? rows : 1, OM);
+    return align_up((size_t)(SL * Rp * Kp * 2)) + align_up(sizeof(int) * Rp) + align_up(sizeof(unsigned long long) * Rp);
 }
 
-// C = alpha * (sa A)(sb B)^T + beta C, A[i,k] = A[i*a_rs + k*a_ks], B[j,k] = B[j*b_rs + k*b_ks].
-int ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, long long a_rs, long long a_ks,
-               double sa, const double* B, long long b_rs, long long b_ks, double sb, double beta, double* C,
-               long long ldc, void* ws, size_t ws_bytes, int* status, int a_skew, int slices, int lower) {
-    if (M <= 0 || N <= 0) return 0;
-    if (K <= 0 || slices < 1 || slices > SL) return SKEW_ERR_UNSUPPORTED;
-    const long long Kp = rup(K, OKA), Mp = rup(M, OM), Np = rup(N, ON);
+size_t ozaki_gemm_ws(int M, int N, int K) { return ozaki_operand_ws(M, K) + ozaki_operand_ws(N, K) + 256; }
+
+// Digit slices of the operand X[r, k] = sgn * src[r * rs + k * ks] (rows x K),
+// or, with skew, of the skew matrix whose strict lower triangle src holds
+// (leading dimension ks).  Rows are padded to a multiple of 128, K to 64.
+int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long rs, long long ks, double sgn, int skew,
+                void* ws, size_t ws_bytes, OzOperand* op) {
+    if (rows <= 0 || K <= 0) return SKEW_ERR_UNSUPPORTED;
+    const long long Kp = rup(K, OKA), Rp = rup(rows, OM);
     Carve cv(ws, ws_bytes);
-    __nv_bfloat16* Ad = cv.take<__nv_bfloat16>((size_t)(SL * Mp * Kp));
-    __nv_bfloat16* Bd = cv.take<__nv_bfloat16>((size_t)(SL * Np * Kp));
-    int* ea = cv.take<int>((size_t)Mp);
-    int* eb = cv.take<int>((size_t)Np);
-    unsigned long long* skew_max = cv.take<unsigned long long>((size_t)Mp);
+    __nv_bfloat16* d = cv.take<__nv_bfloat16>((size_t)(SL * Rp * Kp));
+    int* e = cv.take<int>((size_t)Rp);
+    unsigned long long* rowmax = cv.take<unsigned long long>((size_t)Rp);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
-    auto split = [&](int rows, long long Rp, const double* src, long long rs, long long ks, double sg, int* e,
-                     __nv_bfloat16* d, int skew) {
+    KtScope kt(st, KT_SLICE_SPLIT);
+    if (skew || (rs == 1 && ks != 1)) {
+        if (const cudaError_t err = cudaMemsetAsync(rowmax, 0, sizeof(unsigned long long) * (size_t)Rp, st))
+            return cuda_fail(err);
         if (skew) {
-            cudaMemsetAsync(skew_max, 0, sizeof(unsigned long long) * (size_t)Rp, st);
             const unsigned T = (unsigned)((rows + 31) / 32);
-            oz_skew_rowmax_kernel<<<dim3(T, T), dim3(32, 8), 0, st>>>(rows, src, ks, skew_max);
-            oz_exp_from_max_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, skew_max, e);
+            oz_skew_rowmax_kernel<<<dim3(T, T), dim3(32, 8), 0, st>>>(rows, src, ks, rowmax);
+        } else {
+            oz_rowmax_cols_kernel<<<dim3((unsigned)((rows + 31) / 32), (unsigned)((K + 255) / 256)), dim3(32, 8), 0,
+                                    st>>>(rows, K, src, ks, rowmax);
+        }
+        oz_exp_from_max_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, rowmax, e);
+        if (skew)
             oz_split_skew_kernel<<<dim3((unsigned)((Rp + 31) / 32), (unsigned)((Kp + 31) / 32)), dim3(32, 8), 0, st>>>(
                 rows, (int)Rp, (int)Kp, src, ks, e, d);
-            count_launch(1);
-        } else if (rs == 1 && ks != 1) {
-            oz_exp_cols_kernel<<<(rows + 127) / 128, 128, 0, st>>>(rows, K, src, ks, e);
+        else
             oz_split_cols_kernel<<<dim3((unsigned)((Rp + 31) / 32), (unsigned)((Kp + 31) / 32)), dim3(32, 8), 0, st>>>(
-                rows, K, (int)Rp, (int)Kp, src, ks, sg, e, d);
-        } else {
-            oz_exp_kernel<<<(int)(rows < 16384 ? rows : 16384), 256, 0, st>>>(rows, K, src, rs, ks, e, skew);
-            oz_split_kernel<<<gridn(Rp * Kp), 256, 0, st>>>(rows, K, (int)Rp, (int)Kp, src, rs, ks, sg, e, d, skew);
-        }
-        count_launch(2);
-    };
-    split(M, Mp, A, a_rs, a_ks, sa, ea, Ad, a_skew);
-    if (!a_skew && B == A && b_rs == a_rs && b_ks == a_ks && sb == sa && N == M && Np == Mp) {
-        // same operand (a Gram matrix): reuse its slices
-        Bd = Ad;
-        eb = ea;
+                rows, K, (int)Rp, (int)Kp, src, ks, sgn, e, d);
+        count_launch(3);
     } else {
-        split(N, Np, B, b_rs, b_ks, sb, eb, Bd, 0);
+        oz_exp_kernel<<<(int)(rows < 16384 ? rows : 16384), 256, 0, st>>>(rows, K, src, rs, ks, e, 0);
+        oz_split_kernel<<<gridn(Rp * Kp), 256, 0, st>>>(rows, K, (int)Rp, (int)Kp, src, rs, ks, sgn, e, d, 0);
+        count_launch(2);
     }
+    op->d = d;
+    op->e = e;
+    op->rows = rows;
+    op->K = K;
+    op->Rp = Rp;
+    op->Kp = Kp;
+    return 0;
+}
+
+// C = alpha * A B^T + beta C from split operands (A: M x K, B: N x K).
+int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, double alpha, double beta, double* C,
+                   long long ldc, int* status, int slices, int lower) {
+    const int M = A.rows, N = B.rows, K = A.K;
+    if (M <= 0 || N <= 0) return 0;
+    if (B.K != K || B.Kp != A.Kp || slices < 1 || slices > SL) return SKEW_ERR_UNSUPPORTED;
     CUtensorMap ta, tb;
-    if (!make_tmap_bf16(&ta, Ad, (uint64_t)Kp, (uint64_t)(SL * Mp), (uint64_t)Kp, OM)) return SKEW_ERR_UNSUPPORTED;
-    if (!make_tmap_bf16(&tb, Bd, (uint64_t)Kp, (uint64_t)(SL * Np), (uint64_t)Kp, ON)) return SKEW_ERR_UNSUPPORTED;
+    if (!make_tmap_bf16(&ta, A.d, (uint64_t)A.Kp, (uint64_t)(SL * A.Rp), (uint64_t)A.Kp, OM))
+        return SKEW_ERR_UNSUPPORTED;
+    if (!make_tmap_bf16(&tb, B.d, (uint64_t)B.Kp, (uint64_t)(SL * B.Rp), (uint64_t)B.Kp, ON))
+        return SKEW_ERR_UNSUPPORTED;
     OzParams p{};
     p.M = M;
     p.N = N;
-    p.katoms = (int)(Kp / OKA);
-    p.nchunks = (p.katoms + 1) / 2;
-    p.Mp = (int)Mp;
-    p.Np = (int)Np;
-    p.ea = ea;
-    p.eb = eb;
+    p.nchunks = (int)(A.Kp / OKA);
+    p.Mp = (int)A.Rp;
+    p.Np = (int)B.Rp;
+    p.ea = A.e;
+    p.eb = B.e;
     p.alpha = alpha;
     p.beta = beta;
     p.C = C;
@@ -558,10 +583,10 @@ int ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double*
     p.status = status;
     p.s = slices;
     p.lower = lower;
+    p.mt = (M + OM - 1) / OM;
+    p.nt = (N + ON - 1) / ON;
     const size_t smem = OzSmem::bytes();
     cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    p.mt = (int)(Mp / OM);
-    p.nt = (int)(Np / ON);
     // algorithmic work: the kept slice pairs over the outputs written
     const double pairs = slices * (slices + 1) / 2.0;
     const double outs = lower ? lower_count(M, N) : (double)M * N;
@@ -570,6 +595,26 @@ int ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double*
     kt_end(st, kt, g_kt_ozaki_kind, 2.0 * pairs * outs * K);
     count_launch();
     return cuda_ok(cudaGetLastError());
+}
+
+// C = alpha * (sa A)(sb B)^T + beta C, A[i,k] = A[i*a_rs + k*a_ks], B[j,k] = B[j*b_rs + k*b_ks].
+int ozaki_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double* A, long long a_rs, long long a_ks,
+               double sa, const double* B, long long b_rs, long long b_ks, double sb, double beta, double* C,
+               long long ldc, void* ws, size_t ws_bytes, int* status, int a_skew, int slices, int lower) {
+    if (M <= 0 || N <= 0) return 0;
+    if (K <= 0 || slices < 1 || slices > SL) return SKEW_ERR_UNSUPPORTED;
+    const size_t wa = ozaki_operand_ws(M, K), wb = ozaki_operand_ws(N, K);
+    if (!ws || ws_bytes < wa + wb) return SKEW_ERR_WORKSPACE;
+    OzOperand oa{}, ob{};
+    int rc = ozaki_split(st, M, K, A, a_rs, a_ks, sa, a_skew, ws, wa, &oa);
+    if (rc) return rc;
+    if (!a_skew && B == A && b_rs == a_rs && b_ks == a_ks && sb == sa && N == M) {
+        ob = oa;  // same operand (a Gram matrix): reuse its slices
+    } else {
+        rc = ozaki_split(st, N, K, B, b_rs, b_ks, sb, 0, static_cast<char*>(ws) + wa, wb, &ob);
+        if (rc) return rc;
+    }
+    return ozaki_gemm_pre(st, oa, ob, alpha, beta, C, ldc, status, slices, lower);
 }
 
 }  // namespace sk

@@ -453,7 +453,10 @@ struct RefineWs {
     double *S, *Wg, *AM, *T, *U, *lt, *Vc;
     int *close, *cid, *nbig;
     RefineScalars* sc;
-    void* oz;
+    // digit-slice buffers: S (once per refinement), the columns of M (Wg, AM,
+    // T), the columns of AM and then of U (T, then the update), the rows of M
+    // (the update)
+    void *oz_s, *oz_mc, *oz_amu, *oz_mr;
     size_t oz_bytes;
 };
 
@@ -471,8 +474,11 @@ RefineWs carve_refine(Carve& cv, int n) {
     w.cid = cv.take<int>((size_t)n);
     w.nbig = cv.take<int>(4);
     w.sc = cv.take<RefineScalars>(1);
-    w.oz_bytes = ozaki_gemm_ws(n, n, n);
-    w.oz = cv.take<char>(w.oz_bytes);
+    w.oz_bytes = ozaki_operand_ws(n, n);
+    w.oz_s = cv.take<char>(w.oz_bytes);
+    w.oz_mc = cv.take<char>(w.oz_bytes);
+    w.oz_amu = cv.take<char>(w.oz_bytes);
+    w.oz_mr = cv.take<char>(w.oz_bytes);
     return w;
 }
 
@@ -491,7 +497,10 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
     Carve cv(ws, ws_bytes);
     RefineWs w = carve_refine(cv, n);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
-    skew_full_kernel<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, st>>>(n, A, lda, w.S);
+    {
+        KtScope kt(st, KT_REFINE_AUX);
+        skew_full_kernel<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, st>>>(n, A, lda, w.S);
+    }
     count_launch();
     if (info) {
         info->iterations = 0;
@@ -505,6 +514,10 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
         ~KindScope() { g_kt_ozaki_kind = KT_OZAKI; }
     } kind_scope;
     const long long ldn = n;
+    // row r of S is minus column r of S (skew), read contiguously
+    OzOperand os{}, omc{}, oam{}, ou{}, omr{};
+    int rc = ozaki_split(st, n, n, w.S, ldn, 1, -1.0, 0, w.oz_s, w.oz_bytes, &os);
+    if (rc) return rc;
     for (int it = 0; it < maxit; it++) {
         // The Gram and projection products keep all eight digit slices: an
         // error delta in Wg or T enters E_ij as delta / (l_j - l_i), and dense
@@ -512,32 +525,39 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
         // cheaper product stalls the iteration instead of speeding it up.
         const int sl = 8;
         // Wg = M^T M (symmetric), AM = S M, T = M^T (S M) (skew): FP64-accurate
-        // tensor-core products, Wg and T on their lower triangle
-        int rc = ozaki_gemm(st, n, n, n, 1.0, M, ldn, 1, 1.0, M, ldn, 1, 1.0, 0.0, w.Wg, ldn, w.oz, w.oz_bytes, status,
-                            0, sl, 1);
+        // tensor-core products, Wg and T on their lower triangle; the column
+        // slices of M serve all three
+        rc = ozaki_split(st, n, n, M, ldn, 1, 1.0, 0, w.oz_mc, w.oz_bytes, &omc);
         if (rc) return rc;
-        // row r of S is minus column r of S (skew), read contiguously
-        rc = ozaki_gemm(st, n, n, n, 1.0, w.S, ldn, 1, -1.0, M, ldn, 1, 1.0, 0.0, w.AM, ldn, w.oz, w.oz_bytes, status,
-                        0, sl, 0);
+        rc = ozaki_gemm_pre(st, omc, omc, 1.0, 0.0, w.Wg, ldn, status, sl, 1);
         if (rc) return rc;
-        rc = ozaki_gemm(st, n, n, n, 1.0, M, ldn, 1, 1.0, w.AM, ldn, 1, 1.0, 0.0, w.T, ldn, w.oz, w.oz_bytes, status,
-                        0, sl, 1);
+        rc = ozaki_gemm_pre(st, os, omc, 1.0, 0.0, w.AM, ldn, status, sl, 0);
         if (rc) return rc;
-        refine_lambda_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt);
-        refine_reset_kernel<<<1, 32, 0, st>>>(w.sc);
-        lmax_kernel<<<1, 1024, 0, st>>>(m, w.lt, &w.sc->lmax);
+        rc = ozaki_split(st, n, n, w.AM, ldn, 1, 1.0, 0, w.oz_amu, w.oz_bytes, &oam);
+        if (rc) return rc;
+        rc = ozaki_gemm_pre(st, omc, oam, 1.0, 0.0, w.T, ldn, status, sl, 1);
+        if (rc) return rc;
+        {
+            KtScope kt(st, KT_REFINE_AUX);
+            refine_lambda_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt);
+            refine_reset_kernel<<<1, 32, 0, st>>>(w.sc);
+            lmax_kernel<<<1, 1024, 0, st>>>(m, w.lt, &w.sc->lmax);
+        }
         count_launch(3);
         double lmax = 0.0;
         if (const cudaError_t e = cudaMemcpyAsync(&lmax, &w.sc->lmax, sizeof(double), cudaMemcpyDeviceToHost, st))
             return cuda_fail(e);
         if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
         const double tau = 64.0 * n * DBL_EPSILON * lmax;
-        refine_close_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt, tau, rho, w.close);
-        refine_rr_kernel<<<m, 32, 0, st>>>(m, n, w.Wg, w.T, w.close, w.lt, w.cid, w.Vc, w.nbig);
-        // E~ lives in the AM buffer (free once T is formed)
-        refine_etilde_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, n, w.Wg, w.T, w.lt, w.cid, w.Vc, tau,
-                                                                      w.AM, w.sc);
-        refine_u_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, w.cid, w.Vc, w.AM, w.U, w.sc);
+        {
+            KtScope kt(st, KT_REFINE_AUX);
+            refine_close_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt, tau, rho, w.close);
+            refine_rr_kernel<<<m, 32, 0, st>>>(m, n, w.Wg, w.T, w.close, w.lt, w.cid, w.Vc, w.nbig);
+            // E~ lives in the AM buffer (free once T is formed)
+            refine_etilde_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, n, w.Wg, w.T, w.lt, w.cid, w.Vc, tau,
+                                                                          w.AM, w.sc);
+            refine_u_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, w.cid, w.Vc, w.AM, w.U, w.sc);
+        }
         count_launch(4);
         RefineScalars h{};
         if (const cudaError_t e = cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, st))
@@ -555,8 +575,11 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
             su = su < 3 ? 3 : (su > 8 ? 8 : su);
         }
         // the product reads M's digit slices, taken before C is written
-        rc = ozaki_gemm(st, n, n, n, 1.0, M, 1, ldn, 1.0, w.U, 2LL * m, 1, 1.0, 1.0, M, ldn, w.oz, w.oz_bytes, status,
-                        0, su, 0);
+        rc = ozaki_split(st, n, n, M, 1, ldn, 1.0, 0, w.oz_mr, w.oz_bytes, &omr);
+        if (rc) return rc;
+        rc = ozaki_split(st, n, n, w.U, 2LL * m, 1, 1.0, 0, w.oz_amu, w.oz_bytes, &ou);
+        if (rc) return rc;
+        rc = ozaki_gemm_pre(st, omr, ou, 1.0, 1.0, M, ldn, status, su, 0);
         if (rc) return rc;
         if (const cudaError_t e = cudaMemcpyAsync(lambda, w.lt, sizeof(double) * m, cudaMemcpyDeviceToDevice, st))
             return cuda_fail(e);

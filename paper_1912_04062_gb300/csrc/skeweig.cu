@@ -177,10 +177,13 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     last_refine_info() = RefineInfo{};  // iterations = 0 unless this solve refines
 
     mark(0);
-    zero_int_kernel<<<1, 32, 0, st>>>(p.status);
-    count_launch();
-    copy_lower_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(n, A, lda, p.W, n, o ? o->check_finite : 0, p.status);
-    count_launch();
+    {
+        KtScope kt(st, KT_OTHER);
+        zero_int_kernel<<<1, 32, 0, st>>>(p.status);
+        copy_lower_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(n, A, lda, p.W, n, o ? o->check_finite : 0,
+                                                                   p.status);
+    }
+    count_launch(2);
     mark(1);
     int rc = band_reduce(st, n, p.W, n, p.b, p.Tfac, p.ws_reduce, p.sz_reduce, p.status, p.reduce_prec);
     if (rc) return rc;
@@ -196,6 +199,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     if (vectors) {
         // Algorithm 1 step 3 (D map) fused with the interleaved -> column-major
         // move; Z = [X | Y] is n x 2 nev with leading dimension n.
+        KtScope kt(st, KT_OTHER);
         if (interleaved_to_colmajor(st, n, nev, p.Qi, p.Z, p.Z + (size_t)n * nev, n, true) != cudaSuccess)
             return SKEW_ERR_CUDA;
     }
@@ -205,10 +209,16 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     } else if (vectors) {
         // mixed form: Q_trd in FP32 arithmetic (reflectors from the FP64 chase)
         const size_t cnt = (size_t)n * 2 * nev;
-        f64_to_f32_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z, p.Z32);
+        {
+            KtScope kt(st, KT_OTHER);
+            f64_to_f32_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z, p.Z32);
+        }
         count_launch();
         if (apply_qtrd_f32(st, n, p.b, p.Vtrd, p.tautrd, p.Z32, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
-        f32_to_f64_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z32, p.Z);
+        {
+            KtScope kt(st, KT_OTHER);
+            f32_to_f64_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z32, p.Z);
+        }
         count_launch();
     }
     mark(7);
@@ -227,6 +237,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     }
     mark(9);
     if (vectors) {
+        KtScope kt(st, KT_OTHER);
         split_z_kernel<<<grid_for((size_t)n * nev), 256, 0, st>>>(n, nev, p.Z, n, Zre, Zim, ldz);
         count_launch();
     }

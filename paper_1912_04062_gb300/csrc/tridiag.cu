@@ -160,7 +160,10 @@ int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* la
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
     tri_prep_kernel<<<1, 1024, 0, st>>>(n, alpha, w.a2, w.sc);
     count_launch();
-    bisect_kernel<<<(nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2, w.sc, lambda);
+    {
+        KtScope kt(st, KT_BISECT);
+        bisect_kernel<<<(nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2, w.sc, lambda);
+    }
     count_launch();
     if (Qi) {
         // cluster tolerance relative to ||S||_1: 1e-3 for small n (the usual
@@ -169,7 +172,10 @@ int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* la
         double ctol = fmin(1e-3, 10.0 / ((double)n * sqrt((double)n)));
         set_int_kernel<<<1, 32, 0, st>>>(w.fail, 0x7fffffff);
         count_launch();
-        invit_kernel<<<(nev + 63) / 64, 64, 0, st>>>(n, nev, alpha, lambda, w.sc, ctol, maxit, w.bf, Qi, w.fail);
+        {
+            KtScope kt(st, KT_INVIT);
+            invit_kernel<<<(nev + 63) / 64, 64, 0, st>>>(n, nev, alpha, lambda, w.sc, ctol, maxit, w.bf, Qi, w.fail);
+        }
         count_launch();
         invit_status_kernel<<<1, 32, 0, st>>>(w.fail, nev, d_status);
         count_launch();

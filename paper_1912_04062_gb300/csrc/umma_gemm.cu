@@ -278,9 +278,13 @@ int split_gemm(cudaStream_t st, int M, int N, int K, double alpha, const double*
         return (int)(g > 16384 ? 16384 : (g < 1 ? 1 : g));
     };
     const long long ldb = (long long)nplanes * Kp;
-    split_bf16_kernel<<<grid_for(Mp * Kp), 256, 0, st>>>(M, K, (int)Mp, (int)Kp, A, a_rs, a_ks, a_skew, Ab, ldb,
-                                                         nplanes);
-    split_bf16_kernel<<<grid_for(Np * Kp), 256, 0, st>>>(N, K, (int)Np, (int)Kp, B, b_rs, b_ks, 0, Bb, ldb, nplanes);
+    {
+        KtScope kt(st, KT_SLICE_SPLIT);
+        split_bf16_kernel<<<grid_for(Mp * Kp), 256, 0, st>>>(M, K, (int)Mp, (int)Kp, A, a_rs, a_ks, a_skew, Ab, ldb,
+                                                             nplanes);
+        split_bf16_kernel<<<grid_for(Np * Kp), 256, 0, st>>>(N, K, (int)Np, (int)Kp, B, b_rs, b_ks, 0, Bb, ldb,
+                                                             nplanes);
+    }
     count_launch(2);
     CUtensorMap ta, tb;
     if (!make_tmap(&ta, Ab, (uint64_t)ldb, (uint64_t)Mp, (uint64_t)ldb, UM)) return SKEW_ERR_UNSUPPORTED;

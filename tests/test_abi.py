@@ -99,7 +99,8 @@ def test_kernel_timing_switch_is_host_side(sk):
     assert L.skew_kernel_timing(1) == 0
     ms, fl, k = sk.kernel_timing_read(sk.SKEW_KERNEL_OZAKI)
     assert (ms, fl, k) == (0.0, 0.0, 0)
-    assert L.skew_kernel_timing_read(7, None, None, None) == -1
+    assert L.skew_kernel_timing_read(12, None, None, None) == -1
+    assert L.skew_kernel_timing_read(-1, None, None, None) == -1
     assert L.skew_kernel_timing(0) == 0
 
 
