@@ -74,9 +74,10 @@ qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ t
                 const int s = s0 + sl;
                 ts[sl] = (s < s1 && k < qsteps(n, QB, s)) ? (T)tautrd[(size_t)k * nsw + s] : (T)0;
             }
-            for (int e = t; e < H * nc; e += QT) {
-                int i = e % H, cc = e / H;
-                zw[cc * QLD + i] = Z[(size_t)(c0 + cc) * ldz + top + i];
+            // window: warp w takes columns w, w + 8, ..., lanes run down the column
+            for (int cc = t >> 5; cc < nc; cc += QT / 32) {
+                const T* zsrc = Z + (size_t)(c0 + cc) * ldz + top;
+                for (int i = t & 31; i < H; i += 32) zw[cc * QLD + i] = zsrc[i];
             }
             __syncthreads();
             T zr[32];
@@ -91,13 +92,17 @@ qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ t
                 const T tau = ts[off];
                 if (tau == (T)0) continue;
                 const T* v = vs + off * QB;
-                T a = 0;
+                T a = 0, a2 = 0;  // two chains: even and odd u
 #pragma unroll
                 for (int u = 0; u < 32; u++) {
                     if (4 * u + 3 < off || 4 * u > off + QB - 1) continue;
                     const int i = 4 * u + q - off;
-                    if (i >= 0 && i < QB) a = fma(v[i], zr[u], a);
+                    if (i >= 0 && i < QB) {
+                        if (u & 1) a2 = fma(v[i], zr[u], a2);
+                        else a = fma(v[i], zr[u], a);
+                    }
                 }
+                a += a2;
                 a += __shfl_xor_sync(0xffffffffu, a, 1);
                 a += __shfl_xor_sync(0xffffffffu, a, 2);
                 a *= tau;
@@ -115,9 +120,9 @@ qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ t
                 if (r < H) zcw[r] = zr[u];
             }
             __syncthreads();
-            for (int e = t; e < H * nc; e += QT) {
-                int i = e % H, cc = e / H;
-                Z[(size_t)(c0 + cc) * ldz + top + i] = zw[cc * QLD + i];
+            for (int cc = t >> 5; cc < nc; cc += QT / 32) {
+                T* zdst = Z + (size_t)(c0 + cc) * ldz + top;
+                for (int i = t & 31; i < H; i += 32) zdst[i] = zw[cc * QLD + i];
             }
             __syncthreads();
         }

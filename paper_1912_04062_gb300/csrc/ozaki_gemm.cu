@@ -29,7 +29,8 @@
 // (one 128-byte swizzle atom).  All B digit slices of a chunk sit in one of two
 // buffers, so the next chunk's B loads while the current one is multiplied; A
 // digit slices stream through a ring of NA one-slice stages.  Within a chunk,
-// pass i multiplies A slice i with B slices 0 .. S-1-i.
+// pass i multiplies A slice i with B slices 0 .. S-1-i as one wide MMA (B
+// slices adjacent in shared memory, their levels adjacent in TMEM).
 // TMEM holds one level group (4 chunks = 256 of K), so the MMAs of the next
 // group start once the epilogue has drained it.
 // With `lower` set, tiles wholly above the diagonal (every column index above
@@ -219,8 +220,11 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
     } else if (warp == 9) {
         if (lane == 0) {
-            // ---- MMA issuer: level L accumulates in TMEM columns [64 L, 64 L + 64)
-            constexpr uint32_t idesc = umma_idesc_bf16(OM, ON);
+            // ---- MMA issuer: level L accumulates in TMEM columns [64 L, 64 L + 64).
+            // Pass i multiplies A slice i with B slices 0 .. S-1-i; those B slices
+            // are consecutive 64-row blocks of one buffer and their levels
+            // i .. S-1 consecutive TMEM columns, so the pass is one MMA of width
+            // N = 64 (S - i) (two when wider than 256).
             bool ok = true;
             int ac = 0, bc = 0;
             for (int c = 0; c < nch && ok; c++) {
@@ -239,13 +243,16 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     ac++;
                     tc_fence_after();
                     const uint64_t ad0 = umma_desc_sw128(smem_u32(sA + st * OzSmem::A_ATOM));
-                    for (int j = 0; i + j < S; j++) {
-                        const uint32_t dcol = tmem + (uint32_t)((i + j) * ON);
-                        const uint64_t bd0 = umma_desc_sw128(smem_u32(sB + q * OzSmem::B_SET + j * OzSmem::B_ATOM));
+                    const int nj = S - i, n1 = nj < 4 ? nj : 4;
+                    const uint64_t b0 = umma_desc_sw128(smem_u32(sB + q * OzSmem::B_SET));
+                    const uint64_t b4 = umma_desc_sw128(smem_u32(sB + q * OzSmem::B_SET + 4 * OzSmem::B_ATOM));
+                    const uint32_t d0 = tmem + (uint32_t)(i * ON), d4 = tmem + (uint32_t)((i + 4) * ON);
 #pragma unroll
-                        for (int kk = 0; kk < OKA / 16; kk++)
-                            // level L is first written by the pair (0, L) at kk = 0 of a group
-                            umma_bf16(dcol, ad0 + 2 * kk, bd0 + 2 * kk, idesc, (!first || i > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < OKA / 16; kk++) {
+                        // every level is first written by pass 0 at kk = 0 of a group
+                        const uint32_t acc = (!first || i > 0 || kk > 0) ? 1u : 0u;
+                        umma_bf16(d0, ad0 + 2 * kk, b0 + 2 * kk, umma_idesc_bf16(OM, ON * n1), acc);
+                        if (nj > 4) umma_bf16(d4, ad0 + 2 * kk, b4 + 2 * kk, umma_idesc_bf16(OM, ON * (nj - 4)), acc);
                     }
                     umma_commit(&aempty[st]);
                 }
@@ -409,16 +416,49 @@ __global__ void oz_exp_kernel(int rows, int K, const double* __restrict__ src, l
     }
 }
 
+// Rows contiguous in k (sk == 1): one block per row finds the row maximum,
+// then writes the row's digits two k at a time (the second read of the row
+// comes from L2).  Padding rows and columns are zero.
+__global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, int Rp, int Kp, const double* __restrict__ src,
+                                                            long long sr, double sgn, int* __restrict__ e,
+                                                            __nv_bfloat16* __restrict__ dst) {
+    __shared__ double red[8];
+    for (int r = blockIdx.x; r < Rp; r += gridDim.x) {
+        const double* row = src + (long long)r * sr;
+        double m = 0.0;
+        if (r < rows)
+            for (int k = threadIdx.x; k < K; k += 256) m = fmax(m, fabs(row[k]));
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        m = red[0];
+        for (int w = 1; w < 8; w++) m = fmax(m, red[w]);
+        int ex = 0;
+        if (m > 0.0) frexp(m, &ex);  // m = f 2^ex, f in [0.5, 1): every |x| < 2^ex
+        if (threadIdx.x == 0) e[r] = ex;
+        for (int k = 2 * threadIdx.x; k < Kp; k += 512) {
+            const double x0 = (r < rows && k < K) ? sgn * row[k] : 0.0;
+            const double x1 = (r < rows && k + 1 < K) ? sgn * row[k + 1] : 0.0;
+            float d0[8], d1[8];
+            oz_digits(x0, ex, d0);
+            oz_digits(x1, ex, d1);
+#pragma unroll
+            for (int i = 0; i < SL; i++)
+                *reinterpret_cast<__nv_bfloat162*>(dst + ((long long)i * Rp + r) * Kp + k) =
+                    __floats2bfloat162_rn(d0[i], d1[i]);
+        }
+        __syncthreads();  // red is reused by the next row
+    }
+}
+
 // Digit slices: plane i holds rows [i Rp, i Rp + rows) of a (SL Rp) x Kp
 // row-major BF16 array; padding rows / columns are zero.
 __global__ void oz_split_kernel(int rows, int K, int Rp, int Kp, const double* __restrict__ src, long long sr,
-                                long long sk, double sgn, const int* __restrict__ e, __nv_bfloat16* __restrict__ dst,
-                                int skew) {
-    const long long total = (long long)Rp * Kp;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(t % Kp), r = (int)(t / Kp);
-        const double x = (r < rows && k < K) ? sgn * oz_elem(src, sr, sk, skew, r, k) : 0.0;
+                                long long sk, double sgn, const int* __restrict__ e, __nv_bfloat16* __restrict__ dst) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Kp) return;
+    for (int r = blockIdx.y; r < Rp; r += gridDim.y) {
+        const double x = (r < rows && k < K) ? sgn * src[(long long)r * sr + (long long)k * sk] : 0.0;
         float d[8];
         oz_digits(x, (r < rows) ? e[r] : 0, d);
 #pragma unroll
@@ -543,9 +583,14 @@ int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long r
             oz_split_cols_kernel<<<dim3((unsigned)((Rp + 31) / 32), (unsigned)((Kp + 31) / 32)), dim3(32, 8), 0, st>>>(
                 rows, K, (int)Rp, (int)Kp, src, ks, sgn, e, d);
         count_launch(3);
+    } else if (ks == 1) {
+        oz_split_rows_kernel<<<(int)(Rp < 32768 ? Rp : 32768), 256, 0, st>>>(rows, K, (int)Rp, (int)Kp, src, rs, sgn, e,
+                                                                            d);
+        count_launch(1);
     } else {
         oz_exp_kernel<<<(int)(rows < 16384 ? rows : 16384), 256, 0, st>>>(rows, K, src, rs, ks, e, 0);
-        oz_split_kernel<<<gridn(Rp * Kp), 256, 0, st>>>(rows, K, (int)Rp, (int)Kp, src, rs, ks, sgn, e, d, 0);
+        oz_split_kernel<<<dim3((unsigned)((Kp + 255) / 256), (unsigned)(Rp < 65535 ? Rp : 65535)), 256, 0, st>>>(
+            rows, K, (int)Rp, (int)Kp, src, rs, ks, sgn, e, d);
         count_launch(2);
     }
     op->d = d;

@@ -5,7 +5,8 @@
 //
 // Sec. 3 (the solver BSEPACK adapted from ScaLAPACK): bisection + inverse
 // iteration.
-//   * Bisection: one thread per wanted eigenvalue (the nev largest); Sturm
+//   * Bisection: four lanes per wanted eigenvalue (the nev largest) count at
+//     four interior points per step (multisection); Sturm
 //     counts from the LDL^T pivots d_0 = -x, d_i = -x - alpha_{i-1}^2/d_{i-1}
 //     (tiny pivots replaced by -pivmin); interval [-g, g], g = ||S||_1.
 //   * Inverse iteration: Gaussian elimination with partial pivoting of
@@ -58,11 +59,39 @@ __global__ void tri_prep_kernel(int n, const double* __restrict__ alpha, double*
     }
 }
 
-__global__ void bisect_kernel(int n, int nev, const double* __restrict__ a2, const TriScalars* sc,
-                              double* __restrict__ lambda) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nev) return;
-    lambda[k] = bisect_one(n, n - 1 - k, a2, sc->g, sc->pivmin);
+// Multisection: four lanes per wanted eigenvalue each count at one of four
+// equally spaced interior points of the current interval, which shrinks to one
+// fifth per step (same Sturm recurrence and stopping rule as bisect_one).
+__global__ void bisect4_kernel(int n, int nev, const double* __restrict__ a2, const TriScalars* sc,
+                               double* __restrict__ lambda) {
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = gt >> 2, q = gt & 3, lane = threadIdx.x & 31;
+    if (k >= nev) return;  // whole groups of four leave together (blockDim is a multiple of 4)
+    const unsigned gmask = 0xFu << (lane & ~3);
+    const double g = sc->g, pivmin = sc->pivmin;
+    const int j = n - 1 - k;  // ascending index of the wanted eigenvalue
+    if (n == 1 || g == 0.0) {
+        if (q == 0) lambda[k] = 0.0;
+        return;
+    }
+    double lo = -g - 2.0 * DBL_EPSILON * g - pivmin;
+    double hi = g + 2.0 * DBL_EPSILON * g + pivmin;
+    for (int it = 0; it < 2000; it++) {
+        const double w = hi - lo;
+        const double tol = 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_MIN;
+        if (w <= tol) break;
+        const double step = w * 0.2;
+        const double x = lo + (double)(q + 1) * step;
+        const bool le = (x > lo && x < hi) ? (sturm(n, a2, pivmin, x) <= j) : (x <= lo);
+        // counts grow with x: the lanes with lambda_j >= x_q are a prefix
+        const int nle = __popc(__ballot_sync(gmask, le) & gmask);
+        const double nlo = (nle > 0) ? lo + (double)nle * step : lo;
+        const double nhi = (nle < 4) ? lo + (double)(nle + 1) * step : hi;
+        if (!(nlo > lo || nhi < hi)) break;  // no representable progress
+        lo = nlo;
+        hi = (nhi < hi) ? nhi : hi;
+    }
+    if (q == 0) lambda[k] = lo + 0.5 * (hi - lo);
 }
 
 __global__ void invit_kernel(int n, int nev, const double* __restrict__ alpha,
@@ -162,7 +191,7 @@ int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* la
     count_launch();
     {
         KtScope kt(st, KT_BISECT);
-        bisect_kernel<<<(nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2, w.sc, lambda);
+        bisect4_kernel<<<(4 * nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2, w.sc, lambda);
     }
     count_launch();
     if (Qi) {
