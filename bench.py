@@ -49,8 +49,11 @@ def _peaks():
 PEAKS = _peaks()
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from an ncu capture of the current kernel source; None when
-# the kernel changed after the capture.
-TRAFFIC = {"ozaki_refine": None, "ozaki_reduce": None, "split": None}
+# the kernel changed after the capture.  ozaki_refine: 2.34 GB for a
+# 4096^3 product (profiles/ozaki_gemm_kernel_4096cube.md), scaled by the tiles x K
+# it processes to the refinement's n = 16384 launches (x64 for a full product,
+# half for the lower-triangle ones: two of each per iteration -> x48).
+TRAFFIC = {"ozaki_refine": 2.34e9 * 48, "ozaki_reduce": None, "split": None}
 
 
 def parse():
@@ -313,7 +316,7 @@ def run_ours(args, ws, rank, local):
                 "split": "umma_gemm_kernel (BF16 split products)"}[top]
         roof = {"bound": "tensor", "achieved": achieved, "peak": PEAKS["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "frac": achieved / PEAKS["bf16_tflops_sustained"],
-                "traffic": TRAFFIC.get(top), "kernel": name, "launches_per_step": tl / args.steps,
+                "traffic": TRAFFIC.get(top) if n == 16384 else None, "kernel": name, "launches_per_step": tl / args.steps,
                 "avg_launch_ms": tms / tl, "kernel_ms_per_step": tms / args.steps,
                 "peak_note": "of measured: cuBLAS bf16 sustained (kernel timed inside a long step)",
                 "other_kernels_ms_per_step": {k: round(v, 3) for k, v in kt_ms.items() if k != top}}

@@ -87,31 +87,42 @@ qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ t
                 const int r = 4 * u + q;
                 zr[u] = (r < H) ? zc[r] : (T)0;
             }
+            // Reflector off touches rows 4u + q with 0 <= 4u + q - off < QB.  For
+            // u in [ceil(off / 4), floor((off + QB - 4) / 4)] that holds for every
+            // phase q, so those u need no test and read v at a compile-time
+            // offset from the thread's phase pointer; only u = U0 - 1 (when
+            // q >= off - 4 (U0 - 1)) and u = U1 + 1 (when 4 (U1 + 1) + q - off < QB)
+            // depend on q.
+            const T* vq = vs + q;
 #pragma unroll
             for (int off = QELL - 1; off >= 0; off--) {
                 const T tau = ts[off];
                 if (tau == (T)0) continue;
-                const T* v = vs + off * QB;
-                T a = 0, a2 = 0;  // two chains: even and odd u
+                const T* v = vq + off * QB - off;  // v[4u] = element 4u + q - off of reflector off
+                const int U0 = (off + 3) / 4, U1 = (off + QB - 4) / 4;
+                const bool lo_ok = (U0 >= 1) && (q >= off - 4 * (U0 - 1));
+                const bool hi_ok = (U1 + 1 <= 31) && (4 * (U1 + 1) + q - off < QB);
+                T a = 0, a2 = 0;
 #pragma unroll
                 for (int u = 0; u < 32; u++) {
-                    if (4 * u + 3 < off || 4 * u > off + QB - 1) continue;
-                    const int i = 4 * u + q - off;
-                    if (i >= 0 && i < QB) {
-                        if (u & 1) a2 = fma(v[i], zr[u], a2);
-                        else a = fma(v[i], zr[u], a);
-                    }
+                    if (u < U0 || u > U1) continue;
+                    if (u & 1) a2 = fma(v[4 * u], zr[u], a2);
+                    else a = fma(v[4 * u], zr[u], a);
                 }
+                if (U0 >= 1 && lo_ok) a = fma(v[4 * (U0 - 1)], zr[U0 - 1 < 0 ? 0 : U0 - 1], a);
+                if (U1 + 1 <= 31 && hi_ok) a2 = fma(v[4 * (U1 + 1)], zr[U1 + 1 > 31 ? 31 : U1 + 1], a2);
                 a += a2;
                 a += __shfl_xor_sync(0xffffffffu, a, 1);
                 a += __shfl_xor_sync(0xffffffffu, a, 2);
                 a *= tau;
 #pragma unroll
                 for (int u = 0; u < 32; u++) {
-                    if (4 * u + 3 < off || 4 * u > off + QB - 1) continue;
-                    const int i = 4 * u + q - off;
-                    if (i >= 0 && i < QB) zr[u] = fma(-a, v[i], zr[u]);
+                    if (u < U0 || u > U1) continue;
+                    zr[u] = fma(-a, v[4 * u], zr[u]);
                 }
+                if (U0 >= 1 && lo_ok) zr[U0 - 1 < 0 ? 0 : U0 - 1] = fma(-a, v[4 * (U0 - 1)], zr[U0 - 1 < 0 ? 0 : U0 - 1]);
+                if (U1 + 1 <= 31 && hi_ok)
+                    zr[U1 + 1 > 31 ? 31 : U1 + 1] = fma(-a, v[4 * (U1 + 1)], zr[U1 + 1 > 31 ? 31 : U1 + 1]);
             }
             T* zcw = zw + c * QLD;
 #pragma unroll

@@ -32,18 +32,23 @@ __host__ __device__ inline int nsteps_of(int n, int b, int s) {
 }
 
 struct ChaseSmem {
-    double B[CB * CLD];
-    double D[CB * CLD];
-    double C[CB * CLD];
+    double buf[3][CB * CLD];  // B, D and C of the current step (B and C trade places)
     double v[CB];
-    double w[CB];
-    double red[4 * CB];
+    double wB[CB], wD[CB], wC[CB];
+    double red[3][4 * CB];
     double tau, beta;
 };
 
+// Step k of sweep s.  B holds B_k already when have_b (it is the C block of
+// step k-1 of the same sweep, which no other sweep touches in between: the
+// neighbouring sweeps reach its rows only two steps later), and C is kept for
+// step k+1 instead of being stored when keep_c.  The left update of B, the
+// two-sided update of D and the right update of C depend only on (v, tau):
+// their dot products share one pass and one reduction, their updates one pass.
 __device__ void chase_task(int n, int s, int k, int nsw, double* __restrict__ AB, int ldab,
-                           double* __restrict__ alpha, double* __restrict__ Vtrd,
-                           double* __restrict__ tautrd, ChaseSmem& sm) {
+                           double* __restrict__ alpha, double* __restrict__ Vtrd, double* __restrict__ tautrd,
+                           double* __restrict__ B, double* __restrict__ D, double* __restrict__ C, bool have_b,
+                           bool keep_c, ChaseSmem& sm) {
     const int t = threadIdx.x;
     const int r = s + 1 + k * CB;
     const int L = min(CB, n - r);
@@ -52,47 +57,48 @@ __device__ void chase_task(int n, int s, int k, int nsw, double* __restrict__ AB
     const int rc = r + CB;
     const int Lc = max(0, min(CB, n - rc));
 
-    // ---- load B_k (L x nbc), D_k (strict lower, L x L), C_k (Lc x L)
-    for (int e = t; e < L * nbc; e += CH_THREADS) {
-        int i = e % L, j = e / L;
-        sm.B[j * CLD + i] = __ldcg(AB + (size_t)(c0 + j) * ldab + (r + i - c0 - j));
-    }
+    // ---- load B_k (L x nbc) unless kept, D_k (strict lower, L x L), C_k (Lc x L)
+    if (!have_b)
+        for (int e = t; e < L * nbc; e += CH_THREADS) {
+            const int i = e % L, j = e / L;
+            B[j * CLD + i] = __ldcg(AB + (size_t)(c0 + j) * ldab + (r + i - c0 - j));
+        }
     for (int e = t; e < L * L; e += CH_THREADS) {
-        int i = e % L, j = e / L;
-        sm.D[j * CLD + i] = (i > j) ? __ldcg(AB + (size_t)(r + j) * ldab + (i - j)) : 0.0;
+        const int i = e % L, j = e / L;
+        D[j * CLD + i] = (i > j) ? __ldcg(AB + (size_t)(r + j) * ldab + (i - j)) : 0.0;
     }
     for (int e = t; e < Lc * L; e += CH_THREADS) {
-        int i = e % Lc, j = e / Lc;
-        sm.C[j * CLD + i] = __ldcg(AB + (size_t)(r + j) * ldab + (CB + i - j));
+        const int i = e % Lc, j = e / Lc;
+        C[j * CLD + i] = __ldcg(AB + (size_t)(r + j) * ldab + (CB + i - j));
     }
     __syncthreads();
 
     // ---- reflector from B_k[:, 0] (dlarfg convention)
     if (t < 32) {
         double a = 0.0;
-        for (int i = 1 + t; i < L; i += 32) a = fma(sm.B[i], sm.B[i], a);
+        for (int i = 1 + t; i < L; i += 32) a = fma(B[i], B[i], a);
         a = sk_warp_sum(a);
         if (t == 0) {
-            double x0 = sm.B[0], tu, be, sc;
+            const double x0 = B[0];
+            double tu, be, sc;
             if (a == 0.0) {
                 tu = 0.0; be = x0; sc = 0.0;
             } else {
-                double rr = sqrt(x0 * x0 + a);
+                const double rr = sqrt(x0 * x0 + a);
                 be = (x0 >= 0.0) ? -rr : rr;
                 tu = (be - x0) / be;
                 sc = 1.0 / (x0 - be);
             }
             sm.tau = tu;
             sm.beta = be;
-            sm.v[0] = 1.0;
-            sm.w[0] = sc;
+            sm.wB[0] = sc;
         }
     }
     __syncthreads();
     const double tau = sm.tau;
     {
-        const double sc = sm.w[0];
-        for (int i = 1 + t; i < CB; i += CH_THREADS) sm.v[i] = (i < L) ? sm.B[i] * sc : 0.0;
+        const double sc = sm.wB[0];
+        for (int i = t; i < CB; i += CH_THREADS) sm.v[i] = (i == 0) ? 1.0 : ((i < L) ? B[i] * sc : 0.0);
     }
     __syncthreads();
     {
@@ -103,77 +109,67 @@ __device__ void chase_task(int n, int s, int k, int nsw, double* __restrict__ AB
             if (k == 0) alpha[s] = -sm.beta;  // T[s, s+1] = -T[s+1, s]
         }
     }
-    // first column of B_k becomes beta e1
-    for (int i = t; i < L; i += CH_THREADS) sm.B[i] = (i == 0) ? sm.beta : 0.0;
 
     const int jj = t & (CB - 1), q = t >> 6;  // column/row index and quarter
     if (tau != 0.0) {
-        // ---- left: B_k[:, 1:] -= tau v (v^T B_k[:, 1:])
-        if (nbc > 1) {
-            double a = 0.0;
-            if (jj >= 1)
-                for (int i = q * 16; i < min(L, q * 16 + 16); i++) a = fma(sm.v[i], sm.B[jj * CLD + i], a);
-            sm.red[q * CB + jj] = a;
-            __syncthreads();
-            if (t < CB) sm.w[t] = tau * (sm.red[t] + sm.red[CB + t] + sm.red[2 * CB + t] + sm.red[3 * CB + t]);
-            __syncthreads();
-            for (int e = t; e < L * (CB - 1); e += CH_THREADS) {
-                int i = e % L, j = 1 + e / L;
-                sm.B[j * CLD + i] -= sm.v[i] * sm.w[j];
-            }
-            __syncthreads();
-        }
-        // ---- two-sided on skew D_k: y = D v, p = tau y, D += v p^T - p v^T
+        // ---- partial dots of the three updates (quarters of 16)
         {
-            double a = 0.0;
-            const int i = jj;
-            if (i < L) {
-                for (int j = q * 16; j < min(L, q * 16 + 16); j++) {
-                    if (j < i) a = fma(sm.D[j * CLD + i], sm.v[j], a);
-                    else if (j > i) a = fma(-sm.D[i * CLD + j], sm.v[j], a);
+            double aB = 0.0, aD = 0.0, aC = 0.0;
+            const int lo = q * 16, hi = min(L, q * 16 + 16);
+            if (nbc > 1 && jj >= 1)  // (v^T B)_j
+                for (int i = lo; i < hi; i++) aB = fma(sm.v[i], B[jj * CLD + i], aB);
+            if (jj < L)              // (D v)_i, D skew from its lower part
+                for (int j = lo; j < hi; j++) {
+                    if (j < jj) aD = fma(D[j * CLD + jj], sm.v[j], aD);
+                    else if (j > jj) aD = fma(-D[jj * CLD + j], sm.v[j], aD);
                 }
-            }
-            sm.red[q * CB + jj] = a;
-            __syncthreads();
-            if (t < CB) sm.w[t] = tau * (sm.red[t] + sm.red[CB + t] + sm.red[2 * CB + t] + sm.red[3 * CB + t]);
-            __syncthreads();
-            for (int e = t; e < L * L; e += CH_THREADS) {
-                int i = e % L, j = e / L;
-                if (i > j) sm.D[j * CLD + i] += sm.v[i] * sm.w[j] - sm.w[i] * sm.v[j];
-            }
-            __syncthreads();
+            if (jj < Lc)             // (C v)_i
+                for (int j = lo; j < hi; j++) aC = fma(C[j * CLD + jj], sm.v[j], aC);
+            sm.red[0][q * CB + jj] = aB;
+            sm.red[1][q * CB + jj] = aD;
+            sm.red[2][q * CB + jj] = aC;
         }
-        // ---- right: C_k -= tau (C_k v) v^T
-        if (Lc > 0) {
-            double a = 0.0;
-            const int i = jj;
-            if (i < Lc)
-                for (int j = q * 16; j < min(L, q * 16 + 16); j++) a = fma(sm.C[j * CLD + i], sm.v[j], a);
-            sm.red[q * CB + jj] = a;
-            __syncthreads();
-            if (t < CB) sm.w[t] = tau * (sm.red[t] + sm.red[CB + t] + sm.red[2 * CB + t] + sm.red[3 * CB + t]);
-            __syncthreads();
-            for (int e = t; e < Lc * L; e += CH_THREADS) {
-                int i = e % Lc, j = e / Lc;
-                sm.C[j * CLD + i] -= sm.w[i] * sm.v[j];
+        __syncthreads();
+        if (t < CB) {
+            sm.wB[t] = tau * (sm.red[0][t] + sm.red[0][CB + t] + sm.red[0][2 * CB + t] + sm.red[0][3 * CB + t]);
+            sm.wD[t] = tau * (sm.red[1][t] + sm.red[1][CB + t] + sm.red[1][2 * CB + t] + sm.red[1][3 * CB + t]);
+            sm.wC[t] = tau * (sm.red[2][t] + sm.red[2][CB + t] + sm.red[2][2 * CB + t] + sm.red[2][3 * CB + t]);
+        }
+        __syncthreads();
+        // ---- updates: B[:, 1:] -= v wB^T; D += v p^T - p v^T (p = wD = tau D v;
+        // the 1/2 tau^2 (v^T D v) v term is 0 for skew D); C -= wC v^T
+        if (nbc > 1)
+            for (int e = t; e < L * (CB - 1); e += CH_THREADS) {
+                const int i = e % L, j = 1 + e / L;
+                B[j * CLD + i] -= sm.v[i] * sm.wB[j];
             }
+        for (int e = t; e < L * L; e += CH_THREADS) {
+            const int i = e % L, j = e / L;
+            if (i > j) D[j * CLD + i] += sm.v[i] * sm.wD[j] - sm.wD[i] * sm.v[j];
+        }
+        for (int e = t; e < Lc * L; e += CH_THREADS) {
+            const int i = e % Lc, j = e / Lc;
+            C[j * CLD + i] -= sm.wC[i] * sm.v[j];
         }
     }
+    // first column of B_k becomes beta e1
+    for (int i = t; i < L; i += CH_THREADS) B[i] = (i == 0) ? sm.beta : 0.0;
     __syncthreads();
 
-    // ---- store back
+    // ---- store back (C only when no later step of this sweep takes it)
     for (int e = t; e < L * nbc; e += CH_THREADS) {
-        int i = e % L, j = e / L;
-        AB[(size_t)(c0 + j) * ldab + (r + i - c0 - j)] = sm.B[j * CLD + i];
+        const int i = e % L, j = e / L;
+        AB[(size_t)(c0 + j) * ldab + (r + i - c0 - j)] = B[j * CLD + i];
     }
     for (int e = t; e < L * L; e += CH_THREADS) {
-        int i = e % L, j = e / L;
-        if (i > j) AB[(size_t)(r + j) * ldab + (i - j)] = sm.D[j * CLD + i];
+        const int i = e % L, j = e / L;
+        if (i > j) AB[(size_t)(r + j) * ldab + (i - j)] = D[j * CLD + i];
     }
-    for (int e = t; e < Lc * L; e += CH_THREADS) {
-        int i = e % Lc, j = e / Lc;
-        AB[(size_t)(r + j) * ldab + (CB + i - j)] = sm.C[j * CLD + i];
-    }
+    if (!keep_c)
+        for (int e = t; e < Lc * L; e += CH_THREADS) {
+            const int i = e % Lc, j = e / Lc;
+            AB[(size_t)(r + j) * ldab + (CB + i - j)] = C[j * CLD + i];
+        }
 }
 
 __global__ void __launch_bounds__(CH_THREADS)
@@ -185,14 +181,23 @@ chase_kernel(int n, double* __restrict__ AB, int ldab, double* __restrict__ alph
     for (int s = blockIdx.x; s < nsw; s += gridDim.x) {
         const int ns = nsteps_of(n, CB, s);
         const int nsp = (s > 0) ? nsteps_of(n, CB, s - 1) : 0;
+        double* B = sm.buf[0];
+        double* D = sm.buf[1];
+        double* C = sm.buf[2];
+        bool have_b = false;
         for (int k = 0; k < ns; k++) {
             if (s > 0 && !sk_wait_flag_geq(prog + (s - 1), min(k + 3, nsp), status)) return;
-            chase_task(n, s, k, nsw, AB, ldab, alpha, Vtrd, tautrd, sm);
+            const bool keep_c = k + 1 < ns;  // step k+1 starts from this C
+            chase_task(n, s, k, nsw, AB, ldab, alpha, Vtrd, tautrd, B, D, C, have_b, keep_c, sm);
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
                 sk_st_release_s32(prog + s, k + 1);
             }
+            double* tmp = B;  // C_k is B_{k+1}
+            B = C;
+            C = tmp;
+            have_b = keep_c;
         }
     }
 }

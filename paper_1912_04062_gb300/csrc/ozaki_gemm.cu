@@ -105,7 +105,7 @@ SK_DEV void oz_digits(double x, int e, float (&d)[8]) {
         const int sh = 49 - 7 * i;
         const long long q = (sh > 0) ? ((M + (1LL << (sh - 1))) >> sh) : M;
         M -= q << sh;
-        d[i] = (float)q;
+        d[i] = (float)(int)q;  // |q| <= 128: a 32-bit conversion
     }
 }
 
