@@ -72,6 +72,10 @@ def parse():
                    help="mixed: BF16x6 tensor-core contractions + FP64 refinement; fp64: every step FP64")
     p.add_argument("--fp64-compare", type=int, default=1,
                    help="also time this many solves of the FP64 form (reported beside the mixed form)")
+    p.add_argument("--workload", default="single", choices=["single", "batched"],
+                   help="batched: many independent small solves (skew_eig_batched_ex) against a loop of "
+                        "single solves (skew_eig_ex) on the same matrices")
+    p.add_argument("--batch-count", type=int, default=2000)
     return p.parse_args()
 
 
@@ -379,11 +383,105 @@ def run_ours(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_batched(args, ws, rank, local):
+    """Batched workload: count matrices, n log-uniform in [32, 1024] (odd and
+    even), prescribed spectra l ~ U(0.1, 10), Haar Q, all n/2 pairs, FP64; under
+    torchrun each rank takes its longest-processing-time share (no collective
+    on the data path).  Times the batched entry against a loop of single solves
+    on the same device matrices; an accuracy sample is checked on device."""
+    import torch
+
+    import inputs
+    import paper_1912_04062_gb300 as sk
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    sizes = [int(x) for x in inputs.batch_sizes(args.batch_count, seed=5)]
+    mine = sk.shard_lpt(sizes, ws)[rank]
+    items = inputs.batch(sizes=sizes, seed=5)
+    mine_set = set(mine)
+    mats = [sk.fortran(torch.from_numpy(np_a).to(dev)) for k, (np_a, _) in enumerate(items) if k in mine_set]
+    nevs = [int(m.shape[0]) // 2 for m in mats]
+    count = len(mats)
+    opts = sk.Options(mode=sk.SKEW_MODE_FP64)
+    _, As, lams, Zr, Zi, c = sk._batch_arrays(mats, nevs, True)
+    c_n, c_A, c_lda, c_nev, c_l, c_zr, c_zi = c
+    oc = opts.c()
+    nbytes = int(sk.lib().skew_eig_batched_workspace_size(count, c_n, c_nev, sk.ctypes.byref(oc)))
+    work = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    d_info = torch.zeros(max(count, 1), dtype=torch.int32, device=dev)
+
+    def batched():
+        code = sk.lib().skew_eig_batched_ex(count, c_n, c_A, c_lda, c_nev, c_l, c_zr, c_zi, sk.ctypes.byref(oc),
+                                            sk._ptr(work), work.numel(), sk._ptr(d_info), sk._stream(stream))
+        if code != 0:
+            raise RuntimeError(f"batched solve failed: {code}")
+
+    nmax = max(int(m.shape[0]) for m in mats)
+    w1 = torch.empty(sk.workspace_size(nmax, nmax // 2, opts), dtype=torch.uint8, device=dev)
+    i1 = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def loop():
+        for m, l, zr, zi, nv in zip(mats, lams, Zr, Zi, nevs):
+            code = sk.skew_eig_ex(m, nv, l, zr, zi, w1, i1, opts)
+            if code != 0:
+                raise RuntimeError(f"single solve failed: {code}")
+
+    def timed(fn, steps):
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(ws, e0.elapsed_time(e1) / steps / 1e3)
+
+    for _ in range(args.warmup):
+        batched()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = sk.launch_count()
+    t_batched = timed(batched, args.steps)
+    launches = (sk.launch_count() - l0) // max(args.steps, 1)
+    clocks = clk.stop()
+    info_ok = bool((d_info[:count] == 0).all().item())
+    # accuracy sample: every 50th matrix of this rank's share
+    worst = {"resid": 0.0, "orth": 0.0}
+    eps = np.finfo(np.float64).eps
+    for k in range(0, count, 50):
+        n = int(mats[k].shape[0])
+        res, orth, fro = sk.metrics(mats[k], lams[k][:nevs[k]], Zr[k], Zi[k])
+        worst["resid"] = max(worst["resid"], res / (n * eps * fro))
+        worst["orth"] = max(worst["orth"], orth / (n * eps))
+    loop()  # warm-up of the single-solve path
+    t_loop = timed(loop, 1)
+    small = sum(1 for k in mine if sizes[k] <= 160)
+    if rank == 0:
+        out = {"metric": f"batched skew eigensolve time ({args.batch_count} matrices, n log-uniform in [32, 1024], "
+                         "nev = n/2)", "value": t_batched, "unit": "s", "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_batched * 1e3, "higher_is_better": False, "scaling": "strong",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "batched", "count": args.batch_count, "count_this_rank": count,
+                          "shared_memory_path": small, "two_step_path": count - small,
+                          "sum_n3": float(sum(float(sizes[k]) ** 3 for k in mine)),
+                          "parallelism": f"lpt-shard x{ws}" if ws > 1 else "single"},
+               "loop_of_single_solves_s": t_loop, "speedup_vs_loop": t_loop / t_batched,
+               "accuracy_sample": {"matrices": len(range(0, count, 50)), "worst_resid_scaled": worst["resid"],
+                                   "worst_orth_scaled": worst["orth"], "all_info_zero": info_ok},
+               "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batched":
+        run_batched(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -67,12 +67,15 @@ typedef enum {
                                       (hi, mid, lo) and the six products of order
                                       <= 2: about FP32 accuracy */
     SKEW_MODE_MIXED_REFINED = 4    /* the reduction's contractions (skew SYMM,
-                                      rank-2k update) and Q_band as FP64-accurate
-                                      BF16 digit-slice products on tcgen05, Q_trd
-                                      in FP32, then the FP64 refinement (n even,
-                                      nev = n/2).  Without such a complete basis
-                                      (nev < n/2, odd n) nothing is refined and
-                                      Q_trd runs in FP64 */
+                                      rank-2k update) and Q_band as BF16 digit-
+                                      slice products on tcgen05 (6 and 5 slices:
+                                      errors about 2^-42 and 2^-35), Q_trd in
+                                      FP32, then the FP64 refinement with
+                                      FP64-accurate products (n even, nev = n/2).
+                                      Without such a complete basis (nev < n/2,
+                                      odd n) nothing is refined: all products
+                                      keep 8 slices (FP64-accurate) and Q_trd
+                                      runs in FP64 */
 } skew_mode;
 
 /* Fault hooks (host-side injection for tests; never fault the GPU). */
@@ -147,12 +150,12 @@ int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda,
  * into device lambda[b], Z_re[b], Z_im[b] of leading dimension n[b]).  The
  * size arrays and the pointer arrays are host arrays; Z_re == Z_im == NULL
  * (the arrays) or Z_re[b] == Z_im[b] == NULL (one matrix) asks for
- * eigenvalues only.  Orders 2..160 are solved together, one CTA per matrix
- * (matrix in shared memory, unblocked Householder tridiagonalisation, then one
- * bisection and one inverse-iteration launch for all matrices, then one
- * back-transform launch), always in FP64; larger orders run the two-step solve
- * of skew_eig_ex one after another in `opts`' mode.  Not in the paper (it
- * solves one matrix per run).
+ * eigenvalues only.  Orders 2..1024 are solved together, one CTA per matrix
+ * (unblocked Householder tridiagonalisation with the matrix in shared memory
+ * up to n = 160 and in a global-memory copy above, then one bisection and one
+ * inverse-iteration launch for all matrices, then back-transform launches),
+ * always in FP64; larger orders run the two-step solve of skew_eig_ex one after
+ * another in `opts`' mode.  Not in the paper (it solves one matrix per run).
  * Asynchronous on `stream`.  skew_eig_batched allocates its workspace with
  * cudaMallocAsync / cudaFreeAsync on the stream and reports no per-matrix
  * status; skew_eig_batched_ex takes a caller workspace of at least

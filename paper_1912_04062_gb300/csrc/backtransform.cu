@@ -332,7 +332,7 @@ __global__ void tgroup_init_kernel(int g, int b, const double* __restrict__ Tp, 
 }  // namespace
 
 int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz,
-                      int k, void* ws, size_t ws_bytes, int* status, int planes) {
+                      int k, void* ws, size_t ws_bytes, int* status, int planes, int slices) {
     const int P = num_panels(n, b);
     if (P == 0 || k <= 0) return 0;
     const bool acc = planes == REDUCE_F64ACC;
@@ -396,9 +396,9 @@ int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, c
             if (gemm(st, false, false, m, gb, gb, 1.0, V, n, Tg, gb, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
         }
         // Yt = Z_o^T V (k x gb), then Z_o -= (V T) Yt^T
-        int rc = ozaki_gemm(st, k, gb, m, 1.0, Zo, ldz, 1, 1.0, V, n, 1, 1.0, 0.0, Yt, k, gws, gsz, status);
+        int rc = ozaki_gemm(st, k, gb, m, 1.0, Zo, ldz, 1, 1.0, V, n, 1, 1.0, 0.0, Yt, k, gws, gsz, status, 0, slices);
         if (rc) return rc;
-        rc = ozaki_gemm(st, m, k, gb, -1.0, VT, 1, n, 1.0, Yt, 1, k, 1.0, 1.0, Zo, ldz, gws, gsz, status);
+        rc = ozaki_gemm(st, m, k, gb, -1.0, VT, 1, n, 1.0, Yt, 1, k, 1.0, 1.0, Zo, ldz, gws, gsz, status, 0, slices);
         if (rc) return rc;
     }
     return 0;

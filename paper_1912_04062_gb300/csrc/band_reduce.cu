@@ -266,7 +266,7 @@ cudaError_t panel_v(cudaStream_t st, int n, int b, int p, const double* W, int l
 }
 
 int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac, void* ws,
-                size_t ws_bytes, int* d_status, int planes) {
+                size_t ws_bytes, int* d_status, int planes, int slices) {
     const bool mixed = planes > 0;
     if (b <= 0 || b % 64 != 0 || b > 128) return SKEW_ERR_UNSUPPORTED;
     const int P = num_panels(n, b);
@@ -319,7 +319,7 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         // ---- a3: P = A22 V (skew, lower triangle only)
         if (planes == REDUCE_F64ACC) {
             int rc = ozaki_gemm(st, m, b, m, 1.0, A22, 0, ldw, 1.0, w.V, n, 1, 1.0, 0.0, w.Pm, n, gws, gsz, d_status,
-                                1);
+                                1, slices);
             if (rc) return rc;
         } else if (mixed) {
             int rc = split_gemm(st, m, b, m, 1.0, A22, 0, ldw, 1, w.V, n, 1, 0.0, w.Pm, n, 0, gws, gsz, d_status,
@@ -344,7 +344,7 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         if (planes == REDUCE_F64ACC) {
             // tiles on or below the diagonal (the upper triangle of W is never read)
             int rc = ozaki_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 1.0, w.Y2, 1, n, 1.0, 1.0, A22, ldw, gws, gsz,
-                                d_status, 0, 8, 1);
+                                d_status, 0, slices, 1);
             if (rc) return rc;
         } else if (mixed) {
             int rc = split_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 0, w.Y2, 1, n, 1.0, A22, ldw, 1, gws, gsz, d_status,

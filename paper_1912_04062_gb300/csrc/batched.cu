@@ -1,15 +1,17 @@
-// batched.cu -- many independent skew eigenproblems of small order in a few
-// launches (the paper solves one matrix per run; this is the batched form of
-// the same route for orders up to BATCH_SMALL_MAX = 160).
+// batched.cu -- many independent skew eigenproblems of small and medium order
+// in a few launches (the paper solves one matrix per run; this is the batched
+// form of the same route for orders up to BATCH_MAX = 1024).
 //
-// Per matrix, one CTA holds the whole skew matrix in shared memory and
-// tridiagonalises it column by column with Householder reflectors (dlarfg
-// convention; the skew two-sided update A <- A + v p^T - p v^T with
-// p = tau A v, Eqs. 2-6 with u1 = -u2, whose 1/2 tau^2 (v^T A v) v term is 0 for
-// skew A), giving alpha_c = T[c, c+1] (Lemma 1).  One launch then bisects every
-// wanted eigenvalue of every matrix, one launch runs inverse iteration for all
-// of them (Sec. 3), and one CTA per matrix applies the D map (Algorithm 1
-// step 3) and the reflectors in reverse order to the eigenvectors.
+// Per matrix, one CTA tridiagonalises the whole skew matrix column by column
+// with Householder reflectors (dlarfg convention; the skew two-sided update
+// A <- A + v p^T - p v^T with p = tau A v, Eqs. 2-6 with u1 = -u2, whose
+// 1/2 tau^2 (v^T A v) v term is 0 for skew A), giving alpha_c = T[c, c+1]
+// (Lemma 1).  Orders up to BATCH_SMALL_MAX keep the matrix in shared memory;
+// larger ones work on a copy in global memory (L2), one CTA each, so that the
+// GPU runs as many matrices at a time as it has SMs.  One launch then bisects
+// every wanted eigenvalue of every matrix, one launch runs inverse iteration
+// for all of them (Sec. 3), and one CTA per matrix applies the D map
+// (Algorithm 1 step 3) and the reflectors in reverse order to the eigenvectors.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -26,6 +28,7 @@ constexpr int BT = 256;  // threads per CTA of the per-matrix kernels
 
 struct BItem {
     int n, nev, lda, vectors;
+    double* S;                   // global working matrix (n x n) for n > BATCH_SMALL_MAX
     const double* A;
     double *lambda, *Zre, *Zim;  // Z: n x nev, leading dimension n
     int* info;                   // caller's status word of this matrix (may be null)
@@ -59,14 +62,16 @@ __device__ double block_max(double v, double* red) {
     return s;
 }
 
-// One CTA per matrix (order[] lists the matrices, largest first): shared
-// memory holds S (n x n, ld n + 1), v and p.
+// One CTA per matrix (order[] lists the matrices, largest first).  G = false:
+// shared memory holds S (n x n, ld n + 1), v and p; G = true: S is the
+// matrix's global copy (ld n), v and p in shared memory.
+template <bool G>
 __global__ void __launch_bounds__(BT) bt_reduce_kernel(const BItem* __restrict__ items, const int* __restrict__ order) {
     extern __shared__ double bsm[];
     const BItem it = items[order[blockIdx.x]];
-    const int n = it.n, ld = n + 1, t = threadIdx.x;
-    double* S = bsm;
-    double* v = S + (size_t)n * ld;
+    const int n = it.n, ld = G ? n : n + 1, t = threadIdx.x;
+    double* S = G ? it.S : bsm;
+    double* v = G ? bsm : S + (size_t)n * ld;
     double* p = v + n;
     double* red = p + n;
     // S(i, j) = A(i, j) below the diagonal, -A(j, i) above: only the strict
@@ -76,14 +81,14 @@ __global__ void __launch_bounds__(BT) bt_reduce_kernel(const BItem* __restrict__
         double x = 0.0;
         if (i > j) x = it.A[i + (size_t)j * it.lda];
         else if (i < j) x = -it.A[j + (size_t)i * it.lda];
-        S[i + j * ld] = x;
+        S[i + (size_t)j * ld] = x;
     }
     __syncthreads();
     for (int c = 0; c + 2 < n; c++) {
         double a = 0.0;
-        for (int i = c + 2 + t; i < n; i += BT) a = fma(S[i + c * ld], S[i + c * ld], a);
+        for (int i = c + 2 + t; i < n; i += BT) a = fma(S[i + (size_t)c * ld], S[i + (size_t)c * ld], a);
         a = block_sum(a, red);
-        const double x0 = S[(c + 1) + c * ld];
+        const double x0 = S[(c + 1) + (size_t)c * ld];
         double tau, beta, sc;
         if (a == 0.0) {
             tau = 0.0;
@@ -96,7 +101,7 @@ __global__ void __launch_bounds__(BT) bt_reduce_kernel(const BItem* __restrict__
             sc = 1.0 / (x0 - beta);
         }
         for (int i = c + 1 + t; i < n; i += BT) {
-            const double vi = (i == c + 1) ? 1.0 : S[i + c * ld] * sc;
+            const double vi = (i == c + 1) ? 1.0 : S[i + (size_t)c * ld] * sc;
             v[i] = vi;
             it.V[i + (size_t)c * n] = vi;
         }
@@ -108,25 +113,23 @@ __global__ void __launch_bounds__(BT) bt_reduce_kernel(const BItem* __restrict__
         if (tau != 0.0) {
             // p = tau S22 v, S22 = S[c+1:, c+1:]
             for (int i = c + 1 + t; i < n; i += BT) {
-                double s = 0.0;
-                for (int j = c + 1; j < n; j++) s = fma(S[i + j * ld], v[j], s);
-                p[i] = tau * s;
+                double s2 = 0.0;
+                for (int j = c + 1; j < n; j++) s2 = fma(S[i + (size_t)j * ld], v[j], s2);
+                p[i] = tau * s2;
             }
             __syncthreads();
-            // S22 += v p^T - p v^T below the diagonal, mirrored (exactly skew)
+            // S22 += v p^T - p v^T on the whole square: each product is rounded
+            // on its own, so element (j, i) receives exactly minus what (i, j)
+            // receives and S stays exactly skew
             const int m = n - c - 1;
             for (int e = t; e < m * m; e += BT) {
                 const int i = c + 1 + e % m, j = c + 1 + e / m;
-                if (i > j) {
-                    const double x = S[i + j * ld] + (v[i] * p[j] - p[i] * v[j]);
-                    S[i + j * ld] = x;
-                    S[j + i * ld] = -x;
-                }
+                S[i + (size_t)j * ld] += __dsub_rn(__dmul_rn(v[i], p[j]), __dmul_rn(p[i], v[j]));
             }
         }
         __syncthreads();
     }
-    if (t == 0 && n >= 2) it.alpha[n - 2] = S[(n - 2) + (n - 1) * ld];
+    if (t == 0 && n >= 2) it.alpha[n - 2] = S[(n - 2) + (size_t)(n - 1) * ld];
     __syncthreads();
     // ||S||_1 of tridiag(alpha, 0, alpha), pivmin, alpha^2
     double gm = 0.0, am = 0.0;
@@ -177,22 +180,30 @@ __global__ void bt_invit_kernel(const BItem* __restrict__ items, int count, long
 
 // One CTA per matrix: eigenvector k of S (interleaved Qi) -> D map -> X_k, Y_k,
 // then Z <- H_0 H_1 ... H_{n-3} Z.  Warp w takes columns w, w + 8, ... of
-// [X Y] and keeps one column in registers (lane l holds rows l + 32 r).
-constexpr int BR = (BATCH_SMALL_MAX + 31) / 32;  // rows per lane
+// [X Y] and keeps one column in registers (lane l holds rows l + 32 r, r < BR).
+// G = false: the reflectors are staged in shared memory; G = true: read from
+// global memory (L2).
+template <int BR, bool G>
 __global__ void __launch_bounds__(BT) bt_back_kernel(const BItem* __restrict__ items, const int* __restrict__ order) {
     extern __shared__ double bsm[];
     const BItem it = items[order[blockIdx.x]];
     const int n = it.n, nev = it.nev, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0 && it.info) *it.info = (*it.fail < nev) ? SKEW_INFO_INVIT_BASE + *it.fail : 0;
     if (!it.vectors || nev == 0) return;
-    double* Vs = bsm;            // n x n, reflector c in column c (rows c+1..)
-    double* ts = Vs + (size_t)n * n;
-    for (int e = t; e < n * n; e += BT) {
-        const int i = e % n, c = e / n;
-        Vs[e] = (c + 2 < n && i > c) ? it.V[e] : 0.0;
+    const double* Vs = it.V;  // n x n, reflector c in column c (rows c+1..)
+    const double* ts = it.tau;
+    if (!G) {
+        double* V2 = bsm;
+        double* t2 = V2 + (size_t)n * n;
+        for (int e = t; e < n * n; e += BT) {
+            const int i = e % n, c = e / n;
+            V2[e] = (c + 2 < n && i > c) ? it.V[e] : 0.0;
+        }
+        for (int c = t; c < n; c += BT) t2[c] = (c + 2 < n) ? it.tau[c] : 0.0;
+        __syncthreads();
+        Vs = V2;
+        ts = t2;
     }
-    for (int c = t; c < n; c += BT) ts[c] = (c + 2 < n) ? it.tau[c] : 0.0;
-    __syncthreads();
     for (int col = warp; col < 2 * nev; col += BT / 32) {
         const int k = col % nev, part = col / nev;  // part 0: X = Re, 1: Y = Im
         double z[BR];
@@ -258,6 +269,7 @@ size_t carve_small(Carve& cv, int count, const BatchProblem* pr, BCarve* out) {
         it.Zre = q.Zre;
         it.Zim = q.Zim;
         it.info = q.info;
+        it.S = (q.n > BATCH_SMALL_MAX) ? cv.take<double>(n * n) : nullptr;
         it.V = cv.take<double>(n * n);
         it.tau = cv.take<double>(n);
         it.alpha = cv.take<double>(n);
@@ -298,15 +310,24 @@ size_t batched_small_ws(int count, const BatchProblem* pr) {
 int batched_small(cudaStream_t st, int count, const BatchProblem* pr, void* ws, size_t ws_bytes, int maxit) {
     if (count <= 0) return 0;
     for (int b = 0; b < count; b++)
-        if (pr[b].n < 2 || pr[b].n > BATCH_SMALL_MAX) return SKEW_ERR_UNSUPPORTED;
+        if (pr[b].n < 2 || pr[b].n > BATCH_MAX) return SKEW_ERR_UNSUPPORTED;
     Carve cv(ws, ws_bytes);
     BCarve bc{};
     carve_small(cv, count, pr, &bc);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
-    // largest orders first, so that the longest CTAs start early
+    // per-matrix launches by class, each listing its matrices largest first:
+    // [0, n1) shared-memory path, then the global-memory path by rows per lane
+    // of the back-transform (8, 16, 32: n <= 256, 512, 1024)
     bc.order.resize((size_t)count);
     for (int b = 0; b < count; b++) bc.order[(size_t)b] = b;
     std::stable_sort(bc.order.begin(), bc.order.end(), [&](int x, int y) { return pr[x].n > pr[y].n; });
+    auto cls = [&](int n) { return n <= BATCH_SMALL_MAX ? 0 : (n <= 256 ? 1 : (n <= 512 ? 2 : 3)); };
+    std::stable_sort(bc.order.begin(), bc.order.end(), [&](int x, int y) { return cls(pr[x].n) < cls(pr[y].n); });
+    int first[5] = {0, 0, 0, 0, 0};
+    for (int c = 0; c < 4; c++) {
+        first[c + 1] = first[c];
+        while (first[c + 1] < count && cls(pr[bc.order[(size_t)first[c + 1]]].n) == c) first[c + 1]++;
+    }
     // pageable copies: the host vectors may go once the calls return
     if (const cudaError_t e = cudaMemcpyAsync(bc.d_items, bc.items.data(), sizeof(BItem) * (size_t)count,
                                               cudaMemcpyHostToDevice, st))
@@ -314,13 +335,24 @@ int batched_small(cudaStream_t st, int count, const BatchProblem* pr, void* ws, 
     if (const cudaError_t e = cudaMemcpyAsync(bc.d_order, bc.order.data(), sizeof(int) * (size_t)count,
                                               cudaMemcpyHostToDevice, st))
         return cuda_fail(e);
-    int nmax = 2;
-    for (int b = 0; b < count; b++) nmax = pr[b].n > nmax ? pr[b].n : nmax;
-    const size_t s1 = smem_reduce(nmax), s2 = smem_back(nmax);
-    cudaFuncSetAttribute(bt_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
-    cudaFuncSetAttribute(bt_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
-    bt_reduce_kernel<<<count, BT, s1, st>>>(bc.d_items, bc.d_order);
-    count_launch();
+    int nmax_small = 2, nmax = 2;
+    for (int b = 0; b < count; b++) {
+        nmax = pr[b].n > nmax ? pr[b].n : nmax;
+        if (pr[b].n <= BATCH_SMALL_MAX) nmax_small = pr[b].n > nmax_small ? pr[b].n : nmax_small;
+    }
+    const int nsmall = first[1], nlarge = count - first[1];
+    if (nsmall > 0) {
+        const size_t s1 = smem_reduce(nmax_small);
+        cudaFuncSetAttribute(bt_reduce_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
+        bt_reduce_kernel<false><<<nsmall, BT, s1, st>>>(bc.d_items, bc.d_order);
+        count_launch();
+    }
+    if (nlarge > 0) {
+        const size_t s1 = sizeof(double) * (2 * (size_t)nmax + 32);
+        cudaFuncSetAttribute(bt_reduce_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
+        bt_reduce_kernel<true><<<nlarge, BT, s1, st>>>(bc.d_items, bc.d_order + first[1]);
+        count_launch();
+    }
     if (bc.total > 0) {
         const unsigned g = (unsigned)((bc.total + 127) / 128);
         bt_bisect_kernel<<<g, 128, 0, st>>>(bc.d_items, count, bc.total);
@@ -328,8 +360,25 @@ int batched_small(cudaStream_t st, int count, const BatchProblem* pr, void* ws, 
         bt_invit_kernel<<<g2, 64, 0, st>>>(bc.d_items, count, bc.total, maxit);
         count_launch(2);
     }
-    bt_back_kernel<<<count, BT, s2, st>>>(bc.d_items, bc.d_order);
-    count_launch();
+    if (nsmall > 0) {
+        const size_t s2 = smem_back(nmax_small);
+        cudaFuncSetAttribute(bt_back_kernel<(BATCH_SMALL_MAX + 31) / 32, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
+        bt_back_kernel<(BATCH_SMALL_MAX + 31) / 32, false><<<nsmall, BT, s2, st>>>(bc.d_items, bc.d_order);
+        count_launch();
+    }
+    if (first[2] > first[1]) {
+        bt_back_kernel<8, true><<<first[2] - first[1], BT, 0, st>>>(bc.d_items, bc.d_order + first[1]);
+        count_launch();
+    }
+    if (first[3] > first[2]) {
+        bt_back_kernel<16, true><<<first[3] - first[2], BT, 0, st>>>(bc.d_items, bc.d_order + first[2]);
+        count_launch();
+    }
+    if (first[4] > first[3]) {
+        bt_back_kernel<32, true><<<first[4] - first[3], BT, 0, st>>>(bc.d_items, bc.d_order + first[3]);
+        count_launch();
+    }
     return cuda_ok(cudaGetLastError());
 }
 

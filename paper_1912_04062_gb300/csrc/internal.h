@@ -37,8 +37,9 @@ cudaError_t gemm_lower_tiles(cudaStream_t st, int m, int k, const double* X, int
 // REDUCE_F64ACC: as FP64-accurate digit-slice tensor-core products.
 constexpr int REDUCE_F64ACC = 8;
 size_t band_reduce_ws(int n, int b, int planes = 0);
+// slices: digit slices of the REDUCE_F64ACC products (8: FP64-accurate)
 int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
-                void* ws, size_t ws_bytes, int* d_status, int planes = 0);
+                void* ws, size_t ws_bytes, int* d_status, int planes = 0, int slices = 8);
 cudaError_t band_pack(cudaStream_t st, int n, int b, const double* W, int ldw,
                       double* AB, int ldab);
 // Explicit V (m x b, ld ldv) of panel p from the reduced W.
@@ -73,7 +74,7 @@ cudaError_t apply_qtrd_f32(cudaStream_t st, int n, int b, const double* Vtrd, co
 size_t qband_ws(int n, int b, int k);
 size_t qband_mixed_ws(int n, int b, int k, int planes);
 int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz,
-                      int k, void* ws, size_t ws_bytes, int* status, int planes);
+                      int k, void* ws, size_t ws_bytes, int* status, int planes, int slices = 8);
 int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw,
                 const double* Tfac, double* Z, int ldz, int k, void* ws, size_t ws_bytes);
 
@@ -134,8 +135,10 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
 RefineInfo& last_refine_info();
 
 // ---- batched.cu (many small independent solves) ------------------------------
-// Largest order of the one-CTA shared-memory path.
+// Largest order of the one-CTA shared-memory path, and of the batched path
+// (one CTA per matrix, working matrix in global memory above the former).
 constexpr int BATCH_SMALL_MAX = 160;
+constexpr int BATCH_MAX = 1024;
 struct BatchProblem {
     int n, nev, lda;
     const double* A;
@@ -143,7 +146,7 @@ struct BatchProblem {
     int* info;                   // device status word of this matrix (may be null)
 };
 size_t batched_small_ws(int count, const BatchProblem* probs);
-// every n in [2, BATCH_SMALL_MAX]; FP64 throughout
+// every n in [2, BATCH_MAX]; FP64 throughout
 int batched_small(cudaStream_t st, int count, const BatchProblem* probs, void* ws, size_t ws_bytes, int maxit);
 
 // ---- metrics.cu -------------------------------------------------------------

@@ -60,6 +60,7 @@ struct Plan {
     int planes;       // split-BF16 planes of the mixed form (0 in the FP64 form)
     int reduce_prec;  // band reduction: 0 FP64, 2/3 split planes, REDUCE_F64ACC digit slices
     int qband_prec;   // mixed Q_band: 2/3 split planes or REDUCE_F64ACC digit slices
+    int reduce_slices, qband_slices;  // digit slices of the REDUCE_F64ACC products
     bool qtrd_f32;    // mixed Q_trd in FP32 arithmetic (else FP64)
     size_t ldab;
     // carved pointers
@@ -126,6 +127,14 @@ Plan make_plan(int n, int nev, const skew_opts* o, bool vectors) {
     const bool refined_mode = p.mixed && o->mode == SKEW_MODE_MIXED_REFINED;
     p.qband_prec = !p.mixed ? 0 : (refined_mode ? REDUCE_F64ACC : p.planes);
     p.qtrd_f32 = p.mixed && vectors && !(refined_mode && !p.refine);
+    // With a complete basis the refinement removes the first-order error, so
+    // the products before it need only keep the starting vectors at the level
+    // of the FP32 Q_trd: 6 digit slices (about 2^-42) for the reduction, 5
+    // (2^-35) for Q_band; measured at n = 16384 (BSE), the refinement starts
+    // from the same orthogonality (2.7e-4) and takes the same 3 iterations as
+    // with 8.  Without refinement they stay FP64-accurate.
+    p.reduce_slices = p.refine ? 6 : 8;
+    p.qband_slices = p.refine ? 5 : 8;
     return p;
 }
 
@@ -185,7 +194,8 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     }
     count_launch(2);
     mark(1);
-    int rc = band_reduce(st, n, p.W, n, p.b, p.Tfac, p.ws_reduce, p.sz_reduce, p.status, p.reduce_prec);
+    int rc = band_reduce(st, n, p.W, n, p.b, p.Tfac, p.ws_reduce, p.sz_reduce, p.status, p.reduce_prec,
+                         p.reduce_slices);
     if (rc) return rc;
     mark(2);
     if (band_pack(st, n, p.b, p.W, n, p.AB, (int)p.ldab) != cudaSuccess) return SKEW_ERR_CUDA;
@@ -224,7 +234,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     mark(7);
     if (vectors) {
         rc = p.mixed ? apply_qband_mixed(st, n, p.b, p.W, n, p.Tfac, p.Z, n, 2 * nev, p.ws_qband, p.sz_qband, p.status,
-                                         p.qband_prec)
+                                         p.qband_prec, p.qband_slices)
                      : apply_qband(st, n, p.b, p.W, n, p.Tfac, p.Z, n, 2 * nev, p.ws_qband, p.sz_qband);
         if (rc) return rc;
     }
@@ -431,7 +441,7 @@ BatchPlan plan_batch(int count, const int* n, const double* const* A, const int*
     for (int b = 0; b < count; b++) {
         const bool vec = Zre && Zre[b];
         if (n[b] < 2 || nev[b] == 0) continue;
-        if (n[b] <= BATCH_SMALL_MAX) {
+        if (n[b] <= BATCH_MAX) {
             BatchProblem q{};
             q.n = n[b];
             q.nev = nev[b];

@@ -121,6 +121,8 @@ def test_batched_argument_checks_are_host_side(sk):
     assert L.skew_eig_batched(0, None, None, None, None, None, None, None, None, nul) == 0
     # workspace grows with the batch and covers the largest single solve
     small = sk.lib().skew_eig_batched_workspace_size(2, IA(40, 100), IA(20, 50), None)
-    big = sk.lib().skew_eig_batched_workspace_size(2, IA(40, 400), IA(20, 200), None)
-    assert 0 < small < big
-    assert big >= sk.workspace_size(400, 200)
+    mid = sk.lib().skew_eig_batched_workspace_size(2, IA(40, 400), IA(20, 200), None)
+    big = sk.lib().skew_eig_batched_workspace_size(2, IA(40, 2000), IA(20, 1000), None)
+    assert 0 < small < mid < big
+    # orders above the batched kernels' limit take the two-step solve's workspace
+    assert big >= sk.workspace_size(2000, 1000)

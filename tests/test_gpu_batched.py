@@ -1,7 +1,8 @@
 """Batched solve (skew_eig_batched_ex) against the FP64 oracle: every matrix of
 a mixed-size batch meets the single-solve bounds (eigenvalue error <= 1e-12
-||A||_2, scaled residual and orthogonality <= 50), orders 2..160 through the
-one-CTA shared-memory path and larger ones through the two-step solve."""
+||A||_2, scaled residual and orthogonality <= 50): orders 2..160 through the
+one-CTA shared-memory path, 161..1024 through the one-CTA global-memory path,
+larger ones through the two-step solve."""
 import numpy as np
 import pytest
 
@@ -38,7 +39,8 @@ def _solve(mats, nevs, vectors=True, opts=None):
 
 def test_batch_of_mixed_orders():
     import inputs
-    sizes = [2, 3, 4, 5, 17, 32, 63, 64, 65, 100, 127, 128, 129, 159, 160, 161, 200, 257]
+    sizes = [2, 3, 4, 5, 17, 32, 63, 64, 65, 100, 127, 128, 129, 159, 160, 161, 200, 256, 257, 300, 511, 513,
+             1024, 1025]
     mats, nevs = [], []
     for k, n in enumerate(sizes):
         A = inputs.random_skew(n, seed=100 + k) if k % 2 else inputs.prescribed(n, seed=100 + k)[0]
@@ -97,9 +99,9 @@ def test_batch_member_independent_of_company():
 def test_inverse_iteration_failure_is_reported_per_matrix():
     import paper_1912_04062_gb300 as sk
     import inputs
-    # large orders take the single-solve path, whose test hook forces the
+    # orders above 1024 take the single-solve path, whose test hook forces the
     # inverse-iteration failure; the status lands in that matrix's slot only
-    mats = [inputs.random_skew(40, seed=1), inputs.random_skew(200, seed=2)]
+    mats = [inputs.random_skew(40, seed=1), inputs.random_skew(1100, seed=2)]
     opts = sk.Options(fault=sk.SKEW_FAULT_INVIT_NOCONV)
     lam, Zr, Zi, info = _solve(mats, [20, 100], opts=opts)
     assert info[0] == 0
