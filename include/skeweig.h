@@ -232,9 +232,10 @@ int skew_gemm_bf16x3(int M, int N, int K, double alpha, const double* A,
  * eigenpair refinement of the mixed form:  C = alpha * A B^T + beta * C.
  * Each row of A and of B is scaled by a power of two and cut into 8 digit
  * slices of 7 bits (integers BF16 holds exactly); slice products of equal
- * order are summed exactly in FP32 over K groups of 256 and folded in
- * double-float (about 48 bits), so the error is a few units of 2^-48 times
- * the row-max products, independent of cancellation.  Not in the paper.
+ * order are summed in FP32 over K groups of 512 (exactly for the six leading
+ * orders) and folded in double-float (about 48 bits), so the error is a few
+ * units of 2^-48 times the row-max products, independent of cancellation.
+ * Not in the paper.
  * Layouts and argument numbering as skew_gemm_bf16x3 (no lower mode).
  * skew_gemm_f64acc_ex adds: slices (1..8; the products of slice pairs of
  * order < slices are kept, error about 2^-7 slices of the row-max products,

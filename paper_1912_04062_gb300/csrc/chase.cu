@@ -25,7 +25,9 @@ namespace {
 
 constexpr int CB = 64;          // band width handled by the kernel
 constexpr int CLD = CB + 1;     // padded leading dimension in shared memory
-constexpr int CH_THREADS = 256;
+constexpr int CH_THREADS = 512;
+constexpr int CH_NQ = CH_THREADS / 64;  // row groups of the dot products
+constexpr int CH_QR = 64 / CH_NQ;       // rows per group
 
 __host__ __device__ inline int nsteps_of(int n, int b, int s) {
     return (s <= n - 3) ? 1 + (n - 3 - s) / b : 0;
@@ -35,7 +37,7 @@ struct ChaseSmem {
     double buf[3][CB * CLD];  // B, D and C of the current step (B and C trade places)
     double v[CB];
     double wB[CB], wD[CB], wC[CB];
-    double red[3][4 * CB];
+    double red[3][CH_NQ * CB];
     double tau, beta;
 };
 
@@ -110,12 +112,12 @@ __device__ void chase_task(int n, int s, int k, int nsw, double* __restrict__ AB
         }
     }
 
-    const int jj = t & (CB - 1), q = t >> 6;  // column/row index and quarter
+    const int jj = t & (CB - 1), q = t >> 6;  // column/row index and row group
     if (tau != 0.0) {
-        // ---- partial dots of the three updates (quarters of 16)
+        // ---- partial dots of the three updates (CH_NQ row groups of CH_QR)
         {
             double aB = 0.0, aD = 0.0, aC = 0.0;
-            const int lo = q * 16, hi = min(L, q * 16 + 16);
+            const int lo = q * CH_QR, hi = min(L, q * CH_QR + CH_QR);
             if (nbc > 1 && jj >= 1)  // (v^T B)_j
                 for (int i = lo; i < hi; i++) aB = fma(sm.v[i], B[jj * CLD + i], aB);
             if (jj < L)              // (D v)_i, D skew from its lower part
@@ -130,10 +132,12 @@ __device__ void chase_task(int n, int s, int k, int nsw, double* __restrict__ AB
             sm.red[2][q * CB + jj] = aC;
         }
         __syncthreads();
-        if (t < CB) {
-            sm.wB[t] = tau * (sm.red[0][t] + sm.red[0][CB + t] + sm.red[0][2 * CB + t] + sm.red[0][3 * CB + t]);
-            sm.wD[t] = tau * (sm.red[1][t] + sm.red[1][CB + t] + sm.red[1][2 * CB + t] + sm.red[1][3 * CB + t]);
-            sm.wC[t] = tau * (sm.red[2][t] + sm.red[2][CB + t] + sm.red[2][2 * CB + t] + sm.red[2][3 * CB + t]);
+        if (t < 3 * CB) {
+            const int which = t / CB, col = t % CB;
+            double acc = 0.0;
+#pragma unroll
+            for (int h = 0; h < CH_NQ; h++) acc += sm.red[which][h * CB + col];
+            (which == 0 ? sm.wB : (which == 1 ? sm.wD : sm.wC))[col] = tau * acc;
         }
         __syncthreads();
         // ---- updates: B[:, 1:] -= v wB^T; D += v p^T - p v^T (p = wD = tau D v;

@@ -82,7 +82,7 @@ SK_DEV bool sk_wait_flag_geq(const int* flag, int want, int* status) {
                 ok = 0;
                 break;
             }
-            __nanosleep(128);
+            __nanosleep(32);
         }
         if (!ok) sk_set_error(status, SKEW_ERR_DEVICE_TIMEOUT);
         s_ok = ok;

@@ -16,12 +16,13 @@
 // T_L = sum_{i+j=L} D_i E_j^T over the kept levels L < s (s = 8: 36 slice
 // pairs, the dropped ones below 2^-63 of |a_r|max |b_c|max per term; fewer
 // slices give a cheaper product accurate to about 2^-7s).  The level sums are
-// taken over K groups of 256: level 0 is a sum of 256 products of size
-// <= 2^14, level L >= 1 of 256 (L + 3) 2^12-sized terms (two pairs with a
-// leading digit, |d_0| <= 128), both below 2^24, so FP32 accumulation in TMEM
-// is exact.  After each group the level accumulators (s x 64 TMEM columns)
-// are folded into a double-float (two FP32) running sum per output, which
-// carries about 48 bits.
+// taken over K groups of 512: level 0 is a sum of 512 products of size
+// <= 2^14, level L >= 1 of 512 (L + 3) 2^12-sized terms (two pairs with a
+// leading digit, |d_0| <= 128), so levels 0..5 stay at or below 2^24 and are
+// exact in FP32; levels 6 and 7 may round by one unit of their own level,
+// below 2^-56 of |a_r|max |b_c|max per group.  After each group the level
+// accumulators (s x 64 TMEM columns) are folded into a double-float (two FP32)
+// running sum per output, which carries about 48 bits.
 //
 // Kernel: 128 x 64 output tile per CTA, 320 threads: warps 0-7 drain TMEM
 // (warp w: lanes 32 (w & 3).. = rows, columns 32 (w >> 2)..) and accumulate;
@@ -31,7 +32,7 @@
 // digit slices stream through a ring of NA one-slice stages.  Within a chunk,
 // pass i multiplies A slice i with B slices 0 .. S-1-i as one wide MMA (B
 // slices adjacent in shared memory, their levels adjacent in TMEM).
-// TMEM holds one level group (4 chunks = 256 of K), so the MMAs of the next
+// TMEM holds one level group (8 chunks = 512 of K), so the MMAs of the next
 // group start once the epilogue has drained it.
 // With `lower` set, tiles wholly above the diagonal (every column index above
 // every row index) are skipped: for symmetric or skew results whose upper
@@ -56,7 +57,7 @@ constexpr int OM = 128;      // tile rows
 constexpr int ON = 64;       // tile columns
 constexpr int OKA = 64;      // K per chunk = one 64-wide swizzle atom; K is padded to a multiple of it
 constexpr int NA = 6;        // A stages (one digit slice of one chunk each)
-constexpr int GRP = 4;       // chunks per exact level group (256 of K)
+constexpr int GRP = 8;       // chunks per level group (512 of K)
 constexpr int SL = 8;        // digit slices per operand
 constexpr int OT = 320;      // threads per CTA: 8 epilogue warps, TMA warp, MMA warp
 constexpr int OEPI = 256;    // epilogue threads
