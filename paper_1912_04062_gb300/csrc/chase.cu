@@ -25,8 +25,8 @@ namespace {
 
 constexpr int CB = 64;          // band width handled by the kernel
 constexpr int CLD = CB + 1;     // padded leading dimension in shared memory
-constexpr int CH_THREADS = 512;
-constexpr int CH_NQ = CH_THREADS / 64;  // row groups of the dot products
+constexpr int CH_THREADS = 1024;
+constexpr int CH_NQ = CH_THREADS / 64;  // row groups of the dot products (1 CTA per SM)
 constexpr int CH_QR = 64 / CH_NQ;       // rows per group
 
 __host__ __device__ inline int nsteps_of(int n, int b, int s) {
