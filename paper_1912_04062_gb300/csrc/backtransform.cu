@@ -313,10 +313,48 @@ static size_t qband_gemm_ws(int n, int b, int k, int planes) {
     return g1 > g2 ? g1 : g2;
 }
 
+// Split-K ranges of the group Gram product V^T V
+constexpr int QB_KS = 32;
+
+struct QbMixedWs {
+    double *V, *VT, *Yt, *Tg, *G, *tmp;
+    void* gws;
+    size_t gsz;
+    // FP64-accurate form: split-K partials, digit slices of V (rows = its
+    // columns), of V by rows and of T_g
+    double* part;
+    void *oz_v, *oz_a, *oz_t;
+    size_t oz_vb, oz_ab, oz_tb;
+};
+
+static QbMixedWs carve_qband_mixed(Carve& cv, int n, int b, int k, int planes) {
+    QbMixedWs q{};
+    const bool acc = planes == REDUCE_F64ACC;
+    const size_t w = acc ? (size_t)QG * b : (size_t)b;
+    q.V = cv.take<double>((size_t)n * w);
+    q.VT = cv.take<double>((size_t)n * w);
+    q.Yt = cv.take<double>((size_t)k * w);
+    q.Tg = cv.take<double>(w * w);
+    q.G = cv.take<double>(w * w);
+    q.tmp = cv.take<double>(w * w);
+    q.gsz = qband_gemm_ws(n, b, k, planes);
+    q.gws = cv.take<char>(q.gsz);
+    if (acc) {
+        q.part = cv.take<double>((size_t)QB_KS * w * w);
+        q.oz_vb = ozaki_operand_ws((int)w, n);
+        q.oz_v = cv.take<char>(q.oz_vb);
+        q.oz_ab = ozaki_operand_ws(n, (int)w);
+        q.oz_a = cv.take<char>(q.oz_ab);
+        q.oz_tb = ozaki_operand_ws((int)w, (int)w);
+        q.oz_t = cv.take<char>(q.oz_tb);
+    }
+    return q;
+}
+
 size_t qband_mixed_ws(int n, int b, int k, int planes) {
-    const size_t w = (planes == REDUCE_F64ACC) ? (size_t)QG * b : (size_t)b;
-    return align_up(sizeof(double) * (size_t)n * w) * 2 + align_up(sizeof(double) * (size_t)k * w) +
-           3 * align_up(sizeof(double) * w * w) + qband_gemm_ws(n, b, k, planes) + 256;
+    Carve cv(nullptr, ~size_t(0));
+    carve_qband_mixed(cv, n, b, k, planes);
+    return cv.off + 256;
 }
 
 namespace {
@@ -336,17 +374,12 @@ int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, c
     const int P = num_panels(n, b);
     if (P == 0 || k <= 0) return 0;
     const bool acc = planes == REDUCE_F64ACC;
-    const int w = acc ? QG * b : b;
     Carve cv(ws, ws_bytes);
-    double* V = cv.take<double>((size_t)n * w);
-    double* VT = cv.take<double>((size_t)n * w);
-    double* Yt = cv.take<double>((size_t)k * w);
-    double* Tg = cv.take<double>((size_t)w * w);
-    double* G = cv.take<double>((size_t)w * w);
-    double* tmp = cv.take<double>((size_t)w * w);
-    const size_t gsz = qband_gemm_ws(n, b, k, planes);
-    void* gws = cv.take<char>(gsz);
+    const QbMixedWs q = carve_qband_mixed(cv, n, b, k, planes);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
+    double *V = q.V, *VT = q.VT, *Yt = q.Yt, *Tg = q.Tg, *G = q.G, *tmp = q.tmp;
+    void* gws = q.gws;
+    const size_t gsz = q.gsz;
     if (!acc) {
         for (int p = P - 1; p >= 0; p--) {
             const int o = (p + 1) * b, m = n - o;
@@ -379,24 +412,43 @@ int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, c
             // T of the group
             tgroup_init_kernel<<<(gb * gb + 255) / 256, 256, 0, st>>>(g, b, Tfac + (size_t)p0 * b * b, Tg);
             count_launch();
-            if (g > 1) {
-                if (gemm(st, true, false, gb, gb, m, 1.0, V, n, V, n, 0.0, G, gb) != cudaSuccess) return SKEW_ERR_CUDA;
-                for (int j = 1; j < g; j++) {
-                    const int jb = j * b;
-                    const double* Tj = Tfac + (size_t)(p0 + j) * b * b;
-                    // tmp = (V_1..j-1^T V_j) T_j, then T[0:jb, jb:jb+b] = -T[0:jb, 0:jb] tmp
-                    if (gemm(st, false, false, jb, b, b, 1.0, G + (size_t)jb * gb, gb, Tj, b, 0.0, tmp, gb) !=
-                        cudaSuccess)
-                        return SKEW_ERR_CUDA;
-                    if (gemm(st, false, false, jb, b, jb, -1.0, Tg, gb, tmp, gb, 0.0, Tg + (size_t)jb * gb, gb) !=
-                        cudaSuccess)
-                        return SKEW_ERR_CUDA;
-                }
-            }
-            if (gemm(st, false, false, m, gb, gb, 1.0, V, n, Tg, gb, 0.0, VT, n) != cudaSuccess) return SKEW_ERR_CUDA;
         }
+        // digit slices of V with its gb columns as rows (K = m): the Gram
+        // product and Yt below
+        OzOperand ov{}, oa{}, ot{}, oz{};
+        int rc = ozaki_split(st, gb, m, V, n, 1, 1.0, 0, q.oz_v, q.oz_vb, &ov);
+        if (rc) return rc;
+        if (g > 1) {
+            // G = V^T V on the tensor cores (split K: a few output tiles, K = m)
+            int ks = ((m + 63) / 64 + 1) / 2;
+            if (ks > QB_KS) ks = QB_KS;
+            rc = ozaki_gemm_pre(st, ov, ov, 1.0, 0.0, G, gb, status, 8, 0, ks, q.part);
+            if (rc) return rc;
+            KtScope kt(st, KT_GEMM_F64);
+            for (int j = 1; j < g; j++) {
+                const int jb = j * b;
+                const double* Tj = Tfac + (size_t)(p0 + j) * b * b;
+                // tmp = (V_1..j-1^T V_j) T_j, then T[0:jb, jb:jb+b] = -T[0:jb, 0:jb] tmp
+                // (split K over 16-deep slices: these products have few output tiles)
+                if (gemm(st, false, false, jb, b, b, 1.0, G + (size_t)jb * gb, gb, Tj, b, 0.0, tmp, gb, b / 16) !=
+                    cudaSuccess)
+                    return SKEW_ERR_CUDA;
+                if (gemm(st, false, false, jb, b, jb, -1.0, Tg, gb, tmp, gb, 0.0, Tg + (size_t)jb * gb, gb,
+                         jb / 16) != cudaSuccess)
+                    return SKEW_ERR_CUDA;
+            }
+        }
+        // VT = V T_g (m x gb, K = gb)
+        rc = ozaki_split(st, m, gb, V, 1, n, 1.0, 0, q.oz_a, q.oz_ab, &oa);
+        if (rc) return rc;
+        rc = ozaki_split(st, gb, gb, Tg, gb, 1, 1.0, 0, q.oz_t, q.oz_tb, &ot);
+        if (rc) return rc;
+        rc = ozaki_gemm_pre(st, oa, ot, 1.0, 0.0, VT, n, status, 8);
+        if (rc) return rc;
         // Yt = Z_o^T V (k x gb), then Z_o -= (V T) Yt^T
-        int rc = ozaki_gemm(st, k, gb, m, 1.0, Zo, ldz, 1, 1.0, V, n, 1, 1.0, 0.0, Yt, k, gws, gsz, status, 0, slices);
+        rc = ozaki_split(st, k, m, Zo, ldz, 1, 1.0, 0, gws, gsz, &oz);
+        if (rc) return rc;
+        rc = ozaki_gemm_pre(st, oz, ov, 1.0, 0.0, Yt, k, status, slices);
         if (rc) return rc;
         rc = ozaki_gemm(st, m, k, gb, -1.0, VT, 1, n, 1.0, Yt, 1, k, 1.0, 1.0, Zo, ldz, gws, gsz, status, 0, slices);
         if (rc) return rc;

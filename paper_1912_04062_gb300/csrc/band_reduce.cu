@@ -25,7 +25,7 @@ namespace {
 constexpr int QR_THREADS = 256;
 
 // Per-column partial sums live in part[(buf * G + g) * (nb + 1) + c].
-__global__ void __launch_bounds__(QR_THREADS)
+__global__ void __launch_bounds__(QR_THREADS, 1)
 panel_qr_kernel(int m, int nb, double* __restrict__ P, int ldp, double* __restrict__ tau,
                 double* __restrict__ part, double* __restrict__ rowbuf, unsigned* bar,
                 int* status, int rpc) {
@@ -46,31 +46,48 @@ panel_qr_kernel(int m, int nb, double* __restrict__ P, int ldp, double* __restri
     }
     __syncthreads();
 
-    const int lane = t & 31, warp = t >> 5, nwarp = QR_THREADS / 32;
     const int ncol = min(nb, m);  // columns with a row on the diagonal
     for (int i = 0; i < ncol; i++) {
         const int buf = i & 1;
-        // ---- phase A: partial sums over owned rows with global index > i
+        // ---- phase A: partial sums over owned rows with global index > i;
+        // four threads per column (rows q, q+4, ..), two shuffle levels (the
+        // FP64 pipe, not the rows, bounds this loop)
         double* pp = part + ((size_t)buf * G + g) * (nb + 1);
-        for (int c = i + warp; c < nb; c += nwarp) {
-            double acc = 0.0;
-            for (int r = lane; r < rows; r += 32) {
-                if (r0 + r > i) acc = fma(S[(size_t)i * rpc + r], S[(size_t)c * rpc + r], acc);
+        for (int cb = i; cb < nb; cb += QR_THREADS / 4) {  // uniform trip count: every lane shuffles
+            const int c = cb + (t >> 2), q = t & 3;
+            const int rlo = max(0, i + 1 - r0);  // owned rows with global index > i
+            double a0 = 0.0, a1 = 0.0;
+            int r = (c < nb) ? rlo + ((q - rlo) & 3) : rows;
+            for (; r + 4 < rows; r += 8) {
+                a0 = fma(S[(size_t)i * rpc + r], S[(size_t)c * rpc + r], a0);
+                a1 = fma(S[(size_t)i * rpc + r + 4], S[(size_t)c * rpc + r + 4], a1);
             }
-            acc = sk_warp_sum(acc);
-            if (lane == 0) pp[c] = acc;
+            if (r < rows) a0 = fma(S[(size_t)i * rpc + r], S[(size_t)c * rpc + r], a0);
+            double acc = a0 + a1;
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (q == 0 && c < nb) pp[c] = acc;
         }
         if (r0 <= i && i < r0 + rows) {  // owner of row i publishes it
             for (int c = i + t; c < nb; c += QR_THREADS)
                 rowbuf[buf * nb + c] = S[(size_t)c * rpc + (i - r0)];
         }
         if (!sk_grid_barrier(bar, epoch, status)) return;
-        // ---- phase B: reduce partials (fixed order -> identical in all CTAs)
-        for (int c = i + t; c < nb; c += QR_THREADS) {
-            double acc = 0.0;
-            for (int h = 0; h < G; h++)
-                acc += __ldcg(part + ((size_t)buf * G + h) * (nb + 1) + c);
-            ws[c] = acc;  // ws[i] = ||x_tail||^2, ws[c>i] = x_tail . P_tail[:, c]
+        // ---- phase B: reduce partials, four threads per column over CTAs
+        // q, q+4, .. (a fixed order: identical in all CTAs)
+        for (int cb = i; cb < nb; cb += QR_THREADS / 4) {
+            const int c = cb + (t >> 2), q = t & 3;
+            double a0 = 0.0, a1 = 0.0;
+            int h = (c < nb) ? q : G;
+            for (; h + 4 < G; h += 8) {
+                a0 += __ldcg(part + ((size_t)buf * G + h) * (nb + 1) + c);
+                a1 += __ldcg(part + ((size_t)buf * G + h + 4) * (nb + 1) + c);
+            }
+            if (h < G) a0 += __ldcg(part + ((size_t)buf * G + h) * (nb + 1) + c);
+            double acc = a0 + a1;
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (q == 0 && c < nb) ws[c] = acc;  // ws[i] = ||x_tail||^2, ws[c>i] = x_tail . P_tail[:, c]
         }
         __syncthreads();
         if (t == 0) {
@@ -104,12 +121,13 @@ panel_qr_kernel(int m, int nb, double* __restrict__ P, int ldp, double* __restri
         }
         __syncthreads();
         if (tu != 0.0) {
-            const int nc = nb - i - 1;
-            for (int e = t; e < rows * nc; e += QR_THREADS) {
-                int r = e % rows, c = i + 1 + e / rows;
-                int gr = r0 + r;
-                if (gr > i) S[(size_t)c * rpc + r] -= tu * vs[r] * ws[c];
-                else if (gr == i) S[(size_t)c * rpc + r] -= tu * ws[c];
+            // row r (from t mod rg) x columns i+1+t/rg, step QR_THREADS/rg
+            const int rg = (rows <= QR_THREADS / 2) ? QR_THREADS / 2 : QR_THREADS;
+            for (int r = t % rg; r < rows; r += rg) {
+                const int gr = r0 + r;
+                if (gr < i) continue;
+                const double f = (gr > i) ? tu * vs[r] : tu;
+                for (int c = i + 1 + t / rg; c < nb; c += QR_THREADS / rg) S[(size_t)c * rpc + r] -= f * ws[c];
             }
         }
         if (r0 <= i && i < r0 + rows && t == 0) S[(size_t)i * rpc + (i - r0)] = s_beta;
@@ -137,27 +155,87 @@ __global__ void panel_v_kernel(int m, int nb, const double* __restrict__ P, int 
 
 // T (nb x nb upper, column-major) from tau and the Gram matrix G = V^T V:
 // T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i]   (Eq. 7, forward).
-__global__ void tfactor_kernel(int nb, const double* __restrict__ tau,
-                               const double* __restrict__ Gm, double* __restrict__ T) {
+// T of the compact WY form (Eq. 7): T(i, i) = tau_i and column i above the
+// diagonal T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i), G = V^T V, column by
+// column.  Four threads per row (k = row + q, row + q + 4, ..) and two
+// shuffle levels: on GB300 every FP64 warp instruction costs 16 SM cycles,
+// so the loops stop at each row's own length.  TFL = nb + 1 pads the rows.
+constexpr int TF_THREADS = 256;
+__global__ void __launch_bounds__(TF_THREADS) tfactor_kernel(int nb, const double* __restrict__ tau,
+                                                            const double* __restrict__ Gm, double* __restrict__ T) {
     extern __shared__ double sh[];
-    double* Ts = sh;              // nb x nb
-    double* col = sh + nb * nb;   // nb
+    const int ld = nb + 1;
+    const bool gsm = nb <= 64;   // G staged in shared memory (else read from L2)
+    double* Ts = sh;             // nb x nb, ld nb + 1
+    double* Gs = sh + nb * ld;   // nb x nb, ld nb + 1
     const int t = threadIdx.x;
-    for (int e = t; e < nb * nb; e += blockDim.x) Ts[e] = 0.0;
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        const int r = e % nb, c = e / nb;
+        Ts[c * ld + r] = 0.0;
+        if (gsm) Gs[c * ld + r] = Gm[(size_t)c * nb + r];
+    }
+    if (t == 0 && nb > 0) Ts[0] = tau[0];
     __syncthreads();
-    for (int i = 0; i < nb; i++) {
+    for (int i = 1; i < nb; i++) {
         const double ti = tau[i];
-        if (t < i) {
-            double acc = 0.0;
-            for (int k = t; k < i; k++) acc = fma(Ts[k * nb + t], Gm[(size_t)i * nb + k], acc);
-            col[t] = -ti * acc;
+        const double* gi = gsm ? Gs + i * ld : Gm + (size_t)i * nb;  // column i of G
+        // rows 0 .. i-1; warps with no such row skip the step (uniform per warp)
+        for (int rb = 0; rb < i; rb += TF_THREADS / 4) {
+            const int row = rb + (t >> 2), q = t & 3;
+            if ((rb + ((t & ~31) >> 2)) >= i) continue;  // first row of this warp is past the column
+            double a0 = 0.0, a1 = 0.0;
+            int k = row + q;
+            for (; k + 4 < i; k += 8) {
+                a0 = fma(Ts[k * ld + row], gi[k], a0);
+                a1 = fma(Ts[(k + 4) * ld + row], gi[k + 4], a1);
+            }
+            if (k < i) a0 = fma(Ts[k * ld + row], gi[k], a0);
+            double acc = a0 + a1;
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (q == 0 && row < i) Ts[i * ld + row] = -ti * acc;
         }
-        __syncthreads();
-        if (t < i) Ts[i * nb + t] = col[t];
-        if (t == 0) Ts[i * nb + i] = ti;
+        if (t == 0) Ts[i * ld + i] = ti;
         __syncthreads();
     }
-    for (int e = t; e < nb * nb; e += blockDim.x) T[e] = Ts[e];
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        const int r = e % nb, c = e / nb;
+        T[(size_t)c * nb + r] = Ts[c * ld + r];
+    }
+}
+size_t tfactor_smem(int nb) { return sizeof(double) * (nb <= 64 ? 2 : 1) * (size_t)nb * (nb + 1); }
+
+// From Q = P^T V and the T factor: C1 = V^T P T = Q^T T, C2 = T^T C1 and the
+// right factor Z = [-C2 / 2; T] (2 nb x nb, ld 2 nb) of W = [V P] Z = P T -
+// V C2 / 2 (Eq. 9).  One block per column j, one thread per row i.
+__global__ void wz_kernel(int nb, const double* __restrict__ Q, const double* __restrict__ T,
+                          double* __restrict__ Z) {
+    __shared__ double c1[128];
+    const int j = blockIdx.x, i = threadIdx.x;
+    if (i < nb) {
+        // C1(i, j) = sum_{k <= j} Q(k, i) T(k, j)   (T upper triangular)
+        double a0 = 0.0, a1 = 0.0;
+        int k = 0;
+        for (; k + 1 <= j; k += 2) {
+            a0 = fma(Q[(size_t)i * nb + k], T[(size_t)j * nb + k], a0);
+            a1 = fma(Q[(size_t)i * nb + k + 1], T[(size_t)j * nb + k + 1], a1);
+        }
+        if (k <= j) a0 = fma(Q[(size_t)i * nb + k], T[(size_t)j * nb + k], a0);
+        c1[i] = a0 + a1;
+    }
+    __syncthreads();
+    if (i < nb) {
+        // C2(i, j) = sum_{k <= i} T(k, i) C1(k, j)
+        double a0 = 0.0, a1 = 0.0;
+        int k = 0;
+        for (; k + 1 <= i; k += 2) {
+            a0 = fma(T[(size_t)i * nb + k], c1[k], a0);
+            a1 = fma(T[(size_t)i * nb + k + 1], c1[k + 1], a1);
+        }
+        if (k <= i) a0 = fma(T[(size_t)i * nb + k], c1[k], a0);
+        Z[(size_t)j * 2 * nb + i] = -0.5 * (a0 + a1);
+        Z[(size_t)j * 2 * nb + nb + i] = T[(size_t)j * nb + i];
+    }
 }
 
 // [V W] and [W -V] side by side for the rank-2k update (K = 2 nb).
@@ -203,9 +281,17 @@ inline int grid_for(size_t total) {
     return (int)(g > 8192 ? 8192 : (g == 0 ? 1 : g));
 }
 
+// Split-K ranges of the K = m products of the tensor-core form
+constexpr int KS_MAX = 256;
+
 struct ReduceWs {
     double *V, *Pm, *Y, *X2, *Y2, *G, *C1, *C2, *tau, *part, *rowbuf;
     unsigned* bar;
+    // tensor-core form: Z = [-C2/2; T], split-K partials of the main and side
+    // streams, digit slices of V, P, [V P] and Z
+    double *Z, *part_m, *part_s;
+    void *oz_v, *oz_p, *oz_vp, *oz_z;
+    size_t oz_vb, oz_vpb, oz_zb;
 };
 
 int qr_rows_per_cta(int m, int nb, int maxG) {
@@ -216,11 +302,11 @@ int qr_rows_per_cta(int m, int nb, int maxG) {
 
 size_t qr_smem_bytes(int rpc, int nb) { return sizeof(double) * ((size_t)rpc * nb + rpc + nb); }
 
-ReduceWs carve_reduce(Carve& cv, int n, int b) {
+ReduceWs carve_reduce(Carve& cv, int n, int b, bool f64acc) {
     ReduceWs w{};
     size_t mb = (size_t)n * b;
-    w.V = cv.take<double>(mb);
-    w.Pm = cv.take<double>(mb);
+    w.V = cv.take<double>(2 * mb);  // [V P]: P follows V with the same leading dimension n
+    w.Pm = w.V + mb;
     w.Y = cv.take<double>(mb);
     w.X2 = cv.take<double>(2 * mb);
     w.Y2 = cv.take<double>(2 * mb);
@@ -231,6 +317,18 @@ ReduceWs carve_reduce(Carve& cv, int n, int b) {
     w.part = cv.take<double>((size_t)2 * 1024 * (b + 1));
     w.rowbuf = cv.take<double>((size_t)2 * b);
     w.bar = cv.take<unsigned>(64);
+    if (f64acc) {
+        w.Z = cv.take<double>((size_t)2 * b * b);
+        w.part_m = cv.take<double>((size_t)KS_MAX * b * b);
+        w.part_s = cv.take<double>((size_t)KS_MAX * b * b);
+        w.oz_vb = ozaki_operand_ws(b, n);
+        w.oz_v = cv.take<char>(w.oz_vb);
+        w.oz_p = cv.take<char>(w.oz_vb);
+        w.oz_vpb = ozaki_operand_ws(n, 2 * b);
+        w.oz_vp = cv.take<char>(w.oz_vpb);
+        w.oz_zb = ozaki_operand_ws(b, 2 * b);
+        w.oz_z = cv.take<char>(w.oz_zb);
+    }
     return w;
 }
 
@@ -252,7 +350,7 @@ size_t mixed_gemm_ws(int n, int b, int planes) {
 
 size_t band_reduce_ws(int n, int b, int planes) {
     Carve cv(nullptr, ~size_t(0));
-    carve_reduce(cv, n, b);
+    carve_reduce(cv, n, b, planes == REDUCE_F64ACC);
     if (planes) cv.take<char>(mixed_gemm_ws(n, b, planes));
     return cv.off + 256;
 }
@@ -265,6 +363,92 @@ cudaError_t panel_v(cudaStream_t st, int n, int b, int p, const double* W, int l
     return cudaGetLastError();
 }
 
+namespace {
+
+// A second stream for the T factor, which needs only V: it runs beside the
+// SYMM and is joined before W is formed.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev_v = nullptr, ev_t = nullptr;
+    int init() {
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&ev_v, cudaEventDisableTiming) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&ev_t, cudaEventDisableTiming) != cudaSuccess) return SKEW_ERR_CUDA;
+        return 0;
+    }
+    ~SideStream() {
+        if (ev_v) cudaEventDestroy(ev_v);
+        if (ev_t) cudaEventDestroy(ev_t);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+// T factor and a3-a4 of one panel with every contraction on the tensor cores
+// (FP64-accurate digit-slice products; GB300 runs FP64 at ~1 TFLOP/s):
+//   side stream: G = V^T V (split K), T from G (Eq. 7);
+//   main stream: P = A22 V (Eq. 8, `slices` digit slices), Q = P^T V (split
+//   K), then C1 = V^T P T = Q^T T, C2 = T^T C1 and W = P T - V C2 / 2 =
+//   [V P] [-C2/2; T] (Eq. 9) as one product with K = 2b.
+int panel_update_f64acc(cudaStream_t st, SideStream& side, int n, int m, int b, const double* panel, int ldw,
+                        const double* A22, const double* taup, double* Tp, ReduceWs& w, void* gws, size_t gsz,
+                        int* status, int slices) {
+    {
+        KtScope kt(st, KT_GEMM_F64);
+        panel_v_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, panel, ldw, w.V, n);
+        count_launch();
+    }
+    // rows of these operands are the b columns of V (of P), K = m
+    OzOperand ov{}, op{}, oa{}, ovp{}, oz{};
+    int rc = ozaki_split(st, b, m, w.V, n, 1, 1.0, 0, w.oz_v, w.oz_vb, &ov);
+    if (rc) return rc;
+    const int nch = (m + 63) / 64;
+    int ks = (nch + 1) / 2;  // two 64-wide K chunks per CTA at least
+    if (ks > device_sms()) ks = device_sms();
+    if (ks > KS_MAX) ks = KS_MAX;
+    if (ks < 1) ks = 1;
+    if (cudaEventRecord(side.ev_v, st) != cudaSuccess || cudaStreamWaitEvent(side.s, side.ev_v, 0) != cudaSuccess)
+        return SKEW_ERR_CUDA;
+    rc = ozaki_gemm_pre(side.s, ov, ov, 1.0, 0.0, w.G, b, status, 8, 0, ks, w.part_s);
+    if (rc) return rc;
+    {
+        KtScope kt(side.s, KT_GEMM_F64);
+        tfactor_kernel<<<1, TF_THREADS, tfactor_smem(b), side.s>>>(b, taup, w.G, Tp);
+        count_launch();
+    }
+    if (cudaEventRecord(side.ev_t, side.s) != cudaSuccess) return SKEW_ERR_CUDA;
+    // a3: P = A22 V with A22 the skew matrix of its strict lower triangle
+    rc = ozaki_split(st, m, m, A22, 0, ldw, 1.0, 1, gws, gsz, &oa);
+    if (rc) return rc;
+    rc = ozaki_gemm_pre(st, oa, ov, 1.0, 0.0, w.Pm, n, status, slices);
+    if (rc) return rc;
+    // Q = P^T V
+    rc = ozaki_split(st, b, m, w.Pm, n, 1, 1.0, 0, w.oz_p, w.oz_vb, &op);
+    if (rc) return rc;
+    rc = ozaki_gemm_pre(st, op, ov, 1.0, 0.0, w.C1, b, status, 8, 0, ks, w.part_m);
+    if (rc) return rc;
+    // a4: W = [V P] Z, Z = [-C2/2; T]
+    if (cudaStreamWaitEvent(st, side.ev_t, 0) != cudaSuccess) return SKEW_ERR_CUDA;
+    {
+        KtScope kt(st, KT_GEMM_F64);
+        wz_kernel<<<b, b, 0, st>>>(b, w.C1, Tp, w.Z);
+        count_launch();
+    }
+    rc = ozaki_split(st, m, 2 * b, w.V, 1, n, 1.0, 0, w.oz_vp, w.oz_vpb, &ovp);
+    if (rc) return rc;
+    rc = ozaki_split(st, b, 2 * b, w.Z, 2 * b, 1, 1.0, 0, w.oz_z, w.oz_zb, &oz);
+    if (rc) return rc;
+    rc = ozaki_gemm_pre(st, ovp, oz, 1.0, 0.0, w.Y, n, status, 8);
+    if (rc) return rc;
+    {
+        KtScope kt(st, KT_GEMM_F64);
+        concat_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, w.V, w.Y, n, w.X2, w.Y2);
+        count_launch();
+    }
+    return 0;
+}
+
+}  // namespace
+
 int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac, void* ws,
                 size_t ws_bytes, int* d_status, int planes, int slices) {
     const bool mixed = planes > 0;
@@ -272,7 +456,7 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
     const int P = num_panels(n, b);
     if (P == 0) return 0;
     Carve cv(ws, ws_bytes);
-    ReduceWs w = carve_reduce(cv, n, b);
+    ReduceWs w = carve_reduce(cv, n, b, planes == REDUCE_F64ACC);
     const size_t gsz = mixed ? mixed_gemm_ws(n, b, planes) : 0;
     void* gws = mixed ? cv.take<char>(gsz) : nullptr;
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
@@ -281,6 +465,14 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int sms = device_sms();
+    if (cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tfactor_smem(b)) !=
+        cudaSuccess)
+        return SKEW_ERR_LAUNCH;
+    SideStream side;
+    if (planes == REDUCE_F64ACC) {
+        const int rc = side.init();
+        if (rc) return rc;
+    }
 
     for (int p = 0; p < P; p++) {
         const int o = (p + 1) * b, m = n - o;
@@ -307,21 +499,23 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
                 return SKEW_ERR_LAUNCH;
         }
         count_launch();
+        if (planes == REDUCE_F64ACC) {
+            // ---- T factor, a3, a4 as tensor-core products
+            const int rc = panel_update_f64acc(st, side, n, m, b, panel, ldw, A22, taup, Tp, w, gws, gsz, d_status,
+                                               slices);
+            if (rc) return rc;
+        } else {
         // ---- T factor (Eq. 7)
         {
             KtScope kt(st, KT_GEMM_F64);
             panel_v_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, panel, ldw, w.V, n);
             count_launch();
             if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.V, n, 0.0, w.G, b) != cudaSuccess) return SKEW_ERR_CUDA;
-            tfactor_kernel<<<1, 128, sizeof(double) * (b * b + b), st>>>(b, taup, w.G, Tp);
+            tfactor_kernel<<<1, TF_THREADS, tfactor_smem(b), st>>>(b, taup, w.G, Tp);
             count_launch();
         }
         // ---- a3: P = A22 V (skew, lower triangle only)
-        if (planes == REDUCE_F64ACC) {
-            int rc = ozaki_gemm(st, m, b, m, 1.0, A22, 0, ldw, 1.0, w.V, n, 1, 1.0, 0.0, w.Pm, n, gws, gsz, d_status,
-                                1, slices);
-            if (rc) return rc;
-        } else if (mixed) {
+        if (mixed) {
             int rc = split_gemm(st, m, b, m, 1.0, A22, 0, ldw, 1, w.V, n, 1, 0.0, w.Pm, n, 0, gws, gsz, d_status,
                                 planes);
             if (rc) return rc;
@@ -340,6 +534,7 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
             // ---- a5: A22 += [V W][W -V]^T (lower tiles)
             concat_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, w.V, w.Y, n, w.X2, w.Y2);
             count_launch();
+        }
         }
         if (planes == REDUCE_F64ACC) {
             // tiles on or below the diagonal (the upper triangle of W is never read)

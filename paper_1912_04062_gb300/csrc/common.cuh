@@ -51,7 +51,8 @@ SK_DEV bool sk_grid_barrier(unsigned* counter, unsigned& epoch, int* status) {
     if (threadIdx.x == 0) {
         epoch += 1;
         const unsigned target = epoch * gridDim.x;
-        __threadfence();
+        // the block's writes precede the release (bar.sync, then a gpu-scope
+        // release by this thread)
         sk_atom_add_release(counter, 1u);
         int ok = 1;
         unsigned polls = 0;

@@ -36,7 +36,9 @@
 // group start once the epilogue has drained it.
 // With `lower` set, tiles wholly above the diagonal (every column index above
 // every row index) are skipped: for symmetric or skew results whose upper
-// triangle is not read.
+// triangle is not read.  Split K (for small outputs over a long K): CTA
+// (tile, z) takes chunks [z kz, (z + 1) kz) and stores its unscaled-by-alpha
+// partial tile; a reduction kernel sums the partials in a fixed order.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -74,6 +76,8 @@ struct OzParams {
     int* status;
     int s;                   // digit slices kept (levels L < s)
     int lower;               // skip tiles above the diagonal
+    int kz;                  // split K: chunks per split (blockIdx.y), 0 = whole K
+    double* part;            // split K: partial tiles, [split][N][M]
 };
 
 struct OzSmem {
@@ -165,6 +169,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (p.lower && n0 >= m0 + OM) return;  // whole CTA, before any barrier or TMEM use
     const int S = p.s;
+    const int z = blockIdx.y, c_off = p.kz ? z * p.kz : 0;
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < 2; q++) {
@@ -191,7 +196,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int nch = p.nchunks;
+    const int nch = p.kz ? min(p.kz, p.nchunks - c_off) : p.nchunks;
 
     if (warp == 8) {
         if (lane == 0) {
@@ -205,14 +210,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 if (!(ok = mbar_wait(&bfree[q], ((uint32_t)(c >> 1) & 1u) ^ 1u, p.status))) break;
                 mbar_arrive_expect_tx(&bfull[q], (uint32_t)S * OzSmem::B_ATOM);
                 for (int j = 0; j < S; j++)
-                    tma_load_2d(sB + q * OzSmem::B_SET + j * OzSmem::B_ATOM, &tmB, &bfull[q], c * OKA,
+                    tma_load_2d(sB + q * OzSmem::B_SET + j * OzSmem::B_ATOM, &tmB, &bfull[q], (c_off + c) * OKA,
                                 j * p.Np + n0);
                 bi++;
                 for (int i = 0; i < S; i++) {
                     const int it = c * S + i, st = it % NA;
                     if (!(ok = mbar_wait(&aempty[st], ((uint32_t)(it / NA) & 1u) ^ 1u, p.status))) break;
                     mbar_arrive_expect_tx(&afull[st], OzSmem::A_ATOM);
-                    tma_load_2d(sA + st * OzSmem::A_ATOM, &tmA, &afull[st], c * OKA, i * p.Mp + m0);
+                    tma_load_2d(sA + st * OzSmem::A_ATOM, &tmA, &afull[st], (c_off + c) * OKA, i * p.Mp + m0);
                     ai++;
                 }
             }
@@ -322,6 +327,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 const int col = n0 + half * EC + q;
                 if (col >= p.N) continue;
                 const double val = ldexp((double)ah[q] + (double)al[q], er + p.eb[col] - 14);
+                if (p.part) {
+                    p.part[((long long)z * p.N + col) * p.M + row] = val;
+                    continue;
+                }
                 double* dst = p.C + (long long)col * p.ldc + row;
                 *dst = (p.beta == 0.0) ? p.alpha * val : fma(p.beta, *dst, p.alpha * val);
             }
@@ -538,6 +547,20 @@ __global__ void oz_split_skew_kernel(int rows, int Rp, int Kp, const double* __r
     }
 }
 
+// C = alpha * sum_z part[z] + beta C, the partials summed in order z = 0, 1, ..
+__global__ void oz_splitk_reduce_kernel(int M, int N, int nz, const double* __restrict__ part, double alpha,
+                                        double beta, double* __restrict__ C, long long ldc) {
+    const long long total = (long long)M * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int zz = 0; zz < nz; zz++) acc += __ldcg(part + zz * total + e);
+        const long long col = e / M, row = e - col * M;
+        double* dst = C + col * ldc + row;
+        *dst = (beta == 0.0) ? alpha * acc : fma(beta, *dst, alpha * acc);
+    }
+}
+
 inline long long rup(long long x, long long a) { return (x + a - 1) / a * a; }
 inline int gridn(long long total) {
     long long g = (total + 255) / 256;
@@ -605,7 +628,7 @@ int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long r
 
 // C = alpha * A B^T + beta C from split operands (A: M x K, B: N x K).
 int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, double alpha, double beta, double* C,
-                   long long ldc, int* status, int slices, int lower) {
+                   long long ldc, int* status, int slices, int lower, int ksplit, double* part) {
     const int M = A.rows, N = B.rows, K = A.K;
     if (M <= 0 || N <= 0) return 0;
     if (B.K != K || B.Kp != A.Kp || slices < 1 || slices > SL) return SKEW_ERR_UNSUPPORTED;
@@ -631,15 +654,26 @@ int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, doub
     p.lower = lower;
     p.mt = (M + OM - 1) / OM;
     p.nt = (N + ON - 1) / ON;
+    int nz = 1;
+    if (ksplit > 1) {
+        if (!part) return SKEW_ERR_WORKSPACE;
+        p.kz = (p.nchunks + ksplit - 1) / ksplit;
+        nz = (p.nchunks + p.kz - 1) / p.kz;
+        p.part = part;
+    }
     const size_t smem = OzSmem::bytes();
     cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // algorithmic work: the kept slice pairs over the outputs written
     const double pairs = slices * (slices + 1) / 2.0;
     const double outs = lower ? lower_count(M, N) : (double)M * N;
     const int kt = kt_begin(st);
-    ozaki_gemm_kernel<<<(unsigned)(p.mt * p.nt), OT, smem, st>>>(ta, tb, p);
-    kt_end(st, kt, g_kt_ozaki_kind, 2.0 * pairs * outs * K);
+    ozaki_gemm_kernel<<<dim3((unsigned)(p.mt * p.nt), (unsigned)nz), OT, smem, st>>>(ta, tb, p);
     count_launch();
+    if (nz > 1) {
+        oz_splitk_reduce_kernel<<<gridn((long long)M * N), 256, 0, st>>>(M, N, nz, part, alpha, beta, C, ldc);
+        count_launch();
+    }
+    kt_end(st, kt, g_kt_ozaki_kind, 2.0 * pairs * outs * K);
     return cuda_ok(cudaGetLastError());
 }
 
