@@ -289,7 +289,7 @@ struct ReduceWs {
     unsigned* bar;
     // tensor-core form: Z = [-C2/2; T], split-K partials of the main and side
     // streams, digit slices of V, P, [V P] and Z
-    double *Z, *part_m, *part_s;
+    double *Z, *part_m, *part_s, *part_p;
     void *oz_v, *oz_p, *oz_vp, *oz_z;
     size_t oz_vb, oz_vpb, oz_zb;
 };
@@ -321,6 +321,7 @@ ReduceWs carve_reduce(Carve& cv, int n, int b, bool f64acc) {
         w.Z = cv.take<double>((size_t)2 * b * b);
         w.part_m = cv.take<double>((size_t)KS_MAX * b * b);
         w.part_s = cv.take<double>((size_t)KS_MAX * b * b);
+        w.part_p = cv.take<double>((size_t)KS_MAX * 128 * b);  // SYMM partials: splits x tiles <= KS_MAX
         w.oz_vb = ozaki_operand_ws(b, n);
         w.oz_v = cv.take<char>(w.oz_vb);
         w.oz_p = cv.take<char>(w.oz_vb);
@@ -419,8 +420,17 @@ int panel_update_f64acc(cudaStream_t st, SideStream& side, int n, int m, int b, 
     // a3: P = A22 V with A22 the skew matrix of its strict lower triangle
     rc = ozaki_split(st, m, m, A22, 0, ldw, 1.0, 1, gws, gsz, &oa);
     if (rc) return rc;
-    rc = ozaki_gemm_pre(st, oa, ov, 1.0, 0.0, w.Pm, n, status, slices);
-    if (rc) return rc;
+    {
+        // N = b is a single column of tiles: split K so that the m / 128 row
+        // tiles fill the SMs
+        const int tiles = (m + 127) / 128;
+        int kp = device_sms() / tiles;
+        if (kp * tiles > KS_MAX) kp = KS_MAX / tiles;
+        if (kp > (nch + 1) / 2) kp = (nch + 1) / 2;
+        if (kp < 1) kp = 1;
+        rc = ozaki_gemm_pre(st, oa, ov, 1.0, 0.0, w.Pm, n, status, slices, 0, kp, w.part_p);
+        if (rc) return rc;
+    }
     // Q = P^T V
     rc = ozaki_split(st, b, m, w.Pm, n, 1, 1.0, 0, w.oz_p, w.oz_vb, &op);
     if (rc) return rc;

@@ -114,6 +114,18 @@ SK_DEV void oz_digits(double x, int e, float (&d)[8]) {
     }
 }
 
+// Sign flips and magnitudes of doubles as integer operations on their bits
+// (the split kernels touch every element; GB300's FP64 pipe is 1/64 rate).
+SK_DEV double oz_neg_if(double x, bool neg) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+}
+// |x| as an ordered bit pattern: for non-negative doubles the integer order of
+// the patterns is the numeric order
+SK_DEV unsigned long long oz_absbits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+SK_DEV unsigned long long oz_umax(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+
 SK_DEV void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -138,8 +150,30 @@ SK_DEV void df_add_df(float& hi, float& lo, float xh, float xl) {
     hi = h;
 }
 
+// x 2^sh as a double, exactly, for a normal or zero float x: the exponent is
+// moved with integer operations (GB300 runs FP64 at 1/64 of the FP32 rate, and
+// these scalings are an epilogue's bulk); results outside the normal double
+// range take ldexp.
+SK_DEV double f2d_scaled(float x, int sh) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t ef = (u >> 23) & 0xFFu;
+    if ((u & 0x7FFFFFFFu) == 0u) return 0.0;
+    const int E = (int)ef - 127 + 1023 + sh;
+    if (ef == 0u || E <= 0 || E >= 2047) return ldexp((double)x, sh);
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)E << 52) |
+                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// (hi + lo) 2^sh for a double-float pair (|lo| <= ulp(hi) / 2): the sum of the
+// two exact scaled parts spans at most 49 bits, so it is exact too.
+SK_DEV double df_scaled(float hi, float lo, int sh) { return f2d_scaled(hi, sh) + f2d_scaled(lo, sh); }
+
 // 10 warps: a sub-partition hosts up to 3 of them in its 16K registers, so at
-// most 168 registers per thread
+// most 168 registers per thread.  ONE: one item per CTA (grid = items), for
+// long K, where the per-item epilogue is negligible; otherwise the CTAs are
+// persistent and walk the items.
+template <bool ONE>
 __global__ void __maxnreg__(168)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams p) {
     extern __shared__ unsigned char oz_raw[];
@@ -158,18 +192,28 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     // loads issued (producer) and consumed (MMA): B in chunks, A in slices
     __shared__ int s_bi, s_bc, s_ai, s_ac;
 
-    // tile order: groups of GM tile rows, column-major inside a group, so that
-    // the CTAs resident at one time share few distinct A and B rows (one wave
-    // of 152 covers about 8 x 19 tiles, whose operands L2 holds as the CTAs
-    // step through K together)
-    constexpr int GM = 8;
-    const int t = blockIdx.x, grp_size = GM * p.nt, first_m = (t / grp_size) * GM;
-    const int gm = (p.mt - first_m) < GM ? (p.mt - first_m) : GM;
-    const int m0 = (first_m + (t % grp_size) % gm) * OM, n0 = ((t % grp_size) / gm) * ON;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (p.lower && n0 >= m0 + OM) return;  // whole CTA, before any barrier or TMEM use
     const int S = p.s;
-    const int z = blockIdx.y, c_off = p.kz ? z * p.kz : 0;
+    const int nz = p.kz ? (p.nchunks + p.kz - 1) / p.kz : 1;
+    const int nitems = p.mt * p.nt * nz;  // below 2^31 for every supported size
+    // Work item it = (tile, K range z), tile = it / nz.  Tile order: groups of
+    // GM tile rows, column-major inside a group, so that the items in flight
+    // at one time (one per CTA) share few distinct A and B rows, whose
+    // operands L2 holds as the CTAs step through K together.  Every role
+    // walks the same items and skips the same ones (tiles wholly above the
+    // diagonal with `lower`).
+    constexpr int GM = 8;
+    auto geom = [&](int it, int& m0, int& n0, int& z, int& c_off, int& nch) -> bool {
+        const int t = it / nz;
+        z = it - t * nz;
+        const int grp_size = GM * p.nt, first_m = (t / grp_size) * GM;
+        const int gm = (p.mt - first_m) < GM ? (p.mt - first_m) : GM;
+        m0 = (first_m + (t % grp_size) % gm) * OM;
+        n0 = ((t % grp_size) / gm) * ON;
+        c_off = p.kz ? z * p.kz : 0;
+        nch = p.kz ? min(p.kz, p.nchunks - c_off) : p.nchunks;
+        return !(p.lower && n0 >= m0 + OM);
+    };
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < 2; q++) {
@@ -196,30 +240,34 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int nch = p.kz ? min(p.kz, p.nchunks - c_off) : p.nchunks;
 
     if (warp == 8) {
         if (lane == 0) {
-            // ---- TMA producer: per chunk, its B slices into buffer c & 1 (free
-            // once chunk c - 2 is multiplied), then its A slices (each waits
-            // for its ring stage)
+            // ---- TMA producer: per chunk, its B slices into buffer bi & 1 (free
+            // once the chunk two before it is multiplied), then its A slices
+            // (each waits for its ring stage); bi and ai run across items
             bool ok = true;
             int ai = 0, bi = 0;
-            for (int c = 0; c < nch && ok; c++) {
-                const int q = c & 1;
-                if (!(ok = mbar_wait(&bfree[q], ((uint32_t)(c >> 1) & 1u) ^ 1u, p.status))) break;
-                mbar_arrive_expect_tx(&bfull[q], (uint32_t)S * OzSmem::B_ATOM);
-                for (int j = 0; j < S; j++)
-                    tma_load_2d(sB + q * OzSmem::B_SET + j * OzSmem::B_ATOM, &tmB, &bfull[q], (c_off + c) * OKA,
-                                j * p.Np + n0);
-                bi++;
-                for (int i = 0; i < S; i++) {
-                    const int it = c * S + i, st = it % NA;
-                    if (!(ok = mbar_wait(&aempty[st], ((uint32_t)(it / NA) & 1u) ^ 1u, p.status))) break;
-                    mbar_arrive_expect_tx(&afull[st], OzSmem::A_ATOM);
-                    tma_load_2d(sA + st * OzSmem::A_ATOM, &tmA, &afull[st], (c_off + c) * OKA, i * p.Mp + m0);
-                    ai++;
+            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+                int m0, n0, z, c_off, nch;
+                if (!geom(it, m0, n0, z, c_off, nch)) continue;
+                for (int c = 0; c < nch && ok; c++) {
+                    const int q = bi & 1;
+                    if (!(ok = mbar_wait(&bfree[q], ((uint32_t)(bi >> 1) & 1u) ^ 1u, p.status))) break;
+                    mbar_arrive_expect_tx(&bfull[q], (uint32_t)S * OzSmem::B_ATOM);
+                    for (int j = 0; j < S; j++)
+                        tma_load_2d(sB + q * OzSmem::B_SET + j * OzSmem::B_ATOM, &tmB, &bfull[q],
+                                    (c_off + c) * OKA, j * p.Np + n0);
+                    bi++;
+                    for (int i = 0; i < S; i++) {
+                        const int st = ai % NA;
+                        if (!(ok = mbar_wait(&aempty[st], ((uint32_t)(ai / NA) & 1u) ^ 1u, p.status))) break;
+                        mbar_arrive_expect_tx(&afull[st], OzSmem::A_ATOM);
+                        tma_load_2d(sA + st * OzSmem::A_ATOM, &tmA, &afull[st], (c_off + c) * OKA, i * p.Mp + m0);
+                        ai++;
+                    }
                 }
+                if (ONE) break;
             }
             s_bi = bi;
             s_ai = ai;
@@ -230,110 +278,155 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             // Pass i multiplies A slice i with B slices 0 .. S-1-i; those B slices
             // are consecutive 64-row blocks of one buffer and their levels
             // i .. S-1 consecutive TMEM columns, so the pass is one MMA of width
-            // N = 64 (S - i) (two when wider than 256).
+            // N = 64 (S - i) (two when wider than 256).  A level group starts
+            // once the epilogue has drained the previous one (of this item or
+            // the one before).
             bool ok = true;
-            int ac = 0, bc = 0;
-            for (int c = 0; c < nch && ok; c++) {
-                const bool first = (c % GRP) == 0;  // first chunk of a level group
-                if (first) {
-                    if (!(ok = mbar_wait(tempty, ((uint32_t)(c / GRP) & 1u) ^ 1u, p.status))) break;
-                    tc_fence_after();
-                }
-                const int q = c & 1;
-                if (!(ok = mbar_wait(&bfull[q], (uint32_t)(c >> 1) & 1u, p.status))) break;
-                bc++;
-                tc_fence_after();
-                for (int i = 0; i < S; i++) {
-                    const int it = c * S + i, st = it % NA;
-                    if (!(ok = mbar_wait(&afull[st], (uint32_t)(it / NA) & 1u, p.status))) break;
-                    ac++;
-                    tc_fence_after();
-                    const uint64_t ad0 = umma_desc_sw128(smem_u32(sA + st * OzSmem::A_ATOM));
-                    const int nj = S - i, n1 = nj < 4 ? nj : 4;
-                    const uint64_t b0 = umma_desc_sw128(smem_u32(sB + q * OzSmem::B_SET));
-                    const uint64_t b4 = umma_desc_sw128(smem_u32(sB + q * OzSmem::B_SET + 4 * OzSmem::B_ATOM));
-                    const uint32_t d0 = tmem + (uint32_t)(i * ON), d4 = tmem + (uint32_t)((i + 4) * ON);
-#pragma unroll
-                    for (int kk = 0; kk < OKA / 16; kk++) {
-                        // every level is first written by pass 0 at kk = 0 of a group
-                        const uint32_t acc = (!first || i > 0 || kk > 0) ? 1u : 0u;
-                        umma_bf16(d0, ad0 + 2 * kk, b0 + 2 * kk, umma_idesc_bf16(OM, ON * n1), acc);
-                        if (nj > 4) umma_bf16(d4, ad0 + 2 * kk, b4 + 2 * kk, umma_idesc_bf16(OM, ON * (nj - 4)), acc);
+            int ac = 0, bc = 0, gc = 0;
+            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+                int m0, n0, z, c_off, nch;
+                if (!geom(it, m0, n0, z, c_off, nch)) continue;
+                for (int c = 0; c < nch && ok; c++) {
+                    const bool first = (c % GRP) == 0;  // first chunk of a level group
+                    if (first) {
+                        if (!(ok = mbar_wait(tempty, ((uint32_t)gc & 1u) ^ 1u, p.status))) break;
+                        tc_fence_after();
                     }
-                    umma_commit(&aempty[st]);
+                    const int q = bc & 1;
+                    if (!(ok = mbar_wait(&bfull[q], (uint32_t)(bc >> 1) & 1u, p.status))) break;
+                    tc_fence_after();
+                    for (int i = 0; i < S; i++) {
+                        const int st = ac % NA;
+                        if (!(ok = mbar_wait(&afull[st], (uint32_t)(ac / NA) & 1u, p.status))) break;
+                        ac++;
+                        tc_fence_after();
+                        const uint64_t ad0 = umma_desc_sw128(smem_u32(sA + st * OzSmem::A_ATOM));
+                        const int nj = S - i, n1 = nj < 4 ? nj : 4;
+                        const uint64_t b0 = umma_desc_sw128(smem_u32(sB + q * OzSmem::B_SET));
+                        const uint64_t b4 = umma_desc_sw128(smem_u32(sB + q * OzSmem::B_SET + 4 * OzSmem::B_ATOM));
+                        const uint32_t d0 = tmem + (uint32_t)(i * ON), d4 = tmem + (uint32_t)((i + 4) * ON);
+#pragma unroll
+                        for (int kk = 0; kk < OKA / 16; kk++) {
+                            // every level is first written by pass 0 at kk = 0 of a group
+                            const uint32_t acc = (!first || i > 0 || kk > 0) ? 1u : 0u;
+                            umma_bf16(d0, ad0 + 2 * kk, b0 + 2 * kk, umma_idesc_bf16(OM, ON * n1), acc);
+                            if (nj > 4)
+                                umma_bf16(d4, ad0 + 2 * kk, b4 + 2 * kk, umma_idesc_bf16(OM, ON * (nj - 4)), acc);
+                        }
+                        umma_commit(&aempty[st]);
+                    }
+                    if (!ok) break;
+                    bc++;
+                    umma_commit(&bfree[q]);
+                    if (c % GRP == GRP - 1 || c == nch - 1) {
+                        umma_commit(tfull);
+                        gc++;
+                    }
                 }
-                if (!ok) break;
-                umma_commit(&bfree[q]);
-                if (c % GRP == GRP - 1 || c == nch - 1) umma_commit(tfull);
+                if (ONE) break;
             }
             s_bc = bc;
             s_ac = ac;
         }
     } else {
-        // ---- epilogue warps 0-7: row m0 + 32 (w & 3) + lane, columns n0 + 32 (w >> 2) + [0, 32)
+        // ---- epilogue warps 0-7: row m0 + 32 (w & 3) + lane, columns n0 + 32 (w >> 2) + [0, 32).
+        // TMEM is released after the last level fold of an item, so the FP64
+        // conversion and the update of C overlap the next item's MMAs.
         constexpr int EC = ON / 2;
         const int quad = warp & 3, half = warp >> 2;
-        float ah[EC], al[EC];
-#pragma unroll
-        for (int q = 0; q < EC; q++) { ah[q] = 0.f; al[q] = 0.f; }
-        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * EC);
         bool ok = true;
-        const int ngroups = (nch + GRP - 1) / GRP;
-        for (int grp = 0; grp < ngroups; grp++) {
-            ok = mbar_wait(tfull, (uint32_t)grp & 1u, p.status);
-            tc_fence_after();
-            if (!ok) break;
+        int gc = 0;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * EC);
+        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+            int ngroups;
+            {
+                int m0, n0, z, c_off, nch;
+                if (!geom(it, m0, n0, z, c_off, nch)) continue;
+                ngroups = (nch + GRP - 1) / GRP;
+            }
+            float ah[EC], al[EC];
 #pragma unroll
-            for (int g = 0; g < EC / 16; g++) {
-                float sh[16], sl[16];
+            for (int q = 0; q < EC; q++) { ah[q] = 0.f; al[q] = 0.f; }
+            for (int grp = 0; grp < ngroups; grp++) {
+                ok = mbar_wait(tfull, (uint32_t)gc & 1u, p.status);
+                tc_fence_after();
+                if (!ok) break;
 #pragma unroll
-                for (int q = 0; q < 16; q++) { sh[q] = 0.f; sl[q] = 0.f; }
-                // levels from the smallest up, three TMEM loads in flight per wait
+                for (int g = 0; g < EC / 16; g++) {
+                    float sh[16], sl[16];
+#pragma unroll
+                    for (int q = 0; q < 16; q++) { sh[q] = 0.f; sl[q] = 0.f; }
+                    // levels from the smallest up, three TMEM loads in flight per wait
 #pragma unroll 1
-                for (int top = S - 1; top >= 0; top -= 3) {
-                    uint32_t v0[16], v1[16], v2[16];
-                    const uint32_t col = lane_base + (uint32_t)(g * 16);
-                    tmem_ld16_async(col + (uint32_t)(top * ON), v0);
-                    if (top >= 1) tmem_ld16_async(col + (uint32_t)((top - 1) * ON), v1);
-                    if (top >= 2) tmem_ld16_async(col + (uint32_t)((top - 2) * ON), v2);
-                    tmem_wait_ld16(v0);
-                    tmem_after_wait16(v1);
-                    tmem_after_wait16(v2);
-                    float sc = __int_as_float((127 - 7 * top) << 23);  // 2^-7L
+                    for (int top = S - 1; top >= 0; top -= 3) {
+                        uint32_t v0[16], v1[16], v2[16];
+                        const uint32_t col = lane_base + (uint32_t)(g * 16);
+                        tmem_ld16_async(col + (uint32_t)(top * ON), v0);
+                        if (top >= 1) tmem_ld16_async(col + (uint32_t)((top - 1) * ON), v1);
+                        if (top >= 2) tmem_ld16_async(col + (uint32_t)((top - 2) * ON), v2);
+                        tmem_wait_ld16(v0);
+                        tmem_after_wait16(v1);
+                        tmem_after_wait16(v2);
+                        float sc = __int_as_float((127 - 7 * top) << 23);  // 2^-7L
 #pragma unroll
-                    for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], __uint_as_float(v0[q]) * sc);
-                    if (top >= 1) {
-                        sc *= 128.f;
+                        for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], __uint_as_float(v0[q]) * sc);
+                        if (top >= 1) {
+                            sc *= 128.f;
 #pragma unroll
-                        for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], __uint_as_float(v1[q]) * sc);
+                            for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], __uint_as_float(v1[q]) * sc);
+                        }
+                        if (top >= 2) {
+                            sc *= 128.f;
+#pragma unroll
+                            for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], __uint_as_float(v2[q]) * sc);
+                        }
                     }
-                    if (top >= 2) {
-                        sc *= 128.f;
 #pragma unroll
-                        for (int q = 0; q < 16; q++) df_add(sh[q], sl[q], __uint_as_float(v2[q]) * sc);
-                    }
+                    for (int q = 0; q < 16; q++) df_add_df(ah[g * 16 + q], al[g * 16 + q], sh[q], sl[q]);
                 }
-#pragma unroll
-                for (int q = 0; q < 16; q++) df_add_df(ah[g * 16 + q], al[g * 16 + q], sh[q], sl[q]);
+                tc_fence_before();
+                mbar_arrive(tempty);
+                gc++;
             }
-            tc_fence_before();
-            mbar_arrive(tempty);
-        }
-        const int row = m0 + quad * 32 + lane;
-        if (ok && row < p.M) {
-            const int er = p.ea[row];
-#pragma unroll
-            for (int q = 0; q < EC; q++) {
-                const int col = n0 + half * EC + q;
-                if (col >= p.N) continue;
-                const double val = ldexp((double)ah[q] + (double)al[q], er + p.eb[col] - 14);
+            if (!ok) break;
+            int m0, n0, z, c_off, nch;  // recomputed: not live across the drain
+            geom(it, m0, n0, z, c_off, nch);
+            const int row = m0 + quad * 32 + lane;
+            if (row < p.M) {
+                const int er = p.ea[row] - 14;
                 if (p.part) {
-                    p.part[((long long)z * p.N + col) * p.M + row] = val;
-                    continue;
+#pragma unroll
+                    for (int q = 0; q < EC; q++) {
+                        const int col = n0 + half * EC + q;
+                        if (col < p.N)
+                            p.part[((long long)z * p.N + col) * p.M + row] = df_scaled(ah[q], al[q], er + p.eb[col]);
+                    }
+                } else {
+                    // alpha = +-1 and beta in {0, 1} (every internal use) cost one
+                    // or two FP64 additions per output; the old values are loaded
+                    // 16 at a time ahead of their use
+                    const bool a1 = p.alpha == 1.0, am1 = p.alpha == -1.0;
+                    const bool b0 = p.beta == 0.0, b1 = p.beta == 1.0;
+#pragma unroll
+                    for (int hq = 0; hq < EC; hq += 16) {
+                        double old[16];
+#pragma unroll
+                        for (int q = 0; q < 16; q++) {
+                            const int col = n0 + half * EC + hq + q;
+                            old[q] = (!b0 && col < p.N) ? p.C[(long long)col * p.ldc + row] : 0.0;
+                        }
+#pragma unroll
+                        for (int q = 0; q < 16; q++) {
+                            const int col = n0 + half * EC + hq + q;
+                            if (col >= p.N) continue;
+                            const double val = df_scaled(ah[hq + q], al[hq + q], er + p.eb[col]);
+                            const double av = a1 ? val : (am1 ? -val : p.alpha * val);
+                            p.C[(long long)col * p.ldc + row] = b0 ? av : (b1 ? old[q] + av : fma(p.beta, old[q], av));
+                        }
+                    }
                 }
-                double* dst = p.C + (long long)col * p.ldc + row;
-                *dst = (p.beta == 0.0) ? p.alpha * val : fma(p.beta, *dst, p.alpha * val);
             }
+            if (ONE) break;
         }
     }
     tc_fence_before();
@@ -353,20 +446,20 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 // bit patterns of non-negative doubles) with atomicMax.
 __global__ void oz_rowmax_cols_kernel(int rows, int K, const double* __restrict__ src, long long sk,
                                       unsigned long long* __restrict__ rowmax) {
-    __shared__ double red[8][33];
+    __shared__ unsigned long long red[8][33];
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     const int r = blockIdx.x * 32 + tx, k0 = blockIdx.y * 256;
-    double m = 0.0;
+    unsigned long long m = 0;
     if (r < rows)
         for (int kk = ty; kk < 256; kk += 8) {
             const int k = k0 + kk;
-            if (k < K) m = fmax(m, fabs(src[r + (long long)k * sk]));
+            if (k < K) m = oz_umax(m, oz_absbits(src[r + (long long)k * sk]));
         }
     red[ty][tx] = m;
     __syncthreads();
     if (ty == 0) {
-        for (int q = 1; q < 8; q++) m = fmax(m, red[q][tx]);
-        if (r < rows && m > 0.0) atomicMax(rowmax + r, (unsigned long long)__double_as_longlong(m));
+        for (int q = 1; q < 8; q++) m = oz_umax(m, red[q][tx]);
+        if (r < rows && m > 0) atomicMax(rowmax + r, m);
     }
 }
 
@@ -379,7 +472,7 @@ __global__ void oz_split_cols_kernel(int rows, int K, int Rp, int Kp, const doub
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     for (int kk = ty; kk < 32; kk += 8) {
         const int r = r0 + tx, k = k0 + kk;
-        tile[kk][tx] = (r < rows && k < K) ? sgn * src[r + (long long)k * sk] : 0.0;
+        tile[kk][tx] = (r < rows && k < K) ? oz_neg_if(src[r + (long long)k * sk], sgn < 0.0) : 0.0;
     }
     __syncthreads();
     for (int rr = ty; rr < 32; rr += 8) {
@@ -400,25 +493,25 @@ __global__ void oz_split_cols_kernel(int rows, int K, int Rp, int Kp, const doub
 SK_DEV double oz_elem(const double* __restrict__ src, long long sr, long long sk, int skew, int r, int k) {
     if (!skew) return src[(long long)r * sr + (long long)k * sk];
     if (r > k) return src[(long long)r + (long long)k * sk];
-    if (r < k) return -src[(long long)k + (long long)r * sk];
+    if (r < k) return oz_neg_if(src[(long long)k + (long long)r * sk], true);
     return 0.0;
 }
 
 __global__ void oz_exp_kernel(int rows, int K, const double* __restrict__ src, long long sr, long long sk,
                               int* __restrict__ e, int skew) {
-    __shared__ double red[32];
+    __shared__ unsigned long long red[32];
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-        double m = 0.0;
-        for (int k = threadIdx.x; k < K; k += blockDim.x) m = fmax(m, fabs(oz_elem(src, sr, sk, skew, r, k)));
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        unsigned long long m = 0;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) m = oz_umax(m, oz_absbits(oz_elem(src, sr, sk, skew, r, k)));
+        for (int o = 16; o > 0; o >>= 1) m = oz_umax(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double mm = 0.0;
-            for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) mm = fmax(mm, red[w]);
+            unsigned long long mm = 0;
+            for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) mm = oz_umax(mm, red[w]);
             int ex = 0;
-            if (mm > 0.0) {
-                frexp(mm, &ex);  // mm = f 2^ex, f in [0.5, 1): mm < 2^ex
+            if (mm > 0) {
+                frexp(__longlong_as_double((long long)mm), &ex);  // mm = f 2^ex, f in [0.5, 1): mm < 2^ex
             }
             e[r] = ex;
         }
@@ -432,23 +525,24 @@ __global__ void oz_exp_kernel(int rows, int K, const double* __restrict__ src, l
 __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, int Rp, int Kp, const double* __restrict__ src,
                                                             long long sr, double sgn, int* __restrict__ e,
                                                             __nv_bfloat16* __restrict__ dst) {
-    __shared__ double red[8];
+    __shared__ unsigned long long red[8];
+    const bool neg = sgn < 0.0;
     for (int r = blockIdx.x; r < Rp; r += gridDim.x) {
         const double* row = src + (long long)r * sr;
-        double m = 0.0;
+        unsigned long long m = 0;
         if (r < rows)
-            for (int k = threadIdx.x; k < K; k += 256) m = fmax(m, fabs(row[k]));
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            for (int k = threadIdx.x; k < K; k += 256) m = oz_umax(m, oz_absbits(row[k]));
+        for (int o = 16; o > 0; o >>= 1) m = oz_umax(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
         __syncthreads();
         m = red[0];
-        for (int w = 1; w < 8; w++) m = fmax(m, red[w]);
+        for (int w = 1; w < 8; w++) m = oz_umax(m, red[w]);
         int ex = 0;
-        if (m > 0.0) frexp(m, &ex);  // m = f 2^ex, f in [0.5, 1): every |x| < 2^ex
+        if (m > 0) frexp(__longlong_as_double((long long)m), &ex);  // m = f 2^ex, f in [0.5, 1): every |x| < 2^ex
         if (threadIdx.x == 0) e[r] = ex;
         for (int k = 2 * threadIdx.x; k < Kp; k += 512) {
-            const double x0 = (r < rows && k < K) ? sgn * row[k] : 0.0;
-            const double x1 = (r < rows && k + 1 < K) ? sgn * row[k + 1] : 0.0;
+            const double x0 = (r < rows && k < K) ? oz_neg_if(row[k], neg) : 0.0;
+            const double x1 = (r < rows && k + 1 < K) ? oz_neg_if(row[k + 1], neg) : 0.0;
             float d0[8], d1[8];
             oz_digits(x0, ex, d0);
             oz_digits(x1, ex, d1);
@@ -468,7 +562,7 @@ __global__ void oz_split_kernel(int rows, int K, int Rp, int Kp, const double* _
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Kp) return;
     for (int r = blockIdx.y; r < Rp; r += gridDim.y) {
-        const double x = (r < rows && k < K) ? sgn * src[(long long)r * sr + (long long)k * sk] : 0.0;
+        const double x = (r < rows && k < K) ? oz_neg_if(src[(long long)r * sr + (long long)k * sk], sgn < 0.0) : 0.0;
         float d[8];
         oz_digits(x, (r < rows) ? e[r] : 0, d);
 #pragma unroll
@@ -482,21 +576,21 @@ __global__ void oz_split_kernel(int rows, int K, int Rp, int Kp, const double* _
 // to rowmax (as ordered bit patterns of non-negative doubles) with atomicMax.
 __global__ void oz_skew_rowmax_kernel(int n, const double* __restrict__ W, long long ld,
                                       unsigned long long* __restrict__ rowmax) {
-    __shared__ double tile[32][33];
+    __shared__ unsigned long long tile[32][33];
     const int bi = blockIdx.x, bj = blockIdx.y;
     if (bi < bj) return;
     const int i0 = bi * 32, j0 = bj * 32, tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     for (int jj = ty; jj < 32; jj += 8) {
         const int i = i0 + tx, j = j0 + jj;
-        tile[jj][tx] = (i < n && j < n && i > j) ? fabs(W[i + (long long)j * ld]) : 0.0;
+        tile[jj][tx] = (i < n && j < n && i > j) ? oz_absbits(W[i + (long long)j * ld]) : 0ULL;
     }
     __syncthreads();
     if (ty == 0) {
-        double rm = 0.0, cm = 0.0;  // row i0+tx over the tile's columns; column j0+tx over its rows
-        for (int jj = 0; jj < 32; jj++) rm = fmax(rm, tile[jj][tx]);
-        for (int ii = 0; ii < 32; ii++) cm = fmax(cm, tile[tx][ii]);
-        if (i0 + tx < n && rm > 0.0) atomicMax(rowmax + i0 + tx, (unsigned long long)__double_as_longlong(rm));
-        if (j0 + tx < n && cm > 0.0) atomicMax(rowmax + j0 + tx, (unsigned long long)__double_as_longlong(cm));
+        unsigned long long rm = 0, cm = 0;  // row i0+tx over the tile's columns; column j0+tx over its rows
+        for (int jj = 0; jj < 32; jj++) rm = oz_umax(rm, tile[jj][tx]);
+        for (int ii = 0; ii < 32; ii++) cm = oz_umax(cm, tile[tx][ii]);
+        if (i0 + tx < n && rm > 0) atomicMax(rowmax + i0 + tx, rm);
+        if (j0 + tx < n && cm > 0) atomicMax(rowmax + j0 + tx, cm);
     }
 }
 
@@ -526,13 +620,14 @@ __global__ void oz_split_skew_kernel(int rows, int Rp, int Kp, const double* __r
         // strictly upper tile: S(r, k) = -W(k, r), contiguous in k
         for (int rr = ty; rr < 32; rr += 8) {
             const int r = r0 + rr, k = k0 + tx;
-            tile[tx][rr] = (r < rows && k < rows) ? -W[k + (long long)r * ld] : 0.0;
+            tile[tx][rr] = (r < rows && k < rows) ? oz_neg_if(W[k + (long long)r * ld], true) : 0.0;
         }
     } else {
         for (int kk = ty; kk < 32; kk += 8) {
             const int r = r0 + tx, k = k0 + kk;
             double v = 0.0;
-            if (r < rows && k < rows) v = (r > k) ? W[r + (long long)k * ld] : (r < k ? -W[k + (long long)r * ld] : 0.0);
+            if (r < rows && k < rows)
+                v = (r > k) ? W[r + (long long)k * ld] : (r < k ? oz_neg_if(W[k + (long long)r * ld], true) : 0.0);
             tile[kk][tx] = v;
         }
     }
@@ -662,12 +757,19 @@ int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, doub
         p.part = part;
     }
     const size_t smem = OzSmem::bytes();
-    cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // long K per item (>= 16 chunks): one CTA per item; short K: persistent
+    // CTAs, whose FP64 epilogue overlaps the next item's MMAs
+    const bool one = (p.kz ? p.kz : p.nchunks) >= 16;
+    auto kern = one ? ozaki_gemm_kernel<true> : ozaki_gemm_kernel<false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // algorithmic work: the kept slice pairs over the outputs written
     const double pairs = slices * (slices + 1) / 2.0;
     const double outs = lower ? lower_count(M, N) : (double)M * N;
     const int kt = kt_begin(st);
-    ozaki_gemm_kernel<<<dim3((unsigned)(p.mt * p.nt), (unsigned)nz), OT, smem, st>>>(ta, tb, p);
+    // persistent: one CTA per SM walks the (tile, K range) items
+    const long long items = (long long)p.mt * p.nt * nz;
+    const int grid = (int)((one || items < device_sms()) ? items : device_sms());
+    kern<<<(unsigned)grid, OT, smem, st>>>(ta, tb, p);
     count_launch();
     if (nz > 1) {
         oz_splitk_reduce_kernel<<<gridn((long long)M * N), 256, 0, st>>>(M, N, nz, part, alpha, beta, C, ldc);
