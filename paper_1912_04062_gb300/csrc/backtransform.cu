@@ -20,6 +20,7 @@
 // for p descending, Z[o:, :] -= V_p (T_p (V_p^T Z[o:, :])) with FP64 GEMMs.
 #include "common.cuh"
 #include "internal.h"
+#include "sm100.cuh"
 
 namespace sk {
 namespace {
@@ -32,85 +33,115 @@ constexpr int QT = 256;
 
 __host__ __device__ inline int qsteps(int n, int b, int s) { return (s <= n - 3) ? 1 + (n - 3 - s) / b : 0; }
 
-// Thread t: column c = t / 4 of the slab, row phase q = t % 4.  The thread
-// keeps window rows 4u + q (u < 32) of its column in registers for the whole
-// block; the block's ell reflectors (v zero-padded to b, tau) are staged once
-// in shared memory.  Reflector s touches window rows off..off+b-1 with
-// off = s - s0; the loop over off is unrolled, so every register index is a
-// compile-time constant.  The four threads of a column are lanes of one warp:
-// a reflector costs two shuffles and no block barrier.
-template <typename T>
-__global__ void __launch_bounds__(QT)
-qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ tautrd, T* __restrict__ Z,
-            int ldz, int ncols, int slab) {
-    extern __shared__ __align__(16) unsigned char qtrd_raw[];
-    T* zw = reinterpret_cast<T*>(qtrd_raw);  // QLD x 64 staging of the window
-    T* vs = zw + QLD * 64;                   // QELL x QB reflectors of the block
-    T* ts = vs + QELL * QB;                  // QELL taus
-    const int nsw = n - 2;
+// FP32 form.  Thread t: column c = t / 4 of the slab, row phase q = t % 4; it
+// keeps window rows 4u + q (u < 32) of its column in registers.  Reflector s
+// of a block touches window rows off..off+b-1 with off = s - s0; the loop over
+// off is unrolled, so every register index is a compile-time constant, and
+// the four threads of a column are lanes of one warp: a reflector costs two
+// shuffles and no block barrier.  Consecutive blocks of a group share 63
+// window rows: after block k the window's first 64 rows are final for the
+// group and stored, the registers shift by 16, and the 64 new rows of block
+// k+1 arrive in shared memory by cp.async while block k computes; the next
+// block's reflectors and taus (FP32 copies written by the chase, zero taus
+// for absent steps) arrive by one bulk copy into the other of two buffers.
+constexpr int QS_LD = 68;  // [column][row] staging, = 4 mod 32: conflict-free for the (c, q) pattern
+
+struct QSlideSmem {
+    float v[2][QELL * QB];  // reflectors of the current and the next block
+    float tau[2][QELL];
+    float zin[64 * QS_LD];   // the next block's 64 new window rows
+    float zout[64 * QS_LD];  // the block's 64 finished rows
+    uint64_t bar[2];
+};
+
+SK_DEV void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+SK_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__global__ void __launch_bounds__(256, 2)
+qtrd_slide_kernel(int n, const float* __restrict__ V32, const float* __restrict__ tau32, float* __restrict__ Z,
+                  int ldz, int ncols, int slab, int* status) {
+    extern __shared__ __align__(128) unsigned char qs_raw[];
+    QSlideSmem& sm = *reinterpret_cast<QSlideSmem*>(qs_raw);
+    const int nsw = n - 2, nsw64 = (nsw + 63) / 64 * 64;
     const int c0 = blockIdx.x * slab;
     const int nc = min(slab, ncols - c0);
     if (nc <= 0) return;
-    const int t = threadIdx.x;
-    // every lane takes part in the shuffles; lanes past the slab work on
-    // scratch columns of the (always 64-column) window and store nothing
+    const int t = threadIdx.x, T = blockDim.x;
+    // every lane takes part in the shuffles; lanes past the slab work on zeros
     const int c = t >> 2, q = t & 3;
+    const bool own = c < nc;
+    float* zc = Z + (size_t)(c0 + (own ? c : 0)) * ldz;
+    if (t == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
     const int ngroups = (nsw + QELL - 1) / QELL;
+    constexpr uint32_t VBYTES = QELL * QB * sizeof(float), TBYTES = QELL * sizeof(float);
+    // reflectors of block (g, k) into buffer buf (one thread)
+    auto fetch = [&](int g, int k, int buf) {
+        const size_t slot = (size_t)k * nsw64 + (size_t)g * QELL;
+        mbar_arrive_expect_tx(&sm.bar[buf], VBYTES + TBYTES);
+        bulk_g2s(sm.v[buf], V32 + slot * QB, VBYTES, &sm.bar[buf]);
+        bulk_g2s(sm.tau[buf], tau32 + slot, TBYTES, &sm.bar[buf]);
+    };
+    if (t == 0) fetch(ngroups - 1, 0, 0);
+    int blk = 0;  // blocks so far: buffer blk & 1, barrier phase (blk >> 1) & 1
     for (int g = ngroups - 1; g >= 0; g--) {
-        const int s0 = g * QELL, s1 = min(nsw, s0 + QELL);
+        const int s0 = g * QELL;
         const int kmax = qsteps(n, QB, s0);
-        for (int k = 0; k < kmax; k++) {
-            const int top = s0 + 1 + k * QB;
-            if (top >= n) break;
-            const int H = min(QH, n - top);
-            // stage the reflectors (zero when sweep s has no step k) and the window
-            for (int e = t; e < QELL * QB; e += QT) {
-                const int sl = e / QB, i = e % QB, s = s0 + sl;
-                T v = 0;
-                if (s < s1 && k < qsteps(n, QB, s)) v = (T)Vtrd[((size_t)k * nsw + s) * QB + i];
-                vs[e] = v;
-            }
-            for (int sl = t; sl < QELL; sl += QT) {
-                const int s = s0 + sl;
-                ts[sl] = (s < s1 && k < qsteps(n, QB, s)) ? (T)tautrd[(size_t)k * nsw + s] : (T)0;
-            }
-            // window: warp w takes columns w, w + 8, ..., lanes run down the column
-            for (int cc = t >> 5; cc < nc; cc += QT / 32) {
-                const T* zsrc = Z + (size_t)(c0 + cc) * ldz + top;
-                for (int i = t & 31; i < H; i += 32) zw[cc * QLD + i] = zsrc[i];
-            }
-            __syncthreads();
-            T zr[32];
-            const T* zc = zw + c * QLD;
+        float zr[32];
+        {
+            const int top = s0 + 1, H = min(QH, n - top);
 #pragma unroll
             for (int u = 0; u < 32; u++) {
                 const int r = 4 * u + q;
-                zr[u] = (r < H) ? zc[r] : (T)0;
+                zr[u] = (own && r < H) ? zc[top + r] : 0.f;
             }
-            // Reflector off touches rows 4u + q with 0 <= 4u + q - off < QB.  For
-            // u in [ceil(off / 4), floor((off + QB - 4) / 4)] that holds for every
-            // phase q, so those u need no test and read v at a compile-time
-            // offset from the thread's phase pointer; only u = U0 - 1 (when
-            // q >= off - 4 (U0 - 1)) and u = U1 + 1 (when 4 (U1 + 1) + q - off < QB)
-            // depend on q.
-            const T* vq = vs + q;
+        }
+        for (int k = 0; k < kmax; k++) {
+            const int top = s0 + 1 + k * QB;
+            const int buf = blk & 1;
+            const bool more = k + 1 < kmax;
+            // prefetch: the next block's reflectors, and the 64 new rows
+            // top + 127 .. top + 190 of block k+1
+            if (t == 0) {
+                if (more) fetch(g, k + 1, buf ^ 1);
+                else if (g > 0) fetch(g - 1, 0, buf ^ 1);
+            }
+            if (more) {
+                for (int e = t; e < 64 * nc; e += T) {
+                    const int cc = e >> 6, j = e & 63, row = top + QH + j;
+                    float* d = &sm.zin[cc * QS_LD + j];
+                    if (row < n) cp_async4(d, Z + (size_t)(c0 + cc) * ldz + row);
+                    else *d = 0.f;
+                }
+            }
+            if (!mbar_wait(&sm.bar[buf], (uint32_t)(blk >> 1) & 1u, status)) return;
+            const float* vq = sm.v[buf] + q;
+            const float* ts = sm.tau[buf];
 #pragma unroll
             for (int off = QELL - 1; off >= 0; off--) {
-                const T tau = ts[off];
-                if (tau == (T)0) continue;
-                const T* v = vq + off * QB - off;  // v[4u] = element 4u + q - off of reflector off
+                const float tau = ts[off];
+                if (tau == 0.f) continue;
+                const float* v = vq + off * QB - off;  // v[4u] = element 4u + q - off of reflector off
+                // rows 4u + q with 0 <= 4u + q - off < QB: every phase for u in
+                // [U0, U1]; u = U0 - 1 and U1 + 1 depend on q
                 const int U0 = (off + 3) / 4, U1 = (off + QB - 4) / 4;
                 const bool lo_ok = (U0 >= 1) && (q >= off - 4 * (U0 - 1));
                 const bool hi_ok = (U1 + 1 <= 31) && (4 * (U1 + 1) + q - off < QB);
-                T a = 0, a2 = 0;
+                float a = 0.f, a2 = 0.f;
 #pragma unroll
                 for (int u = 0; u < 32; u++) {
                     if (u < U0 || u > U1) continue;
-                    if (u & 1) a2 = fma(v[4 * u], zr[u], a2);
-                    else a = fma(v[4 * u], zr[u], a);
+                    if (u & 1) a2 = fmaf(v[4 * u], zr[u], a2);
+                    else a = fmaf(v[4 * u], zr[u], a);
                 }
-                if (U0 >= 1 && lo_ok) a = fma(v[4 * (U0 - 1)], zr[U0 - 1 < 0 ? 0 : U0 - 1], a);
-                if (U1 + 1 <= 31 && hi_ok) a2 = fma(v[4 * (U1 + 1)], zr[U1 + 1 > 31 ? 31 : U1 + 1], a2);
+                if (U0 >= 1 && lo_ok) a = fmaf(v[4 * (U0 - 1)], zr[U0 - 1 < 0 ? 0 : U0 - 1], a);
+                if (U1 + 1 <= 31 && hi_ok) a2 = fmaf(v[4 * (U1 + 1)], zr[U1 + 1 > 31 ? 31 : U1 + 1], a2);
                 a += a2;
                 a += __shfl_xor_sync(0xffffffffu, a, 1);
                 a += __shfl_xor_sync(0xffffffffu, a, 2);
@@ -118,24 +149,46 @@ qtrd_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ t
 #pragma unroll
                 for (int u = 0; u < 32; u++) {
                     if (u < U0 || u > U1) continue;
-                    zr[u] = fma(-a, v[4 * u], zr[u]);
+                    zr[u] = fmaf(-a, v[4 * u], zr[u]);
                 }
-                if (U0 >= 1 && lo_ok) zr[U0 - 1 < 0 ? 0 : U0 - 1] = fma(-a, v[4 * (U0 - 1)], zr[U0 - 1 < 0 ? 0 : U0 - 1]);
+                if (U0 >= 1 && lo_ok) zr[U0 - 1 < 0 ? 0 : U0 - 1] = fmaf(-a, v[4 * (U0 - 1)], zr[U0 - 1 < 0 ? 0 : U0 - 1]);
                 if (U1 + 1 <= 31 && hi_ok)
-                    zr[U1 + 1 > 31 ? 31 : U1 + 1] = fma(-a, v[4 * (U1 + 1)], zr[U1 + 1 > 31 ? 31 : U1 + 1]);
+                    zr[U1 + 1 > 31 ? 31 : U1 + 1] = fmaf(-a, v[4 * (U1 + 1)], zr[U1 + 1 > 31 ? 31 : U1 + 1]);
             }
-            T* zcw = zw + c * QLD;
+            if (more) {
+                // rows 0..63 are final for this group: out through shared memory
 #pragma unroll
-            for (int u = 0; u < 32; u++) {
-                const int r = 4 * u + q;
-                if (r < H) zcw[r] = zr[u];
+                for (int u = 0; u < 16; u++) sm.zout[c * QS_LD + 4 * u + q] = zr[u];
+                cp_async_wait_all();
+                __syncthreads();
+                for (int e = t; e < 64 * nc; e += T) {
+                    const int cc = e >> 6, j = e & 63;
+                    Z[(size_t)(c0 + cc) * ldz + top + j] = sm.zout[cc * QS_LD + j];  // top + 63 < n here
+                }
+                // slide by 64 rows: rows 64..126 move up, 63..126 of the new
+                // window come from zin (row 127 is padding)
+#pragma unroll
+                for (int u = 0; u < 16; u++) zr[u] = zr[u + 16];
+                if (q == 3) zr[15] = sm.zin[c * QS_LD];
+#pragma unroll
+                for (int u = 16; u < 32; u++) {
+                    const int j = 4 * u + q - (QH - QB);  // zin row of window row 4u + q
+                    zr[u] = (j < 64) ? sm.zin[c * QS_LD + j] : 0.f;
+                }
+                __syncthreads();
+            } else {
+                // last block of the group: the whole window is final
+                const int H = min(QH, n - top);
+                if (own) {
+#pragma unroll
+                    for (int u = 0; u < 32; u++) {
+                        const int r = 4 * u + q;
+                        if (r < H) zc[top + r] = zr[u];
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
-            for (int cc = t >> 5; cc < nc; cc += QT / 32) {
-                T* zdst = Z + (size_t)(c0 + cc) * ldz + top;
-                for (int i = t & 31; i < H; i += 32) zdst[i] = zw[cc * QLD + i];
-            }
-            __syncthreads();
+            blk++;
         }
     }
 }
@@ -221,12 +274,8 @@ QbandWs carve_qband(Carve& cv, int n, int b, int k) {
     return w;
 }
 
-template <typename T>
-cudaError_t apply_qtrd_t(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, T* Z, int ldz,
-                         int k) {
-    if (b != QB) return cudaErrorInvalidValue;
-    if (n < 3 || k <= 0) return cudaSuccess;
-    // slab width so that the CTA count fills the GPU in whole waves
+// Slab width so that the CTA count fills the GPU in whole waves (per CTAs per SM)
+int qtrd_slab(int k, int* grid) {
     const int sms = device_sms();
     int per = 1, slab = 64;
     while (true) {
@@ -235,33 +284,43 @@ cudaError_t apply_qtrd_t(cudaStream_t st, int n, int b, const double* Vtrd, cons
         per++;
     }
     if (slab < 8) slab = (k < 8) ? k : 8;
-    const int grid = (k + slab - 1) / slab;
-    if (sizeof(T) == sizeof(double)) {
-        const size_t smem = sizeof(T) * (size_t)QLD * 64;
-        cudaFuncSetAttribute(qtrd_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        KtScope kt(st, KT_QTRD);
-        qtrd_smem_kernel<T><<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
-        count_launch();
-        return cudaGetLastError();
-    }
-    const size_t smem = sizeof(T) * ((size_t)QLD * 64 + (size_t)QELL * QB + QELL);
-    cudaFuncSetAttribute(qtrd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    KtScope kt(st, KT_QTRD);
-    qtrd_kernel<T><<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
-    count_launch();
-    return cudaGetLastError();
+    *grid = (k + slab - 1) / slab;
+    return slab;
 }
 
 }  // namespace
 
 cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, double* Z, int ldz,
                        int k) {
-    return apply_qtrd_t<double>(st, n, b, Vtrd, tautrd, Z, ldz, k);
+    if (b != QB) return cudaErrorInvalidValue;
+    if (n < 3 || k <= 0) return cudaSuccess;
+    int grid = 0;
+    const int slab = qtrd_slab(k, &grid);
+    const size_t smem = sizeof(double) * (size_t)QLD * 64;
+    cudaFuncSetAttribute(qtrd_smem_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    KtScope kt(st, KT_QTRD);
+    qtrd_smem_kernel<double><<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
+    count_launch();
+    return cudaGetLastError();
 }
 
-cudaError_t apply_qtrd_f32(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, float* Z, int ldz,
-                           int k) {
-    return apply_qtrd_t<float>(st, n, b, Vtrd, tautrd, Z, ldz, k);
+cudaError_t apply_qtrd_f32(cudaStream_t st, int n, int b, const float* V32, const float* tau32, float* Z, int ldz,
+                           int k, int* status) {
+    if (b != QB) return cudaErrorInvalidValue;
+    if (n < 3 || k <= 0) return cudaSuccess;
+    // two CTAs per SM; 4 threads per column of the slab, whole warps
+    const int sms = device_sms();
+    int slab = (k + 2 * sms - 1) / (2 * sms);
+    if (slab > 64) slab = 64;
+    if (slab < 8) slab = (k < 8) ? k : 8;
+    const int grid = (k + slab - 1) / slab;
+    const int threads = (4 * slab + 31) / 32 * 32;
+    const size_t smem = sizeof(QSlideSmem);
+    cudaFuncSetAttribute(qtrd_slide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    KtScope kt(st, KT_QTRD);
+    qtrd_slide_kernel<<<grid, threads, smem, st>>>(n, V32, tau32, Z, ldz, k, slab, status);
+    count_launch();
+    return cudaGetLastError();
 }
 
 size_t qband_ws(int n, int b, int k) {

@@ -54,7 +54,8 @@ __device__ __forceinline__ double chase_ssq(const double* __restrict__ B, int hi
 // sm.v (zero beyond L), sm.tau, sm.beta and the copies kept for the
 // back-transformation.
 __device__ void chase_reflector(const double* __restrict__ B, int L, double a, ChaseSmem& sm,
-                                double* __restrict__ vg, double* __restrict__ tg, double* __restrict__ alpha_s) {
+                                double* __restrict__ vg, double* __restrict__ tg, float* __restrict__ vf,
+                                float* __restrict__ tf, double* __restrict__ alpha_s) {
     const int lane = threadIdx.x & 31;
     const double x0 = B[0];
     const double x1 = (lane < L) ? B[lane] : 0.0;
@@ -72,12 +73,19 @@ __device__ void chase_reflector(const double* __restrict__ B, int L, double a, C
     const double v2 = x2 * sc;
     sm.v[lane] = v1;
     sm.v[lane + 32] = v2;
-    vg[lane] = v1;
-    vg[lane + 32] = v2;
+    if (vg) {
+        vg[lane] = v1;
+        vg[lane + 32] = v2;
+    }
+    if (vf) {
+        vf[lane] = (float)v1;
+        vf[lane + 32] = (float)v2;
+    }
     if (lane == 0) {
         sm.tau = tu;
         sm.beta = be;
-        *tg = tu;
+        if (tg) *tg = tu;
+        if (tf) *tf = (float)tu;
         if (alpha_s) *alpha_s = -be;  // T[s, s+1] = -T[s+1, s]
     }
 }
@@ -115,22 +123,25 @@ __device__ __forceinline__ bool chase_lower(int t, int u, int& i, int& j) {
 // from the load to the update.  Returns false when the wait gave up.
 __device__ bool chase_task(int n, int s, int k, int nsw, const int* __restrict__ prog_prev, int want,
                            int* __restrict__ status, double* __restrict__ AB, int ldab, double* __restrict__ alpha,
-                           double* __restrict__ Vtrd, double* __restrict__ tautrd, double* __restrict__ B,
-                           double* __restrict__ D, double* __restrict__ C, bool have_b, bool keep_c, bool fix_e,
-                           bool defer_e, ChaseSmem& sm) {
+                           double* __restrict__ Vtrd, double* __restrict__ tautrd, float* __restrict__ V32,
+                           float* __restrict__ tau32, int nsw64, double* __restrict__ B, double* __restrict__ D,
+                           double* __restrict__ C, bool have_b, bool keep_c, bool fix_e, bool defer_e,
+                           ChaseSmem& sm) {
     const int t = threadIdx.x, warp = t >> 5;
     const int r = s + 1 + k * CB;
     const int L = min(CB, n - r);
     const int Lc = max(0, min(CB, n - r - CB));
-    double* vg = Vtrd + ((size_t)k * nsw + s) * CB;
-    double* tg = tautrd + (size_t)k * nsw + s;
+    double* vg = Vtrd ? Vtrd + ((size_t)k * nsw + s) * CB : nullptr;
+    double* tg = tautrd ? tautrd + (size_t)k * nsw + s : nullptr;
+    float* vf = V32 ? V32 + ((size_t)k * nsw64 + s) * CB : nullptr;
+    float* tf = tau32 ? tau32 + (size_t)k * nsw64 + s : nullptr;
 
     // a kept B gives its reflector before the wait, or with fix_e all of its
     // sum of squares but the row-63 term
     double ssq = 0.0;
     if (have_b && warp == 0) {
         ssq = chase_ssq(B, fix_e ? CB - 1 : L);
-        if (!fix_e) chase_reflector(B, L, ssq, sm, vg, tg, nullptr);
+        if (!fix_e) chase_reflector(B, L, ssq, sm, vg, tg, vf, tf, nullptr);
     }
     if (t == 32) {
         int ok = 1;
@@ -185,7 +196,7 @@ __device__ bool chase_task(int n, int s, int k, int nsw, const int* __restrict__
             ssq = fma(wc, wc, ssq);  // x_63 = -wc (v_0 = 1)
         }
         __syncwarp();
-        chase_reflector(B, L, ssq, sm, vg, tg, have_b ? nullptr : alpha + s);
+        chase_reflector(B, L, ssq, sm, vg, tg, vf, tf, have_b ? nullptr : alpha + s);
     }
     // D in both triangles (D^T = -D, zero diagonal and outside the block), C
 #pragma unroll
@@ -270,10 +281,11 @@ __device__ bool chase_task(int n, int s, int k, int nsw, const int* __restrict__
 
 __global__ void __launch_bounds__(CH_THREADS)
 chase_kernel(int n, double* __restrict__ AB, int ldab, double* __restrict__ alpha,
-             double* __restrict__ Vtrd, double* __restrict__ tautrd, int* prog, int* status) {
+             double* __restrict__ Vtrd, double* __restrict__ tautrd, float* __restrict__ V32,
+             float* __restrict__ tau32, int* prog, int* status) {
     extern __shared__ __align__(16) unsigned char chase_raw[];
     ChaseSmem& sm = *reinterpret_cast<ChaseSmem*>(chase_raw);
-    const int nsw = n - 2;
+    const int nsw = n - 2, nsw64 = (nsw + 63) / 64 * 64;
     for (int s = blockIdx.x; s < nsw; s += gridDim.x) {
         const int ns = nsteps_of(n, CB, s);
         const int nsp = (s > 0) ? nsteps_of(n, CB, s - 1) : 0;
@@ -288,7 +300,7 @@ chase_kernel(int n, double* __restrict__ AB, int ldab, double* __restrict__ alph
             const int want = (s > 0) ? min(k + 2, nsp) : 0;
             const bool defer_e = s > 0 && n - (s + 1 + k * CB) >= 2 * CB && k + 2 < nsp;
             if (!chase_task(n, s, k, nsw, prog + (s > 0 ? s - 1 : 0), want, status, AB, ldab, alpha, Vtrd, tautrd,
-                            B, D, C, have_b, keep_c, fix_e, defer_e, sm))
+                            V32, tau32, nsw64, B, D, C, have_b, keep_c, fix_e, defer_e, sm))
                 return;
             // all stores of the step precede the release (bar.sync, then a
             // gpu-scope release by one thread)
@@ -317,7 +329,7 @@ size_t chase_ws(int n, int b) {
 }
 
 int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha, double* Vtrd, double* tautrd,
-          void* ws, size_t ws_bytes, int* d_status, unsigned spin_cap) {
+          void* ws, size_t ws_bytes, int* d_status, unsigned spin_cap, float* V32, float* tau32) {
     (void)spin_cap;
     if (b != CB) return SKEW_ERR_UNSUPPORTED;
     if (n < 2) return 0;
@@ -335,7 +347,7 @@ int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha, do
         if (occ < 1) return SKEW_ERR_LAUNCH;
         int G = occ * device_sms();
         if (G > nsw) G = nsw;
-        void* args[] = {&n, &AB, &ldab, &alpha, &Vtrd, &tautrd, &prog, &d_status};
+        void* args[] = {&n, &AB, &ldab, &alpha, &Vtrd, &tautrd, &V32, &tau32, &prog, &d_status};
         KtScope kt(st, KT_CHASE);
         if (cudaLaunchCooperativeKernel((void*)chase_kernel, dim3(G), dim3(CH_THREADS), args, smem, st) != cudaSuccess)
             return SKEW_ERR_LAUNCH;

@@ -50,9 +50,13 @@ int num_panels(int n, int b);
 // ---- chase.cu ---------------------------------------------------------------
 int chase_steps(int n, int b);
 size_t chase_ws(int n, int b);
+// Vtrd / tautrd (may be null): the reflectors in FP64, slot k nsw + s.  V32 /
+// tau32 (may be null): FP32 copies with the sweep stride padded to a multiple
+// of 64 (slot k nsw64 + s); slots of steps a sweep does not have are not
+// written.
 int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha,
           double* Vtrd, double* tautrd, void* ws, size_t ws_bytes, int* d_status,
-          unsigned spin_cap);
+          unsigned spin_cap, float* V32 = nullptr, float* tau32 = nullptr);
 
 // ---- tridiag.cu -------------------------------------------------------------
 size_t tridiag_ws(int n, int nev);
@@ -69,8 +73,10 @@ cudaError_t dmap_colmajor(cudaStream_t st, int n, int k, const double* Q, int ld
 // ---- backtransform.cu -------------------------------------------------------
 cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd,
                        const double* tautrd, double* Z, int ldz, int k);
-cudaError_t apply_qtrd_f32(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, float* Z,
-                           int ldz, int k);
+// FP32 Q_trd from the chase's FP32 reflectors (stride nsw64, taus of absent
+// steps zero).
+cudaError_t apply_qtrd_f32(cudaStream_t st, int n, int b, const float* V32, const float* tau32, float* Z, int ldz,
+                           int k, int* status);
 size_t qband_ws(int n, int b, int k);
 size_t qband_mixed_ws(int n, int b, int k, int planes);
 int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz,

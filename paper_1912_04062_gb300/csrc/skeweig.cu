@@ -65,7 +65,7 @@ struct Plan {
     size_t ldab;
     // carved pointers
     double *W, *Tfac, *AB, *Vtrd, *tautrd, *alpha, *Qi, *Z;
-    float* Z32;
+    float *Z32, *V32, *tau32;  // FP32 Q_trd: Z and the chase's reflectors (sweep stride padded to 64)
     int* status;
     void *ws_reduce, *ws_chase, *ws_tri, *ws_qband, *ws_refine;
     size_t sz_reduce, sz_chase, sz_tri, sz_qband, sz_refine;
@@ -89,6 +89,9 @@ bool carve_plan(Plan& p, Carve& cv) {
     p.Qi = p.vectors ? cv.take<double>(nn * ne) : nullptr;
     p.Z = p.vectors ? cv.take<double>(nn * 2 * ne) : nullptr;
     p.Z32 = (p.vectors && p.qtrd_f32) ? cv.take<float>(nn * 2 * ne) : nullptr;
+    const size_t nsw64 = (nsw + 63) / 64 * 64;
+    p.V32 = (p.vectors && p.qtrd_f32) ? cv.take<float>(K * nsw64 * b) : nullptr;
+    p.tau32 = (p.vectors && p.qtrd_f32) ? cv.take<float>(K * nsw64) : nullptr;
     p.sz_reduce = band_reduce_ws(p.n, p.b, p.reduce_prec);
     p.ws_reduce = cv.take<char>(p.sz_reduce);
     p.sz_chase = chase_ws(p.n, p.b);
@@ -200,7 +203,17 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     mark(2);
     if (band_pack(st, n, p.b, p.W, n, p.AB, (int)p.ldab) != cudaSuccess) return SKEW_ERR_CUDA;
     mark(3);
-    rc = chase(st, n, p.b, p.AB, (int)p.ldab, p.alpha, p.Vtrd, p.tautrd, p.ws_chase, p.sz_chase, p.status, 0);
+    if (p.tau32) {
+        // FP32 reflector copies for Q_trd: the taus of steps a sweep does not
+        // have stay zero (the FP64 copies are not needed then)
+        const size_t nsw64 = ((size_t)p.nsw + 63) / 64 * 64;
+        if (const cudaError_t e = cudaMemsetAsync(p.tau32, 0, sizeof(float) * (size_t)p.K * nsw64, st))
+            return cuda_fail(e);
+        rc = chase(st, n, p.b, p.AB, (int)p.ldab, p.alpha, nullptr, nullptr, p.ws_chase, p.sz_chase, p.status, 0,
+                   p.V32, p.tau32);
+    } else {
+        rc = chase(st, n, p.b, p.AB, (int)p.ldab, p.alpha, p.Vtrd, p.tautrd, p.ws_chase, p.sz_chase, p.status, 0);
+    }
     if (rc) return rc;
     mark(4);
     rc = tridiag_eig(st, n, p.alpha, nev, lambda, vectors ? p.Qi : nullptr, p.ws_tri, p.sz_tri, p.status, maxit);
@@ -217,14 +230,15 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     if (vectors && !p.qtrd_f32) {
         if (apply_qtrd(st, n, p.b, p.Vtrd, p.tautrd, p.Z, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
     } else if (vectors) {
-        // mixed form: Q_trd in FP32 arithmetic (reflectors from the FP64 chase)
+        // mixed form: Q_trd in FP32 arithmetic (the chase's FP32 reflector copies)
         const size_t cnt = (size_t)n * 2 * nev;
         {
             KtScope kt(st, KT_OTHER);
             f64_to_f32_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z, p.Z32);
         }
         count_launch();
-        if (apply_qtrd_f32(st, n, p.b, p.Vtrd, p.tautrd, p.Z32, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (apply_qtrd_f32(st, n, p.b, p.V32, p.tau32, p.Z32, n, 2 * nev, p.status) != cudaSuccess)
+            return SKEW_ERR_CUDA;
         {
             KtScope kt(st, KT_OTHER);
             f32_to_f64_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z32, p.Z);
