@@ -62,8 +62,10 @@ int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha,
 size_t tridiag_ws(int n, int nev);
 // Eigenvalues (descending) and eigenvectors of tridiag(alpha, 0, alpha).
 // Vectors go to Qi in interleaved layout Qi[i * nev + k].
+// fp64 = false: eigenvalues to about 2^-42 ||S|| from double-float counts
+// only (a caller that refines them afterwards); otherwise finished in FP64.
 int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* lambda,
-                double* Qi, void* ws, size_t ws_bytes, int* d_status, int maxit);
+                double* Qi, void* ws, size_t ws_bytes, int* d_status, int maxit, bool fp64 = true);
 // Interleaved Qi -> column-major X (and Y) with optional D map.
 cudaError_t interleaved_to_colmajor(cudaStream_t st, int n, int nev, const double* Qi,
                                     double* X, double* Y, int ldz, bool dmap);

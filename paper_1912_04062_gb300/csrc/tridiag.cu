@@ -30,9 +30,13 @@ namespace {
 
 using namespace tri;
 
+#ifndef BISECT_LANES
+#define BISECT_LANES 2
+#endif
+
 
 __global__ void tri_prep_kernel(int n, const double* __restrict__ alpha, double* __restrict__ a2,
-                                TriScalars* sc) {
+                                float* __restrict__ a2s, float* __restrict__ a2l, TriScalars* sc) {
     __shared__ double red[32];
     double gmax = 0.0, amax = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -56,37 +60,226 @@ __global__ void tri_prep_kernel(int n, const double* __restrict__ alpha, double*
         for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) { g = fmax(g, red[w]); a = fmax(a, red2[w]); }
         sc->g = g;
         sc->pivmin = DBL_MIN * fmax(1.0, a);
+        red[0] = g;
+    }
+    __syncthreads();
+    // alpha^2 / g^2 as an FP32 pair (a2s + a2l) for the bracketing passes
+    // (entries below FLT_MIN become 0: a perturbation far below their
+    // tolerances)
+    const double g = red[0], ig2 = (g > 0.0) ? 1.0 / (g * g) : 0.0;
+    for (int i = threadIdx.x; i < n - 1; i += blockDim.x) {
+        const double v = a2[i] * ig2;
+        const float h = (float)v;
+        a2s[i] = h;
+        a2l[i] = (float)(v - (double)h);
     }
 }
 
-// Multisection: four lanes per wanted eigenvalue each count at one of four
-// equally spaced interior points of the current interval, which shrinks to one
-// fifth per step (same Sturm recurrence and stopping rule as bisect_one).
-__global__ void bisect4_kernel(int n, int nev, const double* __restrict__ a2, const TriScalars* sc,
-                               double* __restrict__ lambda) {
+// ---- double-float (FP32 pair) arithmetic: Dekker, "A floating-point
+// technique for extending the available precision" (1971); Knuth's two_sum.
+// About 46 bits, at FP32-pipe latency.
+struct Df {
+    float h, l;
+};
+__device__ __forceinline__ Df df_of(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ Df df_fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+// (a + b) with an error below a few 2^-46 (|a| + |b|): as a perturbation of
+// the shift and of the quotient separately, which a Sturm count tolerates
+__device__ __forceinline__ Df df_add(Df a, Df b) {
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b.h - bb);
+    return df_fast_two_sum(s, e + (a.l + b.l));
+}
+// a / b: quotient of the leading parts, corrected by the exact remainder
+__device__ __forceinline__ Df df_div(Df a, Df b) {
+    const float q1 = __fdividef(a.h, b.h);
+    const float p1 = q1 * b.h;
+    const float p2 = fmaf(q1, b.h, -p1);
+    const float r = (((a.h - p1) - p2) + a.l) - q1 * b.l;
+    return df_fast_two_sum(q1, __fdividef(r, b.h));
+}
+
+constexpr float PIV_DF = 7.888609052210118e-31f;  // 2^-100: pivots of S / g raised to this
+
+// Double-float Sturm count of S / g at x (the recurrence of sturm()).
+__device__ __forceinline__ int sturm_df(int n, const float* __restrict__ a2s, const float* __restrict__ a2l, Df x) {
+    int cnt = 0;
+    Df d = {-x.h, -x.l};
+    if (fabsf(d.h) < PIV_DF) d = {-PIV_DF, 0.f};
+    cnt += (d.h < 0.f);
+    for (int i = 1; i < n; i++) {
+        const Df t = df_add(x, df_div({a2s[i - 1], a2l[i - 1]}, d));
+        d = {-t.h, -t.l};
+        if (fabsf(d.h) < PIV_DF) d = {-PIV_DF, 0.f};
+        cnt += (d.h < 0.f);
+    }
+    return cnt;
+}
+
+// FP32 Sturm count of the scaled matrix S / g at x (|x| ~ 1): the recurrence
+// of sturm() with pivots below FLT_MIN raised to FLT_MIN.
+__device__ __forceinline__ int sturm32(int n, const float* __restrict__ a2s, float x) {
+    int cnt = 0;
+    float d = -x;
+    if (fabsf(d) < FLT_MIN) d = -FLT_MIN;
+    cnt += (d < 0.f);
+    for (int i = 1; i < n; i++) {
+        d = -x - __fdividef(a2s[i - 1], d);
+        if (fabsf(d) < FLT_MIN) d = -FLT_MIN;
+        cnt += (d < 0.f);
+    }
+    return cnt;
+}
+
+// Bracketing pass in FP32 (64 times the FP64 rate on this part): four lanes
+// per wanted eigenvalue multisect [-1, 1] for S / g down to 8 eps32.  A
+// floating-point Sturm count is the exact count of a matrix whose entries are
+// perturbed by a few units of roundoff (Kahan), so lambda_j lies within a few
+// eps32 g of the FP32 bracket; the FP64 pass widens it by FP32_SLACK eps32 g
+// and checks it with FP64 counts before trusting it.
+__global__ void bisect32_kernel(int n, int nev, const float* __restrict__ a2s, const TriScalars* sc,
+                                double* __restrict__ lohi) {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gt >> 2, q = gt & 3, lane = threadIdx.x & 31;
-    if (k >= nev) return;  // whole groups of four leave together (blockDim is a multiple of 4)
+    if (k >= nev) return;
     const unsigned gmask = 0xFu << (lane & ~3);
+    const int j = n - 1 - k;
+    float lo = -1.0f - 4.0f * FLT_EPSILON, hi = 1.0f + 4.0f * FLT_EPSILON;
+    for (int it = 0; it < 64; it++) {
+        const float w = hi - lo;
+        if (w <= 8.0f * FLT_EPSILON) break;
+        const float step = w * 0.2f;
+        const float x = lo + (float)(q + 1) * step;
+        const bool le = (x > lo && x < hi) ? (sturm32(n, a2s, x) <= j) : (x <= lo);
+        const int nle = __popc(__ballot_sync(gmask, le) & gmask);
+        const float nlo = (nle > 0) ? lo + (float)nle * step : lo;
+        const float nhi = (nle < 4) ? lo + (float)(nle + 1) * step : hi;
+        if (!(nlo > lo || nhi < hi)) break;
+        lo = nlo;
+        hi = (nhi < hi) ? nhi : hi;
+    }
+    if (q == 0) {
+        lohi[2 * k] = (double)lo;  // in units of g
+        lohi[2 * k + 1] = (double)hi;
+    }
+}
+
+// Second pass: four lanes multisect the FP32 bracket (widened by FP32_SLACK
+// eps32, checked with double-float counts and widened eightfold until the
+// check holds) with double-float counts down to DF_WIDTH.  Writes the
+// bracket (units of g) back and, in lambda, its midpoint times g.
+constexpr double FP32_SLACK = 64.0;
+constexpr double DF_WIDTH = 1.0 / 4398046511104.0;  // 2^-42
+__global__ void bisect_df_kernel(int n, int nev, const float* __restrict__ a2s, const float* __restrict__ a2l,
+                                 const TriScalars* sc, double* __restrict__ lohi, double* __restrict__ lambda) {
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = gt >> 2, q = gt & 3, lane = threadIdx.x & 31;
+    if (k >= nev) return;
+    const unsigned gmask = 0xFu << (lane & ~3);
+    const int j = n - 1 - k;
+    const double g = sc->g;
+    if (n == 1 || g == 0.0) {
+        if (q == 0) lambda[k] = 0.0;
+        return;
+    }
+    const double glo = -1.0 - 1e-6, ghi = 1.0 + 1e-6;
+    double lo = glo, hi = ghi;
+    double slack = FP32_SLACK * FLT_EPSILON;
+    for (int tries = 0; tries < 8; tries++) {
+        const double a = fmax(glo, lohi[2 * k] - slack), b = fmin(ghi, lohi[2 * k + 1] + slack);
+        bool mine = true;
+        if (q == 0) mine = (a == glo) || sturm_df(n, a2s, a2l, df_of(a)) <= j;
+        if (q == 1) mine = (b == ghi) || sturm_df(n, a2s, a2l, df_of(b)) > j;
+        if ((__ballot_sync(gmask, !mine) & gmask) == 0u) {
+            lo = a;
+            hi = b;
+            break;
+        }
+        slack *= 8.0;
+    }
+    for (int it = 0; it < 64; it++) {
+        const double w = hi - lo;
+        if (w <= DF_WIDTH) break;
+        const double step = w * 0.2;
+        const double x = lo + (double)(q + 1) * step;
+        const bool le = (x > lo && x < hi) ? (sturm_df(n, a2s, a2l, df_of(x)) <= j) : (x <= lo);
+        const int nle = __popc(__ballot_sync(gmask, le) & gmask);
+        const double nlo = (nle > 0) ? lo + (double)nle * step : lo;
+        const double nhi = (nle < 4) ? lo + (double)(nle + 1) * step : hi;
+        if (!(nlo > lo || nhi < hi)) break;
+        lo = nlo;
+        hi = (nhi < hi) ? nhi : hi;
+    }
+    if (q == 0) {
+        lohi[2 * k] = lo;
+        lohi[2 * k + 1] = hi;
+        lambda[k] = (lo + 0.5 * (hi - lo)) * g;
+    }
+}
+
+constexpr double DF_SLACK = 1.0 / 68719476736.0;  // 2^-36: widening of a double-float bracket (units of g)
+
+// FP64 multisection with L lanes per wanted eigenvalue (L = 1: bisection):
+// each lane counts at one of L equally spaced interior points, the interval
+// shrinks to 1 / (L + 1) per step (stopping rule of bisect_one).  With lohi,
+// the start is the double-float bracket (units of g) widened by DF_SLACK g
+// once its ends pass the FP64 counts count(lo) <= j < count(hi); a bracket
+// that fails is widened eightfold, up to the whole Gershgorin interval.
+template <int L>
+__global__ void bisect_kernel(int n, int nev, const double* __restrict__ a2, const TriScalars* sc,
+                              const double* __restrict__ lohi, double* __restrict__ lambda) {
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = gt / L, q = gt % L, lane = threadIdx.x & 31;
+    if (k >= nev) return;  // whole lane groups leave together (blockDim is a multiple of L)
+    const unsigned gmask = (L == 1) ? (1u << lane) : (((1u << L) - 1u) << (lane & ~(L - 1)));
     const double g = sc->g, pivmin = sc->pivmin;
     const int j = n - 1 - k;  // ascending index of the wanted eigenvalue
     if (n == 1 || g == 0.0) {
         if (q == 0) lambda[k] = 0.0;
         return;
     }
-    double lo = -g - 2.0 * DBL_EPSILON * g - pivmin;
-    double hi = g + 2.0 * DBL_EPSILON * g + pivmin;
-    for (int it = 0; it < 2000; it++) {
+    const double glo = -g - 2.0 * DBL_EPSILON * g - pivmin, ghi = g + 2.0 * DBL_EPSILON * g + pivmin;
+    double lo = glo, hi = ghi;
+    if (lohi) {
+        double slack = DF_SLACK * g;
+        for (int tries = 0; tries < 8; tries++) {
+            const double a = fmax(glo, lohi[2 * k] * g - slack), b = fmin(ghi, lohi[2 * k + 1] * g + slack);
+            bool ok;
+            if (L == 1) {
+                ok = (a == glo || sturm(n, a2, pivmin, a) <= j) && (b == ghi || sturm(n, a2, pivmin, b) > j);
+            } else {
+                // lane 0 checks the lower end, lane 1 the upper one
+                bool mine = true;
+                if (q == 0) mine = (a == glo) || sturm(n, a2, pivmin, a) <= j;
+                if (q == 1) mine = (b == ghi) || sturm(n, a2, pivmin, b) > j;
+                ok = (__ballot_sync(gmask, !mine) & gmask) == 0u;
+            }
+            if (ok) {
+                lo = a;
+                hi = b;
+                break;
+            }
+            slack *= 8.0;
+        }
+    }
+    for (int it = 0; it < 4000; it++) {
         const double w = hi - lo;
         const double tol = 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_MIN;
         if (w <= tol) break;
-        const double step = w * 0.2;
+        const double step = w / (double)(L + 1);
         const double x = lo + (double)(q + 1) * step;
         const bool le = (x > lo && x < hi) ? (sturm(n, a2, pivmin, x) <= j) : (x <= lo);
         // counts grow with x: the lanes with lambda_j >= x_q are a prefix
-        const int nle = __popc(__ballot_sync(gmask, le) & gmask);
+        const int nle = (L == 1) ? (le ? 1 : 0) : __popc(__ballot_sync(gmask, le) & gmask);
         const double nlo = (nle > 0) ? lo + (double)nle * step : lo;
-        const double nhi = (nle < 4) ? lo + (double)(nle + 1) * step : hi;
+        const double nhi = (nle < L) ? lo + (double)(nle + 1) * step : hi;
         if (!(nlo > lo || nhi < hi)) break;  // no representable progress
         lo = nlo;
         hi = (nhi < hi) ? nhi : hi;
@@ -154,6 +347,8 @@ __global__ void dmap_colmajor_kernel(int n, int k, const double* __restrict__ Q,
 
 struct TriWs {
     double* a2;
+    float *a2s, *a2l;  // alpha^2 / g^2 as an FP32 pair (bracketing passes)
+    double* lohi;   // FP32 brackets, 2 per wanted eigenvalue
     TriScalars* sc;
     int* fail;
     InvitBufs bf;
@@ -163,6 +358,9 @@ TriWs carve_tri(Carve& cv, int n, int nev) {
     TriWs w{};
     size_t nn = (size_t)(n > 0 ? n : 1), ne = (size_t)(nev > 0 ? nev : 1);
     w.a2 = cv.take<double>(nn);
+    w.a2s = cv.take<float>(nn);
+    w.a2l = cv.take<float>(nn);
+    w.lohi = cv.take<double>(2 * ne);
     w.sc = cv.take<TriScalars>(1);
     w.fail = cv.take<int>(1);
     w.bf.u0 = cv.take<double>(nn * ne);
@@ -182,18 +380,24 @@ size_t tridiag_ws(int n, int nev) {
 }
 
 int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* lambda, double* Qi, void* ws,
-                size_t ws_bytes, int* d_status, int maxit) {
+                size_t ws_bytes, int* d_status, int maxit, bool fp64) {
     if (n <= 0 || nev <= 0) return 0;
     Carve cv(ws, ws_bytes);
     TriWs w = carve_tri(cv, n, nev);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
-    tri_prep_kernel<<<1, 1024, 0, st>>>(n, alpha, w.a2, w.sc);
+    tri_prep_kernel<<<1, 1024, 0, st>>>(n, alpha, w.a2, w.a2s, w.a2l, w.sc);
     count_launch();
     {
         KtScope kt(st, KT_BISECT);
-        bisect4_kernel<<<(4 * nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2, w.sc, lambda);
+        bisect32_kernel<<<(4 * nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2s, w.sc, w.lohi);
+        bisect_df_kernel<<<(4 * nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2s, w.a2l, w.sc, w.lohi, lambda);
+        count_launch(2);
+        if (fp64) {
+            bisect_kernel<BISECT_LANES><<<(BISECT_LANES * nev + 63) / 64, 64, 0, st>>>(n, nev, w.a2, w.sc, w.lohi,
+                                                                                        lambda);
+            count_launch();
+        }
     }
-    count_launch();
     if (Qi) {
         // cluster tolerance relative to ||S||_1: 1e-3 for small n (the usual
         // inverse-iteration choice), shrinking like n^-1.5 so that clusters stay
