@@ -358,7 +358,7 @@ int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw, const d
 // recursion of Eq. 7, T_1..j = [[T_1..j-1, -T_1..j-1 (V_1..j-1^T V_j) T_j],
 // [0, T_j]], so Z is read and written once per QG panels and the update has
 // K = QG b)
-constexpr int QG = 4;
+constexpr int QG = 8;
 
 static size_t qband_gemm_ws(int n, int b, int k, int planes) {
     size_t g1, g2;

@@ -5,17 +5,27 @@
 //
 // Sec. 3 (the solver BSEPACK adapted from ScaLAPACK): bisection + inverse
 // iteration.
-//   * Bisection: four lanes per wanted eigenvalue (the nev largest) count at
-//     four interior points per step (multisection); Sturm
-//     counts from the LDL^T pivots d_0 = -x, d_i = -x - alpha_{i-1}^2/d_{i-1}
-//     (tiny pivots replaced by -pivmin); interval [-g, g], g = ||S||_1.
+//   * Bisection: Sturm counts from the LDL^T pivots d_0 = -x,
+//     d_i = -x - alpha_{i-1}^2/d_{i-1} (tiny pivots replaced by -pivmin) on
+//     [-g, g], g = ||S||_1, for the nev largest eigenvalues.  GB300 runs FP64
+//     at 1/64 of the FP32 rate and the FP64 recurrence is latency-bound
+//     (the division chain), so the counts run in three precisions: FP32
+//     counts of S / g bracket each eigenvalue to 8 eps32 (four lanes
+//     multisect), double-float counts (FP32 pairs) check the bracket widened
+//     by 64 eps32 and narrow it to 2^-42, and, where the eigenvalues are not
+//     refined afterwards, FP64 counts check it again (widened by 2^-36 g) and
+//     finish it with two-lane multisection.  Each floating-point Sturm count
+//     is exact for a matrix perturbed by a few units of its roundoff
+//     (Kahan), hence the widening before each check.
 //   * Inverse iteration: Gaussian elimination with partial pivoting of
 //     S - lambda I (pivots below eps g raised to eps g), a counter-based
 //     (splitmix64) start vector, at most maxit solves, one extra solve after
 //     the growth test passes.  Eigenvalues closer than ctol form a cluster; one
 //     thread handles a whole cluster and orthogonalises (modified Gram-Schmidt)
 //     each new vector against the cluster's earlier vectors after every solve.
-//     The largest-modulus entry of each vector is made positive.
+//     The largest-modulus entry of each vector is made positive.  When the
+//     vectors are refined afterwards, the same steps run in double-float
+//     arithmetic (eps = 2^-44).
 // Vectors are kept interleaved, Q[i * nev + k], so consecutive threads
 // (consecutive k) touch consecutive addresses in every sweep over i.
 #include <cfloat>
@@ -36,7 +46,8 @@ using namespace tri;
 
 
 __global__ void tri_prep_kernel(int n, const double* __restrict__ alpha, double* __restrict__ a2,
-                                float* __restrict__ a2s, float* __restrict__ a2l, TriScalars* sc) {
+                                float* __restrict__ a2s, float* __restrict__ a2l, float* __restrict__ alh,
+                                float* __restrict__ all_, TriScalars* sc) {
     __shared__ double red[32];
     double gmax = 0.0, amax = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -72,38 +83,10 @@ __global__ void tri_prep_kernel(int n, const double* __restrict__ alpha, double*
         const float h = (float)v;
         a2s[i] = h;
         a2l[i] = (float)(v - (double)h);
+        const float ah = (float)alpha[i];  // alpha itself as a pair (double-float inverse iteration)
+        alh[i] = ah;
+        all_[i] = (float)(alpha[i] - (double)ah);
     }
-}
-
-// ---- double-float (FP32 pair) arithmetic: Dekker, "A floating-point
-// technique for extending the available precision" (1971); Knuth's two_sum.
-// About 46 bits, at FP32-pipe latency.
-struct Df {
-    float h, l;
-};
-__device__ __forceinline__ Df df_of(double x) {
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ Df df_fast_two_sum(float a, float b) {
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-// (a + b) with an error below a few 2^-46 (|a| + |b|): as a perturbation of
-// the shift and of the quotient separately, which a Sturm count tolerates
-__device__ __forceinline__ Df df_add(Df a, Df b) {
-    const float s = a.h + b.h;
-    const float bb = s - a.h;
-    const float e = (a.h - (s - bb)) + (b.h - bb);
-    return df_fast_two_sum(s, e + (a.l + b.l));
-}
-// a / b: quotient of the leading parts, corrected by the exact remainder
-__device__ __forceinline__ Df df_div(Df a, Df b) {
-    const float q1 = __fdividef(a.h, b.h);
-    const float p1 = q1 * b.h;
-    const float p2 = fmaf(q1, b.h, -p1);
-    const float r = (((a.h - p1) - p2) + a.l) - q1 * b.l;
-    return df_fast_two_sum(q1, __fdividef(r, b.h));
 }
 
 constexpr float PIV_DF = 7.888609052210118e-31f;  // 2^-100: pivots of S / g raised to this
@@ -287,6 +270,14 @@ __global__ void bisect_kernel(int n, int nev, const double* __restrict__ a2, con
     if (q == 0) lambda[k] = lo + 0.5 * (hi - lo);
 }
 
+__global__ void invit_df_kernel(int n, int nev, const float* __restrict__ alh, const float* __restrict__ all_,
+                                const double* __restrict__ lambda, const TriScalars* sc, double ctol_rel, int maxit,
+                                InvitBufs bf, double* __restrict__ Q, int* __restrict__ fail) {
+    const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k0 >= nev) return;
+    invit_cluster_df(n, nev, alh, all_, lambda, sc->g, ctol_rel, maxit, bf, Q, fail, k0);
+}
+
 __global__ void invit_kernel(int n, int nev, const double* __restrict__ alpha,
                              const double* __restrict__ lambda, const TriScalars* sc, double ctol_rel,
                              int maxit, InvitBufs bf, double* __restrict__ Q, int* __restrict__ fail) {
@@ -348,6 +339,7 @@ __global__ void dmap_colmajor_kernel(int n, int k, const double* __restrict__ Q,
 struct TriWs {
     double* a2;
     float *a2s, *a2l;  // alpha^2 / g^2 as an FP32 pair (bracketing passes)
+    float *alh, *all_;  // alpha as an FP32 pair (double-float inverse iteration)
     double* lohi;   // FP32 brackets, 2 per wanted eigenvalue
     TriScalars* sc;
     int* fail;
@@ -360,6 +352,8 @@ TriWs carve_tri(Carve& cv, int n, int nev) {
     w.a2 = cv.take<double>(nn);
     w.a2s = cv.take<float>(nn);
     w.a2l = cv.take<float>(nn);
+    w.alh = cv.take<float>(nn);
+    w.all_ = cv.take<float>(nn);
     w.lohi = cv.take<double>(2 * ne);
     w.sc = cv.take<TriScalars>(1);
     w.fail = cv.take<int>(1);
@@ -385,7 +379,7 @@ int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* la
     Carve cv(ws, ws_bytes);
     TriWs w = carve_tri(cv, n, nev);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
-    tri_prep_kernel<<<1, 1024, 0, st>>>(n, alpha, w.a2, w.a2s, w.a2l, w.sc);
+    tri_prep_kernel<<<1, 1024, 0, st>>>(n, alpha, w.a2, w.a2s, w.a2l, w.alh, w.all_, w.sc);
     count_launch();
     {
         KtScope kt(st, KT_BISECT);
@@ -407,7 +401,12 @@ int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* la
         count_launch();
         {
             KtScope kt(st, KT_INVIT);
-            invit_kernel<<<(nev + 63) / 64, 64, 0, st>>>(n, nev, alpha, lambda, w.sc, ctol, maxit, w.bf, Qi, w.fail);
+            if (fp64)
+                invit_kernel<<<(nev + 63) / 64, 64, 0, st>>>(n, nev, alpha, lambda, w.sc, ctol, maxit, w.bf, Qi,
+                                                             w.fail);
+            else
+                invit_df_kernel<<<(nev + 63) / 64, 64, 0, st>>>(n, nev, w.alh, w.all_, lambda, w.sc, ctol, maxit,
+                                                                w.bf, Qi, w.fail);
         }
         count_launch();
         invit_status_kernel<<<1, 32, 0, st>>>(w.fail, nev, d_status);

@@ -54,6 +54,45 @@ __device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsi
     return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 
+// ---- double-float (FP32 pair) arithmetic: Dekker, "A floating-point
+// technique for extending the available precision" (1971); Knuth's two_sum.
+// About 46 bits, at FP32-pipe latency.
+struct Df {
+    float h, l;
+};
+__device__ __forceinline__ Df df_of(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ Df df_fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+// (a + b) with an error below a few 2^-46 (|a| + |b|): as a perturbation of
+// the shift and of the quotient separately, which a Sturm count tolerates
+__device__ __forceinline__ Df df_add(Df a, Df b) {
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b.h - bb);
+    return df_fast_two_sum(s, e + (a.l + b.l));
+}
+// a / b: quotient of the leading parts, corrected by the exact remainder
+__device__ __forceinline__ Df df_div(Df a, Df b) {
+    const float q1 = __fdividef(a.h, b.h);
+    const float p1 = q1 * b.h;
+    const float p2 = fmaf(q1, b.h, -p1);
+    const float r = (((a.h - p1) - p2) + a.l) - q1 * b.l;
+    return df_fast_two_sum(q1, __fdividef(r, b.h));
+}
+
+__device__ __forceinline__ Df df_mul(Df a, Df b) {
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p) + (a.h * b.l + a.l * b.h);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ Df df_neg(Df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ double df_to_double(Df a) { return (double)a.h + (double)a.l; }
+
 struct InvitBufs {
     double *u0, *u1, *u2, *ml;
     unsigned char* sw;
@@ -163,6 +202,128 @@ __device__ __forceinline__ void invit_cluster(int n, int nev, const double* __re
         if (Q[imax * ld + k] < 0.0)
             for (int i = 0; i < n; i++) Q[i * ld + k] = -Q[i * ld + k];
     }
+}
+
+// Inverse iteration in double-float (about 2^-44 relative; Dekker's pair
+// arithmetic runs at FP32 latency, the FP64 division chain here is about ten
+// times longer): for a caller that refines the vectors afterwards.  The steps
+// are those of invit_cluster with the pivot floor and growth threshold taken
+// at 2^-44; the LU rows and the vectors are kept as FP32 pairs in the same
+// buffers, and the cluster's vectors are converted to FP64 at the end.
+// alpha as a pair: alh + all_.
+__device__ __forceinline__ void invit_cluster_df(int n, int nev, const float* __restrict__ alh,
+                                                 const float* __restrict__ all_, const double* __restrict__ lambda,
+                                                 double g, double ctol_rel, int maxit, const InvitBufs& bf,
+                                                 double* __restrict__ Q, int* __restrict__ fail, int k0) {
+    const double ctol = ctol_rel * g;
+    if (k0 > 0 && !(lambda[k0 - 1] - lambda[k0] > ctol)) return;  // not a cluster leader
+    int k1 = k0 + 1;
+    while (k1 < nev && !(lambda[k1 - 1] - lambda[k1] > ctol)) k1++;
+    const size_t ld = (size_t)nev;
+    if (n == 1 || g == 0.0) {
+        for (int k = k0; k < k1; k++)
+            for (int i = 0; i < n; i++) Q[i * ld + k] = (i == k) ? 1.0 : 0.0;
+        return;
+    }
+    const double eps = 1.0 / 17592186044416.0;  // 2^-44
+    const float ptol = (float)(eps * g);
+    const float grow = (float)(1.0 / (100.0 * sqrt((double)n) * eps * g));
+    Df* U0 = reinterpret_cast<Df*>(bf.u0);
+    Df* U1 = reinterpret_cast<Df*>(bf.u1);
+    Df* U2 = reinterpret_cast<Df*>(bf.u2);
+    Df* ML = reinterpret_cast<Df*>(bf.ml);
+    Df* Qd = reinterpret_cast<Df*>(Q);
+    const Df zero = {0.f, 0.f};
+    for (int k = k0; k < k1; k++) {
+        const Df mlam = df_neg(df_of(lambda[k]));
+        // ---- LU with partial pivoting of S - lam I (U rows: U0, U1, U2)
+        Df a0 = mlam, a1 = {alh[0], all_[0]};
+        for (int i = 0; i < n - 1; i++) {
+            const Df l = {alh[i], all_[i]};
+            const Df un = (i + 1 < n - 1) ? Df{alh[i + 1], all_[i + 1]} : zero;
+            const size_t at = i * ld + k;
+            if (fabsf(a0.h) >= fabsf(l.h)) {
+                Df piv = a0;
+                if (fabsf(piv.h) < ptol) piv = {(piv.h < 0.f) ? -ptol : ptol, 0.f};
+                const Df m = df_div(l, piv);
+                U0[at] = piv; U1[at] = a1; U2[at] = zero; bf.sw[at] = 0; ML[at] = m;
+                a0 = df_add(mlam, df_neg(df_mul(m, a1)));
+                a1 = un;
+            } else {
+                const Df m = df_div(a0, l);
+                U0[at] = l; U1[at] = mlam; U2[at] = un; bf.sw[at] = 1; ML[at] = m;
+                const Df na0 = df_add(a1, df_neg(df_mul(m, mlam)));
+                a1 = df_neg(df_mul(m, un));
+                a0 = na0;
+            }
+        }
+        if (fabsf(a0.h) < ptol) a0 = {(a0.h < 0.f) ? -ptol : ptol, 0.f};
+        {
+            const size_t at = (size_t)(n - 1) * ld + k;
+            U0[at] = a0; U1[at] = zero; U2[at] = zero;
+        }
+        // ---- start vector (the FP64 routine's), norms in FP32
+        float nrm = 0.f;
+        for (int i = 0; i < n; i++) {
+            const Df x = df_of(splitmix_uniform((unsigned long long)k + 1ULL, (unsigned long long)i));
+            Qd[i * ld + k] = x;
+            nrm = fmaf(x.h, x.h, nrm);
+        }
+        {
+            const Df s = {1.0f / sqrtf(nrm), 0.f};
+            for (int i = 0; i < n; i++) Qd[i * ld + k] = df_mul(Qd[i * ld + k], s);
+        }
+        bool conv = false, done = false;
+        for (int it = 0; it < maxit && !done; it++) {
+            // forward: interchanges and multipliers
+            Df prev = Qd[k];
+            for (int i = 0; i < n - 1; i++) {
+                const size_t at = i * ld + k;
+                Df next = Qd[at + ld];
+                if (bf.sw[at]) { const Df tmp = prev; prev = next; next = tmp; }
+                Qd[at] = prev;
+                prev = df_add(next, df_neg(df_mul(ML[at], prev)));
+            }
+            // back substitution
+            Df y2 = zero, y1 = df_div(prev, U0[(size_t)(n - 1) * ld + k]);
+            Qd[(size_t)(n - 1) * ld + k] = y1;
+            for (int i = n - 2; i >= 0; i--) {
+                const size_t at = i * ld + k;
+                const Df r = df_add(Qd[at], df_neg(df_add(df_mul(U1[at], y1), df_mul(U2[at], y2))));
+                const Df y = df_div(r, U0[at]);
+                Qd[at] = y;
+                y2 = y1;
+                y1 = y;
+            }
+            // orthogonalise against the earlier vectors of the cluster
+            for (int p = k0; p < k; p++) {
+                Df d = zero;
+                for (int i = 0; i < n; i++) d = df_add(d, df_mul(Qd[i * ld + p], Qd[i * ld + k]));
+                const Df md = df_neg(d);
+                for (int i = 0; i < n; i++) Qd[i * ld + k] = df_add(Qd[i * ld + k], df_mul(md, Qd[i * ld + p]));
+            }
+            nrm = 0.f;
+            for (int i = 0; i < n; i++) { const float y = Qd[i * ld + k].h; nrm = fmaf(y, y, nrm); }
+            nrm = sqrtf(nrm);
+            if (!(nrm > 0.f) || !isfinite(nrm)) break;
+            const Df s = {1.0f / nrm, 0.f};
+            for (int i = 0; i < n; i++) Qd[i * ld + k] = df_mul(Qd[i * ld + k], s);
+            if (conv) done = true;
+            else if (nrm >= grow) conv = true;
+        }
+        if (!conv) atomicMin(fail, k);
+        // sign: largest-modulus entry positive (lowest index on ties)
+        int imax = 0;
+        float vmax = fabsf(Qd[k].h);
+        for (int i = 1; i < n; i++) {
+            const float a = fabsf(Qd[i * ld + k].h);
+            if (a > vmax) { vmax = a; imax = i; }
+        }
+        if (Qd[imax * ld + k].h < 0.f)
+            for (int i = 0; i < n; i++) Qd[i * ld + k] = df_neg(Qd[i * ld + k]);
+    }
+    for (int k = k0; k < k1; k++)
+        for (int i = 0; i < n; i++) Q[i * ld + k] = df_to_double(Qd[i * ld + k]);
 }
 
 }  // namespace tri
