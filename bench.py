@@ -72,9 +72,13 @@ def parse():
                    help="mixed: BF16x6 tensor-core contractions + FP64 refinement; fp64: every step FP64")
     p.add_argument("--fp64-compare", type=int, default=1,
                    help="also time this many solves of the FP64 form (reported beside the mixed form)")
-    p.add_argument("--workload", default="single", choices=["single", "batched"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "gemm"],
                    help="batched: many independent small solves (skew_eig_batched_ex) against a loop of "
-                        "single solves (skew_eig_ex) on the same matrices")
+                        "single solves (skew_eig_ex) on the same matrices; gemm: one FP64-accurate "
+                        "digit-slice product C = A B^T (skew_gemm_f64acc_ex) of the shape --gemm, for "
+                        "kernel profiles")
+    p.add_argument("--gemm", default="4096,4096,4096,8,0",
+                   help="M,N,K,slices,lower of the gemm workload")
     p.add_argument("--batch-count", type=int, default=2000)
     return p.parse_args()
 
@@ -475,6 +479,40 @@ def run_batched(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_gemm(args, ws, rank, local):
+    """One digit-slice product of the given shape on seeded Gaussian operands
+    (A: M x K with K contiguous, B: N x K), timed with CUDA events after the
+    warm-up; a kernel-profiling driver, not a solver benchmark."""
+    import torch
+    import paper_1912_04062_gb300 as sk
+    M, N, K, sl, lower = (int(x) for x in args.gemm.split(","))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    g = torch.Generator(device=dev).manual_seed(1234)
+    A = torch.randn(M, K, dtype=torch.float64, device=dev, generator=g)
+    B = torch.randn(N, K, dtype=torch.float64, device=dev, generator=g)
+    C = sk.fortran_empty(M, N, dev)
+    C.zero_()
+    for _ in range(args.warmup):
+        sk.gemm_f64acc(A, B, C, slices=sl, lower=bool(lower))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sk.gemm_f64acc(A, B, C, slices=sl, lower=bool(lower))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    outs = M * N / 2 if lower else M * N
+    pairs = sl * (sl + 1) // 2
+    if rank == 0:
+        print(json.dumps({"workload": "gemm", "M": M, "N": N, "K": K, "slices": sl, "lower": lower,
+                          "ms_per_product": ms, "bf16_tflops": 2 * pairs * outs * K / ms / 1e9,
+                          "fp64_equiv_tflops": 2 * outs * K / ms / 1e9, "steps": args.steps,
+                          "warmup": args.warmup}))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -482,6 +520,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batched":
         run_batched(args, ws, rank, local)
+    elif args.workload == "gemm":
+        run_gemm(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

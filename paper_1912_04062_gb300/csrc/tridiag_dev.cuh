@@ -269,45 +269,94 @@ __device__ __forceinline__ void invit_cluster_df(int n, int nev, const float* __
             Qd[i * ld + k] = x;
             nrm = fmaf(x.h, x.h, nrm);
         }
-        {
-            const Df s = {1.0f / sqrtf(nrm), 0.f};
-            for (int i = 0; i < n; i++) Qd[i * ld + k] = df_mul(Qd[i * ld + k], s);
-        }
+        // The sweeps below are sequential in i and each thread owns column k:
+        // loads run IB elements ahead of the dependent arithmetic (a store to
+        // element i never precedes the load of element i), so the chain waits
+        // on global memory once per IB elements instead of once per element.
+        constexpr int IB = 8;
+        auto scale = [&](Df s) {
+            for (int i0 = 0; i0 < n; i0 += IB) {
+                Df v[IB];
+#pragma unroll
+                for (int u = 0; u < IB; u++)
+                    if (i0 + u < n) v[u] = Qd[(size_t)(i0 + u) * ld + k];
+#pragma unroll
+                for (int u = 0; u < IB; u++)
+                    if (i0 + u < n) Qd[(size_t)(i0 + u) * ld + k] = df_mul(v[u], s);
+            }
+        };
+        scale({1.0f / sqrtf(nrm), 0.f});
         bool conv = false, done = false;
         for (int it = 0; it < maxit && !done; it++) {
             // forward: interchanges and multipliers
             Df prev = Qd[k];
-            for (int i = 0; i < n - 1; i++) {
-                const size_t at = i * ld + k;
-                Df next = Qd[at + ld];
-                if (bf.sw[at]) { const Df tmp = prev; prev = next; next = tmp; }
-                Qd[at] = prev;
-                prev = df_add(next, df_neg(df_mul(ML[at], prev)));
+            for (int i0 = 0; i0 < n - 1; i0 += IB) {
+                Df nx[IB], ml[IB];
+                unsigned char sw[IB];
+#pragma unroll
+                for (int u = 0; u < IB; u++)
+                    if (i0 + u < n - 1) {
+                        const size_t at = (size_t)(i0 + u) * ld + k;
+                        nx[u] = Qd[at + ld];
+                        ml[u] = ML[at];
+                        sw[u] = bf.sw[at];
+                    }
+#pragma unroll
+                for (int u = 0; u < IB; u++)
+                    if (i0 + u < n - 1) {
+                        Df next = nx[u];
+                        if (sw[u]) { const Df tmp = prev; prev = next; next = tmp; }
+                        Qd[(size_t)(i0 + u) * ld + k] = prev;
+                        prev = df_add(next, df_neg(df_mul(ml[u], prev)));
+                    }
             }
             // back substitution
             Df y2 = zero, y1 = df_div(prev, U0[(size_t)(n - 1) * ld + k]);
             Qd[(size_t)(n - 1) * ld + k] = y1;
-            for (int i = n - 2; i >= 0; i--) {
-                const size_t at = i * ld + k;
-                const Df r = df_add(Qd[at], df_neg(df_add(df_mul(U1[at], y1), df_mul(U2[at], y2))));
-                const Df y = df_div(r, U0[at]);
-                Qd[at] = y;
-                y2 = y1;
-                y1 = y;
+            for (int i0 = n - 2; i0 >= 0; i0 -= IB) {
+                Df q[IB], u0[IB], u1[IB], u2[IB];
+#pragma unroll
+                for (int u = 0; u < IB; u++)
+                    if (i0 - u >= 0) {
+                        const size_t at = (size_t)(i0 - u) * ld + k;
+                        q[u] = Qd[at];
+                        u0[u] = U0[at];
+                        u1[u] = U1[at];
+                        u2[u] = U2[at];
+                    }
+#pragma unroll
+                for (int u = 0; u < IB; u++)
+                    if (i0 - u >= 0) {
+                        const Df r = df_add(q[u], df_neg(df_add(df_mul(u1[u], y1), df_mul(u2[u], y2))));
+                        const Df y = df_div(r, u0[u]);
+                        Qd[(size_t)(i0 - u) * ld + k] = y;
+                        y2 = y1;
+                        y1 = y;
+                    }
             }
             // orthogonalise against the earlier vectors of the cluster
             for (int p = k0; p < k; p++) {
                 Df d = zero;
                 for (int i = 0; i < n; i++) d = df_add(d, df_mul(Qd[i * ld + p], Qd[i * ld + k]));
                 const Df md = df_neg(d);
-                for (int i = 0; i < n; i++) Qd[i * ld + k] = df_add(Qd[i * ld + k], df_mul(md, Qd[i * ld + p]));
+                for (int i0 = 0; i0 < n; i0 += IB) {
+                    Df a[IB], b[IB];
+#pragma unroll
+                    for (int u = 0; u < IB; u++)
+                        if (i0 + u < n) {
+                            a[u] = Qd[(size_t)(i0 + u) * ld + k];
+                            b[u] = Qd[(size_t)(i0 + u) * ld + p];
+                        }
+#pragma unroll
+                    for (int u = 0; u < IB; u++)
+                        if (i0 + u < n) Qd[(size_t)(i0 + u) * ld + k] = df_add(a[u], df_mul(md, b[u]));
+                }
             }
             nrm = 0.f;
             for (int i = 0; i < n; i++) { const float y = Qd[i * ld + k].h; nrm = fmaf(y, y, nrm); }
             nrm = sqrtf(nrm);
             if (!(nrm > 0.f) || !isfinite(nrm)) break;
-            const Df s = {1.0f / nrm, 0.f};
-            for (int i = 0; i < n; i++) Qd[i * ld + k] = df_mul(Qd[i * ld + k], s);
+            scale({1.0f / nrm, 0.f});
             if (conv) done = true;
             else if (nrm >= grow) conv = true;
         }
