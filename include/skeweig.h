@@ -310,6 +310,13 @@ long long skew_launch_count(void);
 #define SKEW_KERNEL_KINDS 12
 int skew_kernel_timing(int enable);
 int skew_kernel_timing_read(int kind, double* ms, double* flops, long long* launches);
+/* Timeline of the same records: for the first min(cap, records) records in
+ * launch order, kinds[i] (SKEW_KERNEL_*), and the start and end of record i in
+ * milliseconds after the start of record 0 (events of different streams, as
+ * the side stream of the band reduction, interleave).  Any output pointer may
+ * be NULL.  Waits for the recorded events.  Returns the number of records
+ * written, -1 for cap < 0, or SKEW_ERR_CUDA. */
+int skew_kernel_timeline(int cap, int* kinds, double* start_ms, double* end_ms);
 
 /* ------------------------------------------------------------------------
  * Stage entry points (the steps of Algorithm 1 one at a time; used by the

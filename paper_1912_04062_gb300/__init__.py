@@ -62,6 +62,7 @@ SIGNATURES = {
     "skew_refine_slices": (_i, [_p, _p, _i]),
     "skew_kernel_timing": (_i, [_i]),
     "skew_kernel_timing_read": (_i, [_i, _p, _p, _p]),
+    "skew_kernel_timeline": (_i, [_i, _p, _p, _p]),
     "skew_gemm_bf16x3_ws": (_sz, [_i, _i, _i]),
     "skew_gemm_f64acc_ws": (_sz, [_i, _i, _i]),
     "skew_gemm_f64acc": (_i, [_i, _i, _i, _d, _p, ctypes.c_longlong, ctypes.c_longlong, _p, ctypes.c_longlong,
@@ -359,6 +360,18 @@ def kernel_timing_read(kind: int):
     _check(code, "skew_kernel_timing_read")
     return ms.value, fl.value, k.value
 
+
+
+def kernel_timeline(cap=16384):
+    """[(kind name, start ms, end ms)] of the timing records in launch order,
+    relative to the first record's start (skew_kernel_timeline)."""
+    kinds = (ctypes.c_int * cap)()
+    t0 = (ctypes.c_double * cap)()
+    t1 = (ctypes.c_double * cap)()
+    cnt = lib().skew_kernel_timeline(cap, kinds, t0, t1)
+    _check(min(cnt, 0), "skew_kernel_timeline")
+    return [(KERNEL_KINDS[kinds[i]] if 0 <= kinds[i] < len(KERNEL_KINDS) else "?", t0[i], t1[i])
+            for i in range(cnt)]
 
 def _batch_arrays(As, nevs, vectors):
     torch = _torch()

@@ -283,6 +283,8 @@ inline int grid_for(size_t total) {
 
 // Split-K ranges of the K = m products of the tensor-core form
 constexpr int KS_MAX = 256;
+// Panels per lazy trailing update in the tensor-core form
+constexpr int LAZY_G = 4;
 
 struct ReduceWs {
     double *V, *Pm, *Y, *X2, *Y2, *G, *C1, *C2, *tau, *part, *rowbuf;
@@ -290,6 +292,12 @@ struct ReduceWs {
     // tensor-core form: Z = [-C2/2; T], split-K partials of the main and side
     // streams, digit slices of V, P, [V P] and Z
     double *Z, *part_m, *part_s, *part_p;
+    // lazy trailing update: [V_q W_q] and [W_q -V_q] of the group's panels
+    // (global row index, 2b columns per panel), Y2acc^T V, and a workspace for
+    // the small products of the group (the group's A22 split holds the other)
+    double *X2acc, *Y2acc, *Cc;
+    void* gws2;
+    size_t gsz2;
     void *oz_v, *oz_p, *oz_vp, *oz_z;
     size_t oz_vb, oz_vpb, oz_zb;
 };
@@ -329,6 +337,12 @@ ReduceWs carve_reduce(Carve& cv, int n, int b, bool f64acc) {
         w.oz_vp = cv.take<char>(w.oz_vpb);
         w.oz_zb = ozaki_operand_ws(b, 2 * b);
         w.oz_z = cv.take<char>(w.oz_zb);
+        w.X2acc = cv.take<double>((size_t)n * 2 * b * LAZY_G);
+        w.Y2acc = cv.take<double>((size_t)n * 2 * b * LAZY_G);
+        w.Cc = cv.take<double>((size_t)2 * b * LAZY_G * b);
+        const size_t g1 = ozaki_gemm_ws(n, b, 2 * b * LAZY_G), g2 = ozaki_operand_ws(2 * b * LAZY_G, n);
+        w.gsz2 = g1 > g2 ? g1 : g2;
+        w.gws2 = cv.take<char>(w.gsz2);
     }
     return w;
 }
@@ -384,75 +398,152 @@ struct SideStream {
     }
 };
 
-// T factor and a3-a4 of one panel with every contraction on the tensor cores
-// (FP64-accurate digit-slice products; GB300 runs FP64 at ~1 TFLOP/s):
+// Cooperative panel QR of panel p (a2): Householder vectors below the
+// diagonal block in place, taus into w.tau.
+int launch_panel_qr(cudaStream_t st, int n, int b, int p, double* W, int ldw, ReduceWs& w, int* d_status,
+                    int max_smem, int sms) {
+    const int o = (p + 1) * b, m = n - o;
+    double* panel = W + (size_t)p * b * ldw + o;
+    int rpc = qr_rows_per_cta(m, b, sms);
+    const int G = (m + rpc - 1) / rpc;
+    const size_t smem = qr_smem_bytes(rpc, b);
+    if ((int)smem > max_smem - 1024 || G > 1024) return SKEW_ERR_UNSUPPORTED;
+    cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_qr_kernel, QR_THREADS, smem);
+    if (occ * sms < G) return SKEW_ERR_LAUNCH;
+    if (cudaMemsetAsync(w.bar, 0, sizeof(unsigned), st) != cudaSuccess) return SKEW_ERR_CUDA;
+    int ldp = ldw, nbv = b, mm = m;
+    double* taup = w.tau;
+    void* args[] = {&mm, &nbv, &panel, &ldp, &taup, &w.part, &w.rowbuf, &w.bar, &d_status, &rpc};
+    KtScope kt(st, KT_PANEL_QR);
+    if (cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st) != cudaSuccess)
+        return SKEW_ERR_LAUNCH;
+    count_launch();
+    return 0;
+}
+
+// Band reduction in the tensor-core form with a lazy trailing update.  The
+// panels go in groups of LAZY_G.  At a group's start the trailing matrix
+// A22_0 = W[o0:, o0:] is up to date and is split into digit slices once;
+// panel p = p0 + i of the group then works with
+//   A22_p = A22_0[d:, d:] + sum_{q < p in the group} X2_q Y2_q^T  (d = o_p - o0),
+// X2_q = [V_q W_q], Y2_q = [W_q -V_q] (Eq. 10): its SYMM reads a view of the
+// group split and adds X2 (Y2^T V) (Eq. 8 with the pending terms), its own
+// columns get the pending terms just before its QR, and at the group's end one
+// rank-2 b LAZY_G product brings the rest of the trailing matrix up to date
+// (K = 512 instead of four K = 128 updates: the product's FP64 epilogue and
+// the split pass, the costs of a short-K update, run once per group).
+// Per panel, as tensor-core products (FP64-accurate digit slices):
 //   side stream: G = V^T V (split K), T from G (Eq. 7);
-//   main stream: P = A22 V (Eq. 8, `slices` digit slices), Q = P^T V (split
-//   K), then C1 = V^T P T = Q^T T, C2 = T^T C1 and W = P T - V C2 / 2 =
-//   [V P] [-C2/2; T] (Eq. 9) as one product with K = 2b.
-int panel_update_f64acc(cudaStream_t st, SideStream& side, int n, int m, int b, const double* panel, int ldw,
-                        const double* A22, const double* taup, double* Tp, ReduceWs& w, void* gws, size_t gsz,
-                        int* status, int slices) {
-    {
-        KtScope kt(st, KT_GEMM_F64);
-        panel_v_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, panel, ldw, w.V, n);
-        count_launch();
-    }
-    // rows of these operands are the b columns of V (of P), K = m
-    OzOperand ov{}, op{}, oa{}, ovp{}, oz{};
-    int rc = ozaki_split(st, b, m, w.V, n, 1, 1.0, 0, w.oz_v, w.oz_vb, &ov);
-    if (rc) return rc;
-    const int nch = (m + 63) / 64;
-    int ks = (nch + 1) / 2;  // two 64-wide K chunks per CTA at least
-    if (ks > device_sms()) ks = device_sms();
-    if (ks > KS_MAX) ks = KS_MAX;
-    if (ks < 1) ks = 1;
-    if (cudaEventRecord(side.ev_v, st) != cudaSuccess || cudaStreamWaitEvent(side.s, side.ev_v, 0) != cudaSuccess)
-        return SKEW_ERR_CUDA;
-    rc = ozaki_gemm_pre(side.s, ov, ov, 1.0, 0.0, w.G, b, status, 8, 0, ks, w.part_s);
-    if (rc) return rc;
-    {
-        KtScope kt(side.s, KT_GEMM_F64);
-        tfactor_kernel<<<1, TF_THREADS, tfactor_smem(b), side.s>>>(b, taup, w.G, Tp);
-        count_launch();
-    }
-    if (cudaEventRecord(side.ev_t, side.s) != cudaSuccess) return SKEW_ERR_CUDA;
-    // a3: P = A22 V with A22 the skew matrix of its strict lower triangle
-    rc = ozaki_split(st, m, m, A22, 0, ldw, 1.0, 1, gws, gsz, &oa);
-    if (rc) return rc;
-    {
-        // N = b is a single column of tiles: split K so that the m / 128 row
-        // tiles fill the SMs
-        const int tiles = (m + 127) / 128;
-        int kp = device_sms() / tiles;
-        if (kp * tiles > KS_MAX) kp = KS_MAX / tiles;
-        if (kp > (nch + 1) / 2) kp = (nch + 1) / 2;
-        if (kp < 1) kp = 1;
-        rc = ozaki_gemm_pre(st, oa, ov, 1.0, 0.0, w.Pm, n, status, slices, 0, kp, w.part_p);
+//   main stream: P = A22_p V, Q = P^T V (split K), C1 = V^T P T = Q^T T,
+//   C2 = T^T C1 and W = P T - V C2 / 2 = [V P] [-C2/2; T] (Eq. 9) with K = 2b.
+int band_reduce_f64acc(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac, ReduceWs& w, void* gws,
+                       size_t gsz, int* status, int slices, SideStream& side, int max_smem, int sms) {
+    const int P = num_panels(n, b);
+    const long long ldx = n;
+    for (int p0 = 0; p0 < P; p0 += LAZY_G) {
+        const int p1 = (p0 + LAZY_G < P) ? p0 + LAZY_G : P;
+        const int o0 = (p0 + 1) * b, m0 = n - o0;
+        OzOperand oa{};  // the group's A22 split (skew, rows and K = m0)
+        int rc = ozaki_split(st, m0, m0, W + (size_t)o0 * ldw + o0, 0, ldw, 1.0, 1, gws, gsz, &oa);
         if (rc) return rc;
-    }
-    // Q = P^T V
-    rc = ozaki_split(st, b, m, w.Pm, n, 1, 1.0, 0, w.oz_p, w.oz_vb, &op);
-    if (rc) return rc;
-    rc = ozaki_gemm_pre(st, op, ov, 1.0, 0.0, w.C1, b, status, 8, 0, ks, w.part_m);
-    if (rc) return rc;
-    // a4: W = [V P] Z, Z = [-C2/2; T]
-    if (cudaStreamWaitEvent(st, side.ev_t, 0) != cudaSuccess) return SKEW_ERR_CUDA;
-    {
-        KtScope kt(st, KT_GEMM_F64);
-        wz_kernel<<<b, b, 0, st>>>(b, w.C1, Tp, w.Z);
-        count_launch();
-    }
-    rc = ozaki_split(st, m, 2 * b, w.V, 1, n, 1.0, 0, w.oz_vp, w.oz_vpb, &ovp);
-    if (rc) return rc;
-    rc = ozaki_split(st, b, 2 * b, w.Z, 2 * b, 1, 1.0, 0, w.oz_z, w.oz_zb, &oz);
-    if (rc) return rc;
-    rc = ozaki_gemm_pre(st, ovp, oz, 1.0, 0.0, w.Y, n, status, 8);
-    if (rc) return rc;
-    {
-        KtScope kt(st, KT_GEMM_F64);
-        concat_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, w.V, w.Y, n, w.X2, w.Y2);
-        count_launch();
+        for (int p = p0; p < p1; p++) {
+            const int i = p - p0, o = (p + 1) * b, m = n - o, d = o - o0, pb = p * b;
+            double* panel = W + (size_t)pb * ldw + o;
+            double* Tp = Tfac + (size_t)p * b * b;
+            if (i > 0) {
+                // the pending terms of the panel's own columns (rows from its diagonal block)
+                rc = ozaki_gemm(st, n - pb, b, 2 * b * i, 1.0, w.X2acc + pb, 1, ldx, 1.0, w.Y2acc + pb, 1, ldx, 1.0,
+                                1.0, W + (size_t)pb * ldw + pb, ldw, w.gws2, w.gsz2, status, 0, 8, 0);
+                if (rc) return rc;
+            }
+            rc = launch_panel_qr(st, n, b, p, W, ldw, w, status, max_smem, sms);
+            if (rc) return rc;
+            {
+                KtScope kt(st, KT_GEMM_F64);
+                panel_v_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, panel, ldw, w.V, n);
+                count_launch();
+            }
+            // rows of these operands are the b columns of V (of P), K = m
+            OzOperand ov{}, op{}, ovp{}, oz{};
+            rc = ozaki_split(st, b, m, w.V, n, 1, 1.0, 0, w.oz_v, w.oz_vb, &ov);
+            if (rc) return rc;
+            const int nch = (m + 63) / 64;
+            int ks = (nch + 1) / 2;  // two 64-wide K chunks per CTA at least
+            if (ks > sms) ks = sms;
+            if (ks > KS_MAX) ks = KS_MAX;
+            if (ks < 1) ks = 1;
+            if (cudaEventRecord(side.ev_v, st) != cudaSuccess || cudaStreamWaitEvent(side.s, side.ev_v, 0) != cudaSuccess)
+                return SKEW_ERR_CUDA;
+            rc = ozaki_gemm_pre(side.s, ov, ov, 1.0, 0.0, w.G, b, status, 8, 0, ks, w.part_s);
+            if (rc) return rc;
+            {
+                KtScope kt(side.s, KT_GEMM_F64);
+                tfactor_kernel<<<1, TF_THREADS, tfactor_smem(b), side.s>>>(b, w.tau, w.G, Tp);
+                count_launch();
+            }
+            if (cudaEventRecord(side.ev_t, side.s) != cudaSuccess) return SKEW_ERR_CUDA;
+            // a3: P = A22_0[d:, d:] V (a view of the group split; N = b is a
+            // single column of tiles, so K is split to fill the SMs) ...
+            {
+                const int tiles = (m + 127) / 128;
+                int kp = sms / tiles;
+                if (kp * tiles > KS_MAX) kp = KS_MAX / tiles;
+                if (kp > (nch + 1) / 2) kp = (nch + 1) / 2;
+                if (kp < 1) kp = 1;
+                rc = ozaki_gemm_pre(st, oz_view(oa, d, d, m, m), ov, 1.0, 0.0, w.Pm, n, status, slices, 0, kp,
+                                    w.part_p);
+                if (rc) return rc;
+            }
+            if (i > 0) {
+                // ... + X2 (Y2^T V) over the group's earlier panels
+                const int kq = 2 * b * i;
+                OzOperand oy{};
+                rc = ozaki_split(st, kq, m, w.Y2acc + o, ldx, 1, 1.0, 0, w.gws2, w.gsz2, &oy);
+                if (rc) return rc;
+                rc = ozaki_gemm_pre(st, oy, ov, 1.0, 0.0, w.Cc, 2 * b * LAZY_G, status, 8, 0, ks, w.part_m);
+                if (rc) return rc;
+                rc = ozaki_gemm(st, m, b, kq, 1.0, w.X2acc + o, 1, ldx, 1.0, w.Cc, 2 * b * LAZY_G, 1, 1.0, 1.0, w.Pm, n,
+                                w.gws2, w.gsz2, status, 0, 8, 0);
+                if (rc) return rc;
+            }
+            // Q = P^T V
+            rc = ozaki_split(st, b, m, w.Pm, n, 1, 1.0, 0, w.oz_p, w.oz_vb, &op);
+            if (rc) return rc;
+            rc = ozaki_gemm_pre(st, op, ov, 1.0, 0.0, w.C1, b, status, 8, 0, ks, w.part_m);
+            if (rc) return rc;
+            // a4: W = [V P] Z, Z = [-C2/2; T]
+            if (cudaStreamWaitEvent(st, side.ev_t, 0) != cudaSuccess) return SKEW_ERR_CUDA;
+            {
+                KtScope kt(st, KT_GEMM_F64);
+                wz_kernel<<<b, b, 0, st>>>(b, w.C1, Tp, w.Z);
+                count_launch();
+            }
+            rc = ozaki_split(st, m, 2 * b, w.V, 1, n, 1.0, 0, w.oz_vp, w.oz_vpb, &ovp);
+            if (rc) return rc;
+            rc = ozaki_split(st, b, 2 * b, w.Z, 2 * b, 1, 1.0, 0, w.oz_z, w.oz_zb, &oz);
+            if (rc) return rc;
+            rc = ozaki_gemm_pre(st, ovp, oz, 1.0, 0.0, w.Y, n, status, 8);
+            if (rc) return rc;
+            {
+                // X2_p, Y2_p into the group's accumulators (rows o.. of columns 2 b i ..)
+                KtScope kt(st, KT_GEMM_F64);
+                concat_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, w.V, w.Y, n,
+                                                                      w.X2acc + (size_t)2 * b * i * ldx + o,
+                                                                      w.Y2acc + (size_t)2 * b * i * ldx + o);
+                count_launch();
+            }
+        }
+        // group end: the trailing matrix from the last panel's o (the next
+        // group's first panel columns included) takes all the group's terms,
+        // tiles on or below the diagonal (the upper triangle of W is never read)
+        const int oL = p1 * b, mL = n - oL;
+        if (mL > 0) {
+            const int rc2 = ozaki_gemm(st, mL, mL, 2 * b * (p1 - p0), 1.0, w.X2acc + oL, 1, ldx, 1.0, w.Y2acc + oL, 1,
+                                       ldx, 1.0, 1.0, W + (size_t)oL * ldw + oL, ldw, gws, gsz, status, 0, slices, 1);
+            if (rc2) return rc2;
+        }
     }
     return 0;
 }
@@ -484,6 +575,12 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         if (rc) return rc;
     }
 
+    if (planes == REDUCE_F64ACC) {
+        const int rc = band_reduce_f64acc(st, n, W, ldw, b, Tfac, w, gws, gsz, d_status, slices, side, max_smem, sms);
+        if (rc) return rc;
+        return cudaGetLastError() == cudaSuccess ? 0 : SKEW_ERR_CUDA;
+    }
+
     for (int p = 0; p < P; p++) {
         const int o = (p + 1) * b, m = n - o;
         double* panel = W + (size_t)p * b * ldw + o;
@@ -491,30 +588,8 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
         double* Tp = Tfac + (size_t)p * b * b;
         double* taup = w.tau;
         // ---- a2: panel QR (cooperative)
-        int rpc = qr_rows_per_cta(m, b, sms);
-        int G = (m + rpc - 1) / rpc;
-        size_t smem = qr_smem_bytes(rpc, b);
-        if ((int)smem > max_smem - 1024 || G > 1024) return SKEW_ERR_UNSUPPORTED;
-        cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_qr_kernel, QR_THREADS, smem);
-        if (occ * sms < G) return SKEW_ERR_LAUNCH;
-        if (cudaMemsetAsync(w.bar, 0, sizeof(unsigned), st) != cudaSuccess) return SKEW_ERR_CUDA;
-        int ldp = ldw, nbv = b, mm = m;
-        void* args[] = {&mm, &nbv, &panel, &ldp, &taup, &w.part, &w.rowbuf, &w.bar, &d_status, &rpc};
+        if (const int rc0 = launch_panel_qr(st, n, b, p, W, ldw, w, d_status, max_smem, sms)) return rc0;
         {
-            KtScope kt(st, KT_PANEL_QR);
-            if (cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st) !=
-                cudaSuccess)
-                return SKEW_ERR_LAUNCH;
-        }
-        count_launch();
-        if (planes == REDUCE_F64ACC) {
-            // ---- T factor, a3, a4 as tensor-core products
-            const int rc = panel_update_f64acc(st, side, n, m, b, panel, ldw, A22, taup, Tp, w, gws, gsz, d_status,
-                                               slices);
-            if (rc) return rc;
-        } else {
         // ---- T factor (Eq. 7)
         {
             KtScope kt(st, KT_GEMM_F64);
@@ -546,12 +621,7 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
             count_launch();
         }
         }
-        if (planes == REDUCE_F64ACC) {
-            // tiles on or below the diagonal (the upper triangle of W is never read)
-            int rc = ozaki_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 1.0, w.Y2, 1, n, 1.0, 1.0, A22, ldw, gws, gsz,
-                                d_status, 0, slices, 1);
-            if (rc) return rc;
-        } else if (mixed) {
+        if (mixed) {
             int rc = split_gemm(st, m, m, 2 * b, 1.0, w.X2, 1, n, 0, w.Y2, 1, n, 1.0, A22, ldw, 1, gws, gsz, d_status,
                                 planes);
             if (rc) return rc;

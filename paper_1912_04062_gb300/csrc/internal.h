@@ -109,7 +109,14 @@ struct OzOperand {
     int* e;
     int rows, K;
     long long Rp, Kp;
+    // a view into a larger split (oz_view): row r of the view is row roff + r
+    // of the split (d and e already advanced by roff), element k of a row is
+    // element koff + k (koff a multiple of 64)
+    int roff, koff;
 };
+// Rows r0 .. r0+rows-1 and elements k0 .. k0+K-1 of a split operand, without
+// copying (k0 a multiple of 64; rows and K within the operand).
+OzOperand oz_view(const OzOperand& o, int r0, int k0, int rows, int K);
 size_t ozaki_operand_ws(int rows, int K);
 int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long rs, long long ks, double sgn, int skew,
                 void* ws, size_t ws_bytes, OzOperand* op);

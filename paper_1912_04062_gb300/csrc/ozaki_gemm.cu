@@ -78,6 +78,7 @@ struct OzParams {
     int lower;               // skip tiles above the diagonal
     int kz;                  // split K: chunks per split (blockIdx.y), 0 = whole K
     double* part;            // split K: partial tiles, [split][N][M]
+    int akoff, bkoff;        // K offsets of views into larger splits (elements)
 };
 
 struct OzSmem {
@@ -257,13 +258,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     mbar_arrive_expect_tx(&bfull[q], (uint32_t)S * OzSmem::B_ATOM);
                     for (int j = 0; j < S; j++)
                         tma_load_2d(sB + q * OzSmem::B_SET + j * OzSmem::B_ATOM, &tmB, &bfull[q],
-                                    (c_off + c) * OKA, j * p.Np + n0);
+                                    p.bkoff + (c_off + c) * OKA, j * p.Np + n0);
                     bi++;
                     for (int i = 0; i < S; i++) {
                         const int st = ai % NA;
                         if (!(ok = mbar_wait(&aempty[st], ((uint32_t)(ai / NA) & 1u) ^ 1u, p.status))) break;
                         mbar_arrive_expect_tx(&afull[st], OzSmem::A_ATOM);
-                        tma_load_2d(sA + st * OzSmem::A_ATOM, &tmA, &afull[st], (c_off + c) * OKA, i * p.Mp + m0);
+                        tma_load_2d(sA + st * OzSmem::A_ATOM, &tmA, &afull[st], p.akoff + (c_off + c) * OKA,
+                                    i * p.Mp + m0);
                         ai++;
                     }
                 }
@@ -718,7 +720,20 @@ int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long r
     op->K = K;
     op->Rp = Rp;
     op->Kp = Kp;
+    op->roff = 0;
+    op->koff = 0;
     return 0;
+}
+
+OzOperand oz_view(const OzOperand& o, int r0, int k0, int rows, int K) {
+    OzOperand v = o;
+    v.d = o.d + (size_t)r0 * (size_t)o.Kp;
+    v.e = o.e + r0;
+    v.rows = rows;
+    v.K = K;
+    v.roff = o.roff + r0;
+    v.koff = o.koff + k0;
+    return v;
 }
 
 // C = alpha * A B^T + beta C from split operands (A: M x K, B: N x K).
@@ -726,16 +741,23 @@ int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, doub
                    long long ldc, int* status, int slices, int lower, int ksplit, double* part) {
     const int M = A.rows, N = B.rows, K = A.K;
     if (M <= 0 || N <= 0) return 0;
-    if (B.K != K || B.Kp != A.Kp || slices < 1 || slices > SL) return SKEW_ERR_UNSUPPORTED;
+    if (B.K != K || slices < 1 || slices > SL) return SKEW_ERR_UNSUPPORTED;
+    const long long kpad = rup(K, OKA);  // K chunks read from each operand
+    if (A.koff % OKA || B.koff % OKA || A.koff + kpad > A.Kp || B.koff + kpad > B.Kp) return SKEW_ERR_UNSUPPORTED;
+    // a view's map starts at its first row and ends where the split ends:
+    // rows past it (last plane, last tile) read as zeros instead of memory
+    // beyond the buffer
     CUtensorMap ta, tb;
-    if (!make_tmap_bf16(&ta, A.d, (uint64_t)A.Kp, (uint64_t)(SL * A.Rp), (uint64_t)A.Kp, OM))
+    if (!make_tmap_bf16(&ta, A.d, (uint64_t)A.Kp, (uint64_t)(SL * A.Rp - A.roff), (uint64_t)A.Kp, OM))
         return SKEW_ERR_UNSUPPORTED;
-    if (!make_tmap_bf16(&tb, B.d, (uint64_t)B.Kp, (uint64_t)(SL * B.Rp), (uint64_t)B.Kp, ON))
+    if (!make_tmap_bf16(&tb, B.d, (uint64_t)B.Kp, (uint64_t)(SL * B.Rp - B.roff), (uint64_t)B.Kp, ON))
         return SKEW_ERR_UNSUPPORTED;
     OzParams p{};
     p.M = M;
     p.N = N;
-    p.nchunks = (int)(A.Kp / OKA);
+    p.nchunks = (int)(kpad / OKA);
+    p.akoff = A.koff;
+    p.bkoff = B.koff;
     p.Mp = (int)A.Rp;
     p.Np = (int)B.Rp;
     p.ea = A.e;

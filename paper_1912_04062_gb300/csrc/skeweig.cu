@@ -694,6 +694,25 @@ int skew_kernel_timing_read(int kind, double* ms, double* flops, long long* laun
     return 0;
 }
 
+int skew_kernel_timeline(int cap, int* kinds, double* start_ms, double* end_ms) {
+    if (cap < 0) return -1;
+    KTimer& t = ktimer();
+    if (t.used == 0) return 0;
+    const int cnt = (int)(t.used < (size_t)cap ? t.used : (size_t)cap);
+    const cudaEvent_t t0 = t.recs[0].a;
+    for (int i = 0; i < cnt; i++) {
+        const KtRec& r = t.recs[i];
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return SKEW_ERR_CUDA;
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, t0, r.a) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (cudaEventElapsedTime(&b, t0, r.b) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (kinds) kinds[i] = r.kind;
+        if (start_ms) start_ms[i] = a;
+        if (end_ms) end_ms[i] = b;
+    }
+    return cnt;
+}
+
 int skew_refine_stats(double* emax, int* nclose, int cap) {
     const RefineInfo& r = last_refine_info();
     for (int i = 0; i < cap && i < 8; i++) {

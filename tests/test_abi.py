@@ -101,6 +101,9 @@ def test_kernel_timing_switch_is_host_side(sk):
     assert (ms, fl, k) == (0.0, 0.0, 0)
     assert L.skew_kernel_timing_read(12, None, None, None) == -1
     assert L.skew_kernel_timing_read(-1, None, None, None) == -1
+    # no records yet: an empty timeline; a negative capacity is an argument error
+    assert sk.kernel_timeline() == []
+    assert L.skew_kernel_timeline(-1, None, None, None) == -1
     assert L.skew_kernel_timing(0) == 0
 
 
