@@ -311,9 +311,11 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
     double emax = 0.0, rn2 = 0.0;
     unsigned int close = 0;
     unsigned long long wloc = 0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mm;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % m), j = (int)(e / m);
+    // element (i, j), e = j m + i: threads along i, the grid's y along j (no
+    // 64-bit division per element)
+    for (int j = blockIdx.y; j < m; j += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const long long e = (long long)j * m + i;
         const double li = lt[i], lj = lt[j];
         int ia[KC], ja[KC];
         cplx ic[KC], jc[KC];
@@ -383,9 +385,9 @@ __global__ void refine_u_kernel(int m, const int* __restrict__ cid, const double
                                 const double* __restrict__ Et, double* __restrict__ U, RefineScalars* sc) {
     const long long mm = (long long)m * m, ldu = 2LL * m;
     double umax = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mm;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(e % m), j = (int)(e / m);
+    for (int j = blockIdx.y; j < m; j += gridDim.y)
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+        const long long e = (long long)j * m + q;
         cplx E11, E21;
         const int c = cid[q];
         if (c < 0) {
@@ -444,10 +446,17 @@ __global__ void lmax_kernel(int m, const double* __restrict__ lt, double* __rest
     }
 }
 
-inline int gridn(long long total) {
-    long long g = (total + 255) / 256;
-    return (int)(g > 8192 ? 8192 : (g < 1 ? 1 : g));
+// 2-D grid for the m x m element kernels: x over i (256 threads a block), y
+// over j, at most 8192 blocks
+inline dim3 grid2(int m) {
+    const int gx = (m + 255) / 256;
+    int gy = 8192 / (gx > 0 ? gx : 1);
+    if (gy > m) gy = m;
+    if (gy < 1) gy = 1;
+    if (gy > 65535) gy = 65535;
+    return dim3((unsigned)(gx > 0 ? gx : 1), (unsigned)gy);
 }
+
 
 struct RefineWs {
     double *S, *Wg, *AM, *T, *U, *lt, *Vc;
@@ -554,9 +563,9 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
             refine_close_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt, tau, rho, w.close);
             refine_rr_kernel<<<m, 32, 0, st>>>(m, n, w.Wg, w.T, w.close, w.lt, w.cid, w.Vc, w.nbig);
             // E~ lives in the AM buffer (free once T is formed)
-            refine_etilde_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, n, w.Wg, w.T, w.lt, w.cid, w.Vc, tau,
+            refine_etilde_kernel<<<grid2(m), 256, 0, st>>>(m, n, w.Wg, w.T, w.lt, w.cid, w.Vc, tau,
                                                                           w.AM, w.sc);
-            refine_u_kernel<<<gridn((long long)m * m), 256, 0, st>>>(m, w.cid, w.Vc, w.AM, w.U, w.sc);
+            refine_u_kernel<<<grid2(m), 256, 0, st>>>(m, w.cid, w.Vc, w.AM, w.U, w.sc);
         }
         count_launch(4);
         RefineScalars h{};
