@@ -373,8 +373,9 @@ def run_ours(args, ws, rank, local):
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": (f"BSE-shaped skew n={n} nev={nev}, " +
                                        ("mixed form (reduction contractions and Q_band as FP64-accurate BF16 "
-                                        "digit-slice tensor-core products, Q_trd FP32, FP64 panels/chase/"
-                                        "tridiagonal) + FP64 refinement" if mixed else
+                                        "digit-slice tensor-core products, Q_trd FP32, FP64 panel QR and chase, "
+                                        "FP32 + double-float bisection and inverse iteration) + FP64 refinement"
+                                        if mixed else
                                         "FP64 form (all steps FP64)")),
                           "n": n, "nev": nev, "band": 64, "form": args.form,
                           "l2": "inputs larger than L2 (A = %.1f GB)" % (8 * n * n / 1e9),

@@ -481,7 +481,7 @@ int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, c
             // G = V^T V on the tensor cores (split K: a few output tiles, K = m)
             int ks = ((m + 63) / 64 + 1) / 2;
             if (ks > QB_KS) ks = QB_KS;
-            rc = ozaki_gemm_pre(st, ov, ov, 1.0, 0.0, G, gb, status, 8, 0, ks, q.part);
+            rc = ozaki_gemm_pre(st, ov, ov, 1.0, 0.0, G, gb, status, 8, 0, ks, q.part, (size_t)QB_KS * gb * gb);
             if (rc) return rc;
             KtScope kt(st, KT_GEMM_F64);
             for (int j = 1; j < g; j++) {

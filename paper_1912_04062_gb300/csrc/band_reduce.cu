@@ -292,6 +292,7 @@ struct ReduceWs {
     // tensor-core form: Z = [-C2/2; T], split-K partials of the main and side
     // streams, digit slices of V, P, [V P] and Z
     double *Z, *part_m, *part_s, *part_p;
+    size_t part_m_n, part_s_n, part_p_n;  // capacities (doubles)
     // lazy trailing update: [V_q W_q] and [W_q -V_q] of the group's panels
     // (global row index, 2b columns per panel), Y2acc^T V, and a workspace for
     // the small products of the group (the group's A22 split holds the other)
@@ -327,9 +328,14 @@ ReduceWs carve_reduce(Carve& cv, int n, int b, bool f64acc) {
     w.bar = cv.take<unsigned>(64);
     if (f64acc) {
         w.Z = cv.take<double>((size_t)2 * b * b);
-        w.part_m = cv.take<double>((size_t)KS_MAX * b * b);
-        w.part_s = cv.take<double>((size_t)KS_MAX * b * b);
-        w.part_p = cv.take<double>((size_t)KS_MAX * 128 * b);  // SYMM partials: splits x tiles <= KS_MAX
+        // split-K partials: main stream (P^T V, b x b, and Y2^T V, up to
+        // 2 b LAZY_G x b), side stream (V^T V), SYMM (splits x tiles <= KS_MAX)
+        w.part_m_n = (size_t)KS_MAX * 2 * b * LAZY_G * b;
+        w.part_s_n = (size_t)KS_MAX * b * b;
+        w.part_p_n = (size_t)KS_MAX * 128 * b;
+        w.part_m = cv.take<double>(w.part_m_n);
+        w.part_s = cv.take<double>(w.part_s_n);
+        w.part_p = cv.take<double>(w.part_p_n);
         w.oz_vb = ozaki_operand_ws(b, n);
         w.oz_v = cv.take<char>(w.oz_vb);
         w.oz_p = cv.take<char>(w.oz_vb);
@@ -476,7 +482,7 @@ int band_reduce_f64acc(cudaStream_t st, int n, double* W, int ldw, int b, double
             if (ks < 1) ks = 1;
             if (cudaEventRecord(side.ev_v, st) != cudaSuccess || cudaStreamWaitEvent(side.s, side.ev_v, 0) != cudaSuccess)
                 return SKEW_ERR_CUDA;
-            rc = ozaki_gemm_pre(side.s, ov, ov, 1.0, 0.0, w.G, b, status, 8, 0, ks, w.part_s);
+            rc = ozaki_gemm_pre(side.s, ov, ov, 1.0, 0.0, w.G, b, status, 8, 0, ks, w.part_s, w.part_s_n);
             if (rc) return rc;
             {
                 KtScope kt(side.s, KT_GEMM_F64);
@@ -493,7 +499,7 @@ int band_reduce_f64acc(cudaStream_t st, int n, double* W, int ldw, int b, double
                 if (kp > (nch + 1) / 2) kp = (nch + 1) / 2;
                 if (kp < 1) kp = 1;
                 rc = ozaki_gemm_pre(st, oz_view(oa, d, d, m, m), ov, 1.0, 0.0, w.Pm, n, status, slices, 0, kp,
-                                    w.part_p);
+                                    w.part_p, w.part_p_n);
                 if (rc) return rc;
             }
             if (i > 0) {
@@ -502,7 +508,8 @@ int band_reduce_f64acc(cudaStream_t st, int n, double* W, int ldw, int b, double
                 OzOperand oy{};
                 rc = ozaki_split(st, kq, m, w.Y2acc + o, ldx, 1, 1.0, 0, w.gws2, w.gsz2, &oy);
                 if (rc) return rc;
-                rc = ozaki_gemm_pre(st, oy, ov, 1.0, 0.0, w.Cc, 2 * b * LAZY_G, status, 8, 0, ks, w.part_m);
+                rc = ozaki_gemm_pre(st, oy, ov, 1.0, 0.0, w.Cc, 2 * b * LAZY_G, status, 8, 0, ks, w.part_m,
+                                    w.part_m_n);
                 if (rc) return rc;
                 rc = ozaki_gemm(st, m, b, kq, 1.0, w.X2acc + o, 1, ldx, 1.0, w.Cc, 2 * b * LAZY_G, 1, 1.0, 1.0, w.Pm, n,
                                 w.gws2, w.gsz2, status, 0, 8, 0);
@@ -511,7 +518,7 @@ int band_reduce_f64acc(cudaStream_t st, int n, double* W, int ldw, int b, double
             // Q = P^T V
             rc = ozaki_split(st, b, m, w.Pm, n, 1, 1.0, 0, w.oz_p, w.oz_vb, &op);
             if (rc) return rc;
-            rc = ozaki_gemm_pre(st, op, ov, 1.0, 0.0, w.C1, b, status, 8, 0, ks, w.part_m);
+            rc = ozaki_gemm_pre(st, op, ov, 1.0, 0.0, w.C1, b, status, 8, 0, ks, w.part_m, w.part_m_n);
             if (rc) return rc;
             // a4: W = [V P] Z, Z = [-C2/2; T]
             if (cudaStreamWaitEvent(st, side.ev_t, 0) != cudaSuccess) return SKEW_ERR_CUDA;

@@ -120,11 +120,13 @@ OzOperand oz_view(const OzOperand& o, int r0, int k0, int rows, int K);
 size_t ozaki_operand_ws(int rows, int K);
 int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long rs, long long ks, double sgn, int skew,
                 void* ws, size_t ws_bytes, OzOperand* op);
-// ksplit > 1: K is cut into that many ranges (one CTA per tile and range) and
-// the partial tiles, ksplit x N x M doubles in part, are summed in order.
+// ksplit > 1: K is cut into up to that many ranges (one CTA per tile and
+// range) and the partial tiles, ranges x N x M doubles in part (capacity
+// part_elems doubles: fewer ranges are taken when they would not fit), are
+// summed in order.
 int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, double alpha, double beta, double* C,
                    long long ldc, int* status, int slices = 8, int lower = 0, int ksplit = 1,
-                   double* part = nullptr);
+                   double* part = nullptr, size_t part_elems = 0);
 // a_skew: A is the skew matrix of the strict lower triangle stored column-major
 // with leading dimension a_ks (a_rs unused).  slices (1..8): digit slices kept,
 // accuracy about 2^-7 slices relative to |a_r|max |b_c|max per term.  lower:

@@ -738,7 +738,7 @@ OzOperand oz_view(const OzOperand& o, int r0, int k0, int rows, int K) {
 
 // C = alpha * A B^T + beta C from split operands (A: M x K, B: N x K).
 int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, double alpha, double beta, double* C,
-                   long long ldc, int* status, int slices, int lower, int ksplit, double* part) {
+                   long long ldc, int* status, int slices, int lower, int ksplit, double* part, size_t part_elems) {
     const int M = A.rows, N = B.rows, K = A.K;
     if (M <= 0 || N <= 0) return 0;
     if (B.K != K || slices < 1 || slices > SL) return SKEW_ERR_UNSUPPORTED;
@@ -772,6 +772,12 @@ int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, doub
     p.mt = (M + OM - 1) / OM;
     p.nt = (N + ON - 1) / ON;
     int nz = 1;
+    if (ksplit > 1) {
+        // no more ranges than the partial buffer holds
+        const size_t per = (size_t)M * (size_t)N;
+        const long long fit = per ? (long long)(part_elems / per) : 0;
+        if (ksplit > fit) ksplit = (int)fit;
+    }
     if (ksplit > 1) {
         if (!part) return SKEW_ERR_WORKSPACE;
         p.kz = (p.nchunks + ksplit - 1) / ksplit;

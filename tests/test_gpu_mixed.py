@@ -278,3 +278,27 @@ def test_refined_mode_without_complete_basis(n, nev, kind):
     assert np.max(np.abs(lam - lam_o)) <= 1e-12 * float(lam_o.max())
     m = oracle.scaled_metrics(A, lam, X, Y)
     assert m["resid"] <= 50 and m["orth"] <= 50, m
+
+
+# --- the refined mode with a complete basis (the metric's configuration) ---------
+@pytest.mark.parametrize("n,kind", [(1100, "bse"), (770, "prescribed")])
+def test_refined_mode_complete_basis_is_accurate_and_deterministic(n, kind):
+    # n = 1100: 17 panels, so the band reduction's lazy trailing update runs
+    # over full and partial groups of panels; two solves in one process must
+    # agree bit for bit (a race or an uninitialised workspace read would not)
+    import inputs
+    import oracle
+    import paper_1912_04062_gb300 as sk
+    A = inputs.bse(n, seed=4) if kind == "bse" else inputs.prescribed(n, seed=4)[0]
+    nev = n // 2
+    info, lam, X, Y = _mixed_solve(A, nev, sk.SKEW_MODE_MIXED_REFINED)
+    assert info == 0
+    it, emax, nclose = sk.refine_stats()
+    assert 1 <= it <= 6 and emax[-1] < 1e-8, (it, emax)
+    lam_o, *_ = oracle.skew_eig(A, nev, vectors=False)
+    assert np.max(np.abs(lam - lam_o)) <= 1e-12 * float(lam_o.max())
+    m = oracle.scaled_metrics(A, lam, X, Y)
+    assert m["resid"] <= 50 and m["orth"] <= 50, (m, it, emax)
+    info2, lam2, X2, Y2 = _mixed_solve(A, nev, sk.SKEW_MODE_MIXED_REFINED)
+    assert info2 == 0
+    assert np.array_equal(lam, lam2) and np.array_equal(X, X2) and np.array_equal(Y, Y2)
