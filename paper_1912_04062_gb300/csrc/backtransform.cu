@@ -264,6 +264,8 @@ qtrd_smem_kernel(int n, const double* __restrict__ Vtrd, const double* __restric
 
 struct QbandWs {
     double *V, *Y, *Y2;
+    double* part;  // split-K partials of V^T Z
+    size_t part_n;
 };
 
 QbandWs carve_qband(Carve& cv, int n, int b, int k) {
@@ -271,6 +273,8 @@ QbandWs carve_qband(Carve& cv, int n, int b, int k) {
     w.V = cv.take<double>((size_t)n * b);
     w.Y = cv.take<double>((size_t)b * k);
     w.Y2 = cv.take<double>((size_t)b * k);
+    w.part_n = (size_t)b * (4 * (size_t)k > 1024 ? 4 * (size_t)k : 1024);
+    w.part = cv.take<double>(w.part_n);
     return w;
 }
 
@@ -342,7 +346,8 @@ int apply_qband(cudaStream_t st, int n, int b, const double* W, int ldw, const d
         double* Zo = Z + o;
         KtScope kt(st, KT_GEMM_F64);
         if (panel_v(st, n, b, p, W, ldw, w.V, n) != cudaSuccess) return SKEW_ERR_CUDA;
-        if (gemm(st, true, false, b, k, m, 1.0, w.V, n, Zo, ldz, 0.0, w.Y, b) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (gemm(st, true, false, b, k, m, 1.0, w.V, n, Zo, ldz, 0.0, w.Y, b, 0, w.part, w.part_n) != cudaSuccess)
+            return SKEW_ERR_CUDA;
         if (gemm(st, false, false, b, k, b, 1.0, Tp, b, w.Y, b, 0.0, w.Y2, b) != cudaSuccess) return SKEW_ERR_CUDA;
         if (gemm(st, false, false, m, k, b, -1.0, w.V, n, w.Y2, b, 1.0, Zo, ldz) != cudaSuccess) return SKEW_ERR_CUDA;
     }
@@ -382,6 +387,7 @@ struct QbMixedWs {
     // FP64-accurate form: split-K partials, digit slices of V (rows = its
     // columns), of V by rows and of T_g
     double* part;
+    size_t part_n;
     void *oz_v, *oz_a, *oz_t;
     size_t oz_vb, oz_ab, oz_tb;
 };
@@ -399,7 +405,8 @@ static QbMixedWs carve_qband_mixed(Carve& cv, int n, int b, int k, int planes) {
     q.gsz = qband_gemm_ws(n, b, k, planes);
     q.gws = cv.take<char>(q.gsz);
     if (acc) {
-        q.part = cv.take<double>((size_t)QB_KS * w * w);
+        q.part_n = (size_t)QB_KS * w * w;
+        q.part = cv.take<double>(q.part_n);
         q.oz_vb = ozaki_operand_ws((int)w, n);
         q.oz_v = cv.take<char>(q.oz_vb);
         q.oz_ab = ozaki_operand_ws(n, (int)w);
@@ -489,11 +496,11 @@ int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, c
                 const double* Tj = Tfac + (size_t)(p0 + j) * b * b;
                 // tmp = (V_1..j-1^T V_j) T_j, then T[0:jb, jb:jb+b] = -T[0:jb, 0:jb] tmp
                 // (split K over 16-deep slices: these products have few output tiles)
-                if (gemm(st, false, false, jb, b, b, 1.0, G + (size_t)jb * gb, gb, Tj, b, 0.0, tmp, gb, b / 16) !=
-                    cudaSuccess)
+                if (gemm(st, false, false, jb, b, b, 1.0, G + (size_t)jb * gb, gb, Tj, b, 0.0, tmp, gb, b / 16,
+                         q.part, q.part_n) != cudaSuccess)
                     return SKEW_ERR_CUDA;
                 if (gemm(st, false, false, jb, b, jb, -1.0, Tg, gb, tmp, gb, 0.0, Tg + (size_t)jb * gb, gb,
-                         jb / 16) != cudaSuccess)
+                         jb / 16, q.part, q.part_n) != cudaSuccess)
                     return SKEW_ERR_CUDA;
             }
         }

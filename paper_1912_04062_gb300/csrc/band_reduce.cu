@@ -326,16 +326,18 @@ ReduceWs carve_reduce(Carve& cv, int n, int b, bool f64acc) {
     w.part = cv.take<double>((size_t)2 * 1024 * (b + 1));
     w.rowbuf = cv.take<double>((size_t)2 * b);
     w.bar = cv.take<unsigned>(64);
+    // split-K partials of the SYMM (splits x tiles <= KS_MAX); in the FP64
+    // form also of V^T V and V^T Y
+    w.part_p_n = (size_t)KS_MAX * 128 * b;
+    w.part_p = cv.take<double>(w.part_p_n);
     if (f64acc) {
         w.Z = cv.take<double>((size_t)2 * b * b);
         // split-K partials: main stream (P^T V, b x b, and Y2^T V, up to
-        // 2 b LAZY_G x b), side stream (V^T V), SYMM (splits x tiles <= KS_MAX)
+        // 2 b LAZY_G x b), side stream (V^T V)
         w.part_m_n = (size_t)KS_MAX * 2 * b * LAZY_G * b;
         w.part_s_n = (size_t)KS_MAX * b * b;
-        w.part_p_n = (size_t)KS_MAX * 128 * b;
         w.part_m = cv.take<double>(w.part_m_n);
         w.part_s = cv.take<double>(w.part_s_n);
-        w.part_p = cv.take<double>(w.part_p_n);
         w.oz_vb = ozaki_operand_ws(b, n);
         w.oz_v = cv.take<char>(w.oz_vb);
         w.oz_p = cv.take<char>(w.oz_vb);
@@ -602,7 +604,9 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
             KtScope kt(st, KT_GEMM_F64);
             panel_v_kernel<<<grid_for((size_t)m * b), 256, 0, st>>>(m, b, panel, ldw, w.V, n);
             count_launch();
-            if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.V, n, 0.0, w.G, b) != cudaSuccess) return SKEW_ERR_CUDA;
+            if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.V, n, 0.0, w.G, b, 0, w.part_p, w.part_p_n) !=
+                cudaSuccess)
+                return SKEW_ERR_CUDA;
             tfactor_kernel<<<1, TF_THREADS, tfactor_smem(b), st>>>(b, taup, w.G, Tp);
             count_launch();
         }
@@ -613,13 +617,16 @@ int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
             if (rc) return rc;
         } else {
             KtScope kt(st, KT_GEMM_F64);
-            if (skew_symm(st, m, b, A22, ldw, w.V, n, w.Pm, n) != cudaSuccess) return SKEW_ERR_CUDA;
+            if (skew_symm(st, m, b, A22, ldw, w.V, n, w.Pm, n, 0, w.part_p, w.part_p_n) != cudaSuccess)
+                return SKEW_ERR_CUDA;
         }
         {
             // ---- a4: Y = P T; C = T^T (V^T Y); W = Y - V C / 2
             KtScope kt(st, KT_GEMM_F64);
             if (gemm(st, false, false, m, b, b, 1.0, w.Pm, n, Tp, b, 0.0, w.Y, n) != cudaSuccess) return SKEW_ERR_CUDA;
-            if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.Y, n, 0.0, w.C1, b) != cudaSuccess) return SKEW_ERR_CUDA;
+            if (gemm(st, true, false, b, b, m, 1.0, w.V, n, w.Y, n, 0.0, w.C1, b, 0, w.part_p, w.part_p_n) !=
+                cudaSuccess)
+                return SKEW_ERR_CUDA;
             if (gemm(st, true, false, b, b, b, 1.0, Tp, b, w.C1, b, 0.0, w.C2, b) != cudaSuccess) return SKEW_ERR_CUDA;
             if (gemm(st, false, false, m, b, b, -0.5, w.V, n, w.C2, b, 1.0, w.Y, n) != cudaSuccess)
                 return SKEW_ERR_CUDA;

@@ -7,7 +7,9 @@
 // busy while touching HBM/L2 only once per tile and K slice.
 //
 // Three shapes are served:
-//   * plain C = alpha op(A) op(B) + beta C (split-K with FP64 atomics);
+//   * plain C = alpha op(A) op(B) + beta C (split K: partial products in a
+//     caller buffer summed in a fixed order, so results do not depend on the
+//     order in which CTAs finish; FP64 atomics when no buffer is given);
 //   * skew-symmetric A given by its strict lower triangle (Sec. 2.3.2: "symmetry
 //     is assumed ... sign changes"): element (i, k) of S is W[i,k] below the
 //     diagonal, -W[k,i] above it, 0 on it -- the A V product of Eqs. 8-10;
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(int M, int N, int K, double al
                                                   const double* __restrict__ A, int lda,
                                                   const double* __restrict__ B, int ldb,
                                                   double beta, double* __restrict__ C, int ldc,
-                                                  int kchunk) {
+                                                  int kchunk, double* __restrict__ part) {
     const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(K, kbeg + kchunk);
@@ -153,6 +155,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(int M, int N, int K, double al
     if (kbeg < kend) tile_mma<AM, TB>(acc, A, lda, B, ldb, M, N, K, i0, j0, kbeg, kend);
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const bool split = gridDim.z > 1;
+    // K range z's partial product, M x N with leading dimension M
+    double* Pz = part ? part + (size_t)blockIdx.z * M * N : nullptr;
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         int gj = j0 + ty + 16 * c;
@@ -163,7 +167,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(int M, int N, int K, double al
             if (gi >= M) continue;
             double* p = C + (size_t)gj * ldc + gi;
             double v = alpha * acc[r][c];
-            if (split) atomicAdd(p, v);
+            if (Pz) Pz[(size_t)gj * M + gi] = v;
+            else if (split) atomicAdd(p, v);
             else *p = (beta == 0.0) ? v : fma(beta, *p, v);
         }
     }
@@ -208,11 +213,41 @@ __global__ void scale_kernel(int M, int N, double beta, double* C, int ldc) {
     }
 }
 
+// C = beta C + sum of the s partial products, added in order z = 0, 1, ...
+__global__ void splitk_sum_kernel(int M, int N, int s, const double* __restrict__ part, double beta,
+                                  double* __restrict__ C, int ldc) {
+    const size_t MN = (size_t)M * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < MN; e += (size_t)gridDim.x * blockDim.x) {
+        double v = part[e];
+        for (int z = 1; z < s; z++) v += part[(size_t)z * MN + e];
+        const size_t j = e / M, i = e % M;
+        double* p = C + j * ldc + i;
+        *p = (beta == 0.0) ? v : fma(beta, *p, v);
+    }
+}
+
+unsigned sum_blocks(size_t mn) {
+    const size_t b = (mn + 255) / 256;
+    return (unsigned)(b < 4096 ? b : 4096);
+}
+
 int pick_split(int tiles, int K, int requested) {
     if (requested > 0) return requested;
     const int target = 2 * device_sms();
     int s = 1;
     while (tiles * s < target && K / (s * 2) >= 64) s *= 2;
+    return s;
+}
+
+// K ranges: the requested count, else enough CTAs for two waves while each
+// range keeps at least 64 of K; at most part_elems / (M N) when the partial
+// products go to a buffer
+int pick_split_cap(int tiles, int K, int requested, size_t mn, const double* part, size_t part_elems) {
+    int s = pick_split(tiles, K, requested);
+    if (part && s > 1) {
+        const size_t cap = part_elems / mn;
+        if ((size_t)s > cap) s = cap > 1 ? (int)cap : 1;
+    }
     return s;
 }
 
@@ -231,7 +266,7 @@ int device_sms() {
 
 cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
                  const double* A, int lda, const double* B, int ldb, double beta, double* C,
-                 int ldc, int splitk) {
+                 int ldc, int splitk, double* part, size_t part_elems) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (K <= 0) {
         scale_kernel<<<min(1024, (M * N + 255) / 256 + 1), 256, 0, st>>>(M, N, beta, C, ldc);
@@ -239,40 +274,55 @@ cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double 
         return cudaGetLastError();
     }
     const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-    int s = pick_split(tm * tn, K, splitk);
+    const size_t mn = (size_t)M * N;
+    int s = pick_split_cap(tm * tn, K, splitk, mn, part, part_elems);
     int kchunk = ((K + s - 1) / s + BK - 1) / BK * BK;
     s = (K + kchunk - 1) / kchunk;
-    if (s > 1) {
+    const bool ordered = part && s > 1;
+    if (s > 1 && !ordered) {
         scale_kernel<<<min(4096, (M * N + 255) / 256 + 1), 256, 0, st>>>(M, N, beta, C, ldc);
         count_launch();
     }
+    double* pz = ordered ? part : nullptr;
     dim3 grid(tm, tn, s);
     if (!ta && !tb)
-        gemm_kernel<A_PLAIN_N, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk);
+        gemm_kernel<A_PLAIN_N, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, pz);
     else if (!ta && tb)
-        gemm_kernel<A_PLAIN_N, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk);
+        gemm_kernel<A_PLAIN_N, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, pz);
     else if (ta && !tb)
-        gemm_kernel<A_PLAIN_T, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk);
+        gemm_kernel<A_PLAIN_T, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, pz);
     else
-        gemm_kernel<A_PLAIN_T, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk);
+        gemm_kernel<A_PLAIN_T, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, pz);
     count_launch();
+    if (ordered) {
+        splitk_sum_kernel<<<sum_blocks(mn), 256, 0, st>>>(M, N, s, part, beta, C, ldc);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 cudaError_t skew_symm(cudaStream_t st, int m, int nb, const double* W, int ldw, const double* V,
-                      int ldv, double* P, int ldp, int splitk) {
+                      int ldv, double* P, int ldp, int splitk, double* part, size_t part_elems) {
     if (m <= 0 || nb <= 0) return cudaSuccess;
     const int tm = (m + BM - 1) / BM, tn = (nb + BN - 1) / BN;
-    int s = pick_split(tm * tn, m, splitk);
+    const size_t mn = (size_t)m * nb;
+    int s = pick_split_cap(tm * tn, m, splitk, mn, part, part_elems);
     int kchunk = ((m + s - 1) / s + BK - 1) / BK * BK;
     s = (m + kchunk - 1) / kchunk;
-    scale_kernel<<<min(4096, (m * nb + 255) / 256 + 1), 256, 0, st>>>(m, nb, 0.0, P, ldp);
-    count_launch();
+    const bool ordered = part && s > 1;
+    if (s > 1 && !ordered) {
+        // the K ranges accumulate into P with atomics
+        scale_kernel<<<min(4096, (m * nb + 255) / 256 + 1), 256, 0, st>>>(m, nb, 0.0, P, ldp);
+        count_launch();
+    }
     dim3 grid(tm, tn, s);
-    // force the atomic path even when s == 1 (P was zeroed above)
-    if (s == 1) grid.z = 1;
-    gemm_kernel<A_SKEW, false><<<grid, NT, 0, st>>>(m, nb, m, 1.0, W, ldw, V, ldv, 0.0, P, ldp, kchunk);
+    gemm_kernel<A_SKEW, false><<<grid, NT, 0, st>>>(m, nb, m, 1.0, W, ldw, V, ldv, 0.0, P, ldp, kchunk,
+                                                    ordered ? part : nullptr);
     count_launch();
+    if (ordered) {
+        splitk_sum_kernel<<<sum_blocks(mn), 256, 0, st>>>(m, nb, s, part, 0.0, P, ldp);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 

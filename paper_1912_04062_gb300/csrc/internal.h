@@ -13,17 +13,22 @@ namespace sk {
 // ---- gemm_f64.cu -----------------------------------------------------------
 // C[M x N] = alpha * op(A) op(B) + beta * C, column-major FP64.
 // op(A) = A (ta = false) or A^T (ta = true); likewise op(B).
-// splitk > 1 splits the K range over CTAs and accumulates with atomics
-// (beta is applied first by a separate scaling launch).
+// splitk > 1 (or 0: chosen from the tile count) splits the K range over
+// CTAs.  With part (part_elems doubles, at least M N for a split to happen)
+// each range writes its partial product there and a second launch adds them
+// in range order, so the result is the same on every run; the split count is
+// limited to part_elems / (M N).  Without part the ranges accumulate into C
+// with FP64 atomics (beta applied first), whose order varies.
 cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
                  const double* A, int lda, const double* B, int ldb, double beta,
-                 double* C, int ldc, int splitk = 0);
+                 double* C, int ldc, int splitk = 0, double* part = nullptr, size_t part_elems = 0);
 
 // P[m x nb] = S V where S = L - L^T is the skew matrix whose strict lower
-// triangle is stored in W (ld ldw); V is m x nb (ld ldv).  Split-K with
-// atomics; P is overwritten.
+// triangle is stored in W (ld ldw); V is m x nb (ld ldv).  Split K as for
+// gemm (ordered with part, atomics without); P is overwritten.
 cudaError_t skew_symm(cudaStream_t st, int m, int nb, const double* W, int ldw,
-                      const double* V, int ldv, double* P, int ldp, int splitk = 0);
+                      const double* V, int ldv, double* P, int ldp, int splitk = 0,
+                      double* part = nullptr, size_t part_elems = 0);
 
 // Lower 64 x 64 tiles (diagonal tiles complete) of C[m x m] +=
 // X[m x k] Y[m x k]^T.  Used for the skew rank-2k update with

@@ -302,3 +302,19 @@ def test_refined_mode_complete_basis_is_accurate_and_deterministic(n, kind):
     info2, lam2, X2, Y2 = _mixed_solve(A, nev, sk.SKEW_MODE_MIXED_REFINED)
     assert info2 == 0
     assert np.array_equal(lam, lam2) and np.array_equal(X, X2) and np.array_equal(Y, Y2)
+
+
+@pytest.mark.parametrize("n", [1100, 2050])
+def test_fp64_form_is_deterministic(n):
+    # the FP64 form splits the K range of its small products (V^T V, V^T Y,
+    # the SYMM, V^T Z) over CTAs; the partial products are added in a fixed
+    # order, so two solves agree bit for bit
+    import inputs
+    import paper_1912_04062_gb300 as sk
+    A = inputs.bse(n, seed=6)
+    nev = n // 2
+    info, lam, X, Y = _mixed_solve(A, nev, sk.SKEW_MODE_FP64)
+    assert info == 0
+    info2, lam2, X2, Y2 = _mixed_solve(A, nev, sk.SKEW_MODE_FP64)
+    assert info2 == 0
+    assert np.array_equal(lam, lam2) and np.array_equal(X, X2) and np.array_equal(Y, Y2)
