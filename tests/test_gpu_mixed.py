@@ -318,3 +318,46 @@ def test_fp64_form_is_deterministic(n):
     info2, lam2, X2, Y2 = _mixed_solve(A, nev, sk.SKEW_MODE_FP64)
     assert info2 == 0
     assert np.array_equal(lam, lam2) and np.array_equal(X, X2) and np.array_equal(Y, Y2)
+
+
+# --- one refinement step through skew_refine against the oracle's step ---------
+def test_one_refinement_step_matches_oracle():
+    # n = 256 with eigenvalues 1, 1.05, ..., 7.35 and the oracle's eigenvectors
+    # moved by 1e-6 per column: every pair takes the first-order formula on
+    # both sides (no cluster, no R / 2 off the diagonal), so one step of the
+    # GPU refinement must equal the oracle's Ogita-Aishima step up to rounding.
+    # Bound: S and R carry at most n eps (lambda_max, 1) absolute error on
+    # either side, so each E_ij differs by at most 4 n eps lambda_max / gap, and
+    # each new entry, a sum of n terms |Zh_ik| |E_kj|, by n max|Z| times that.
+    import torch
+    import inputs
+    import oracle
+    from oracle.refine import refine_step
+    import paper_1912_04062_gb300 as sk
+    n, gap = 256, 0.05
+    m = n // 2
+    eps64 = np.finfo(np.float64).eps
+    l = 1.0 + gap * np.arange(m)
+    A = inputs.from_spectrum(l, n, np.random.default_rng(7))
+    lam, X, Y, _ = oracle.skew_eig(A, m)
+    rng = np.random.default_rng(3)
+    s = 1e-6 / np.sqrt(2 * n)
+    Xp = X + s * rng.standard_normal((n, m))
+    Yp = Y + s * rng.standard_normal((n, m))
+    lt, Xo, Yo, info = refine_step(A, Xp, Yp)
+    assert info["close"] == 0
+    dA = sk.fortran(torch.from_numpy(np.asfortranarray(A)).cuda())
+    dl = torch.from_numpy(lam.copy()).cuda()
+    dX = sk.fortran(torch.from_numpy(np.asfortranarray(Xp)).cuda())
+    dY = sk.fortran(torch.from_numpy(np.asfortranarray(Yp)).cuda())
+    sk.refine(dA, dl, dX, dY, iters=1)
+    torch.cuda.synchronize()
+    it, emax, nclose = sk.refine_stats()
+    assert it == 1 and nclose == [0], (it, nclose)
+    lam_g, Xg, Yg = dl.cpu().numpy(), dX.cpu().numpy(), dY.cpu().numpy()
+    assert np.max(np.abs(lam_g - lt)) <= 4 * n * eps64 * l.max()
+    zmax = max(np.abs(Xp).max(), np.abs(Yp).max())
+    tol = n * zmax * 4 * n * eps64 * l.max() / gap
+    d_ora = np.maximum(np.abs(Xo - Xp), np.abs(Yo - Yp)).max()
+    assert tol <= 0.02 * d_ora           # the comparison resolves the correction itself
+    assert np.max(np.abs(Xg - Xo)) <= tol and np.max(np.abs(Yg - Yo)) <= tol
