@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances (the benchmark spec): eigenvalue error <= 1e-12 ||A||_2, scaled
+Tolerances of the accuracy target: eigenvalue error <= 1e-12 ||A||_2, scaled
 residual ||AZ - Z Lambda||_F / (n eps ||A||_F) <= 50, orthogonality
 ||Z^H Z - I||_F / (n eps) <= 50.  Eigenvectors are unique only up to a unit
 complex factor (and only for simple eigenvalues), so they are compared by
