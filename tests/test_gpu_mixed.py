@@ -221,7 +221,7 @@ def test_gemm_f64acc_under_cancellation():
     assert e_b6 > 2.0 ** 12 * e_oz
 
 
-# --- mixed + refined: the benchmark spec's tolerances against the FP64 oracle ---------
+# --- mixed + refined: the accuracy target's tolerances against the FP64 oracle --
 @pytest.mark.parametrize("n,kind,planes", [(128, "random", 3), (512, "prescribed", 3), (1024, "bse", 3),
                                           (512, "prescribed", 2)])
 def test_mixed_refined_meets_fp64_tolerances(n, kind, planes):
