@@ -48,7 +48,7 @@ def from_spectrum(l: np.ndarray, n: int, rng: np.random.Generator) -> np.ndarray
 
 
 def prescribed(n: int, seed: int = 1, lo: float = 0.1, hi: float = 10.0):
-    """Config-1 style matrix; returns (A, l) with l the prescribed values."""
+    """Prescribed spectrum, l ~ U(lo, hi); returns (A, l) with l the prescribed values."""
     rng = np.random.default_rng(seed)
     l = rng.uniform(lo, hi, size=n // 2)
     return from_spectrum(l, n, rng), l
@@ -73,7 +73,8 @@ def bse(n: int, seed: int = 2) -> np.ndarray:
 
 
 def clustered(n: int, seed: int = 4, frac: float = 0.05, group: int = 16, width: float = 1e-10):
-    """Config-4 style matrix; returns (A, l)."""
+    """Clustered small spectrum (log-uniform in [1e-6, 1], a fraction `frac` in
+    groups of `group` within `width`); returns (A, l)."""
     rng = np.random.default_rng(seed)
     m = n // 2
     l = np.exp(rng.uniform(np.log(1e-6), np.log(1.0), size=m))
@@ -97,7 +98,8 @@ def batch_sizes(count: int = 2000, seed: int = 5, lo: int = 32, hi: int = 1024) 
 
 
 def batch(count: int = 2000, seed: int = 5, sizes=None):
-    """Config-5 style batch: list of (A_i, l_i), one child seed per matrix."""
+    """Batch of prescribed-spectrum matrices of uneven order (l ~ U(0.1, 10)):
+    list of (A_i, l_i), one child seed per matrix."""
     if sizes is None:
         sizes = batch_sizes(count, seed)
     children = np.random.SeedSequence(seed).spawn(len(sizes))

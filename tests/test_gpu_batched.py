@@ -52,7 +52,7 @@ def test_batch_of_mixed_orders():
         _check(A, nev, l, zr, zi)
 
 
-def test_config5_style_sample():
+def test_uneven_batch_sample():
     # orders drawn like the batched workload (log-uniform in [32, 1024]),
     # prescribed spectra l ~ U(0.1, 10); a bounded sample the oracle checks fast
     import inputs

@@ -165,7 +165,7 @@ def test_solve_random_skew(n):
     _check_solve(A, n // 2)
 
 
-def test_solve_prescribed_n512_config1():
+def test_solve_prescribed_n512():
     A, l = inputs.prescribed(512, seed=1)
     _check_solve(A, 256, lam_ref=np.sort(l)[::-1])
 
