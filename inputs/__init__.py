@@ -54,6 +54,19 @@ def prescribed(n: int, seed: int = 1, lo: float = 0.1, hi: float = 10.0):
     return from_spectrum(l, n, rng), l
 
 
+def bse_from_blocks(Ad: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Skew K = L^T J L from real symmetric blocks Ad, B (h x h) with
+    M = [[Ad, B], [B, Ad]] positive definite, M = L L^T, J = [[0, I], [-I, 0]],
+    then K = (K - K^T)/2."""
+    h = Ad.shape[0]
+    M = np.block([[Ad, B], [B, Ad]])
+    L = np.linalg.cholesky(M)
+    J = np.block([[np.zeros((h, h)), np.eye(h)], [-np.eye(h), np.zeros((h, h))]])
+    K = L.T @ J @ L
+    K = 0.5 * (K - K.T)
+    return np.asfortranarray(K)
+
+
 def bse(n: int, seed: int = 2) -> np.ndarray:
     """BSE-shaped skew matrix K = L^T J L of order n (n even)."""
     if n % 2:
@@ -64,12 +77,7 @@ def bse(n: int, seed: int = 2) -> np.ndarray:
     Ad = np.diag(rng.uniform(2.0, 20.0, size=h)) + 0.05 * 0.5 * (G + G.T) / np.sqrt(h)
     G2 = rng.standard_normal((h, h))
     B = 0.02 * 0.5 * (G2 + G2.T) / np.sqrt(h)
-    M = np.block([[Ad, B], [B, Ad]])
-    L = np.linalg.cholesky(M)
-    J = np.block([[np.zeros((h, h)), np.eye(h)], [-np.eye(h), np.zeros((h, h))]])
-    K = L.T @ J @ L
-    K = 0.5 * (K - K.T)
-    return np.asfortranarray(K)
+    return bse_from_blocks(Ad, B)
 
 
 def clustered(n: int, seed: int = 4, frac: float = 0.05, group: int = 16, width: float = 1e-10):
