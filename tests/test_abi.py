@@ -129,3 +129,20 @@ def test_batched_argument_checks_are_host_side(sk):
     assert 0 < small < mid < big
     # orders above the batched kernels' limit take the two-step solve's workspace
     assert big >= sk.workspace_size(2000, 1000)
+
+
+def test_binding_constants_match_the_header(sk):
+    # every SKEW_* integer constant of the header has the same value in the
+    # Python binding (status codes, modes, fault hooks, kernel kinds)
+    text = open(HEADER).read()
+    consts = dict((k, int(v)) for k, v in re.findall(r"^#define\s+(SKEW_\w+)\s+(-?\d+)\b", text, flags=re.M))
+    # enumerators of the mode enum
+    consts.update((k, int(v)) for k, v in re.findall(r"^\s+(SKEW_MODE_\w+)\s*=\s*(\d+)", text, flags=re.M))
+    assert len(consts) >= 30 and "SKEW_MODE_MIXED_REFINED" in consts
+    missing = [k for k in consts if not hasattr(sk, k) and k not in ("SKEW_NSTAGES", "SKEW_KERNEL_KINDS")]
+    assert not missing, missing
+    for k, v in consts.items():
+        if hasattr(sk, k):
+            assert getattr(sk, k) == v, (k, getattr(sk, k), v)
+    assert len(sk.STAGES) == consts["SKEW_NSTAGES"]
+    assert len(sk.KERNEL_KINDS) == consts["SKEW_KERNEL_KINDS"]
