@@ -146,3 +146,20 @@ def test_binding_constants_match_the_header(sk):
             assert getattr(sk, k) == v, (k, getattr(sk, k), v)
     assert len(sk.STAGES) == consts["SKEW_NSTAGES"]
     assert len(sk.KERNEL_KINDS) == consts["SKEW_KERNEL_KINDS"]
+
+
+def test_opts_struct_layout_matches_the_header(sk):
+    # the ctypes mirror of skew_opts has the header's fields, in order, and
+    # skew_opts_default fills it as documented (FP64 mode, b = 64 or 0)
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct \{(.*?)\} skew_opts;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"int\s+(\w+)(\[\d+\])?\s*;", body)
+    names = [f[0] for f in fields]
+    assert names == [f[0] for f in sk.skew_opts._fields_]
+    for (name, arr), (pname, ptype) in zip(fields, sk.skew_opts._fields_):
+        n = int(arr[1:-1]) if arr else 1
+        assert ctypes.sizeof(ptype) == n * ctypes.sizeof(ctypes.c_int), name
+    o = sk.skew_opts()
+    sk.lib().skew_opts_default(ctypes.byref(o))
+    assert o.mode == sk.SKEW_MODE_FP64 and o.band in (0, 64) and o.fault == 0
