@@ -163,3 +163,41 @@ def test_opts_struct_layout_matches_the_header(sk):
     o = sk.skew_opts()
     sk.lib().skew_opts_default(ctypes.byref(o))
     assert o.mode == sk.SKEW_MODE_FP64 and o.band in (0, 64) and o.fault == 0
+
+
+def _prototypes():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"^\s*#.*$", "", text, flags=re.M)
+    out = {}
+    for m in re.finditer(r"([\w\s\*]+?)\b(skew_\w+)\s*\(([^)]*)\)\s*;", text):
+        ret, name, params = m.group(1).strip(), m.group(2), m.group(3).strip()
+        plist = [] if params in ("", "void") else [q.strip() for q in params.split(",")]
+        out[name] = (ret, plist)
+    return out
+
+
+def _ctype_of(decl):
+    d = " ".join(decl.replace("*", " * ").split())
+    if "*" in d:
+        return "ptr"
+    base = re.sub(r"\b(const|unsigned)\b", "", d).split()
+    t = " ".join(base[:-1]) if len(base) > 1 else base[0]
+    return {"int": "int", "size_t": "size_t", "double": "double", "long long": "longlong", "void": "void",
+            "long": "longlong"}[t]
+
+
+def test_binding_signatures_match_the_prototypes(sk):
+    # argument count and kind (pointer / int / size_t / double / long long) of
+    # every ctypes declaration equal the header's prototype
+    kind = {ctypes.c_void_p: "ptr", ctypes.c_char_p: "ptr", ctypes.c_int: "int", ctypes.c_size_t: "size_t",
+            ctypes.c_double: "double", ctypes.c_longlong: "longlong", None: "void"}
+    protos = _prototypes()
+    assert set(protos) == set(sk.SIGNATURES)
+    for name, (ret, params) in protos.items():
+        restype, argtypes = sk.SIGNATURES[name]
+        assert len(argtypes) == len(params), (name, len(argtypes), len(params))
+        for a, decl in zip(argtypes, params):
+            assert kind[a] == _ctype_of(decl), (name, decl, a)
+        want_ret = "ptr" if "*" in ret else _ctype_of(ret + " x")
+        assert kind[restype] == want_ret, (name, ret, restype)
