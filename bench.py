@@ -319,7 +319,7 @@ def run_ours(args, ws, rank, local):
     F = {"band_reduce": 4.0 / 3.0 * n ** 3, "qtrd": 4.0 * n * n * nev, "qband": 4.0 * n * n * nev,
          "chase": 12.0 * 64 * 64 * (n * n / (2 * 64))}
     kern = {"band_reduce": "panel_qr_kernel + skew SYMM/rank-2k gemm_kernel/lower_tiles_kernel",
-            "qtrd": "qtrd_kernel (1 launch per solve)", "qband": "gemm_kernel (3 per panel)",
+            "qtrd": "qtrd_smem_kernel<double> (1 launch per solve)", "qband": "gemm_kernel (3 per panel)",
             "chase": "chase_kernel (1 launch per solve)"}
     kt_ms = {k: v[0] / args.steps for k, v in ktime.items()}
     single = {k: stage_ms[k] for k in ("qtrd", "chase")}
