@@ -102,11 +102,14 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, x):
+    """Largest x over the ranks (the timed region's duration of the slowest
+    rank); a device tensor under NCCL, a host tensor under gloo."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

@@ -45,3 +45,43 @@ def test_clock_summary():
     hot = bench.summarize_clocks(["0, 1500, 2070, 1400, 0x48, Active, Active, Not Active, Not Active"])
     assert hot["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
     assert bench.summarize_clocks([])["sm_mhz"] is None
+
+
+def _free_port():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    bench.barrier(world)
+    # each rank's own timed-region length; every rank must report the slowest
+    t = bench.max_over_ranks(world, 10.0 + 7.5 * rank)
+    bench.barrier(world)
+    dist.destroy_process_group()
+    out.put((rank, t))
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, 17.5), (1, 17.5)]
