@@ -32,6 +32,9 @@
  *   - Return codes: 0 success; -k argument k invalid; 1000 + j inverse
  *     iteration did not converge for eigenpair j (results still written);
  *     SKEW_ERR_* below.
+ *   - Diagnostics (refinement statistics, launch count, kernel timing) are
+ *     process-wide records of the most recent call.  Calls from several
+ *     host threads at once are not tested; their records would mix.
  */
 #ifndef SKEWEIG_H
 #define SKEWEIG_H
