@@ -89,3 +89,17 @@ def test_batch_orders():
     e3 = (1024.0 ** 3 - 32.0 ** 3) / (3 * np.log(32.0))
     assert abs(np.mean(sizes.astype(float) ** 2) / e2 - 1) < 0.1
     assert abs(np.mean(sizes.astype(float) ** 3) / e3 - 1) < 0.1
+
+
+def test_bse_device_follows_the_same_recipe():
+    # the benchmark's generator (final product in torch) draws the same blocks
+    # and builds the same K up to the rounding of one matrix product; run here
+    # with torch on the host
+    import torch
+    n, seed = 256, 3
+    Kd = inputs.bse_device(n, seed=seed, device="cpu")
+    assert Kd.dtype == torch.float64 and Kd.stride() == (1, n)     # column-major
+    Kd = Kd.numpy()
+    K = inputs.bse(n, seed=seed)
+    assert np.array_equal(Kd, -Kd.T)
+    assert np.max(np.abs(Kd - K)) <= 1e-13 * np.max(np.abs(K))
