@@ -10,8 +10,9 @@
 // one step k into a block (a parallelogram of rows s0+1+k b .. s0+ell-1+k b+b)
 // the order "groups descending; inside a group k ascending; inside a block s
 // descending" equals the reverse generation order up to swaps of reflectors
-// with disjoint rows (for ell <= b, H_{s',k'} and H_{s,k} with s' > s and
-// k' > k never share a row; the same holds for equal s).  Each CTA owns a slab
+// with disjoint rows (H_{s',k'} and H_{s,k} with s' >= s and k' > k never
+// share a row, since s'+1+k'b > s+kb+b, whatever ell is; ell only sets the
+// window height ell + b - 1).  Each CTA owns a slab
 // of columns and keeps one block's row window in shared memory while it
 // applies the block's ell reflectors, so Z crosses HBM once per block instead
 // of once per reflector.
