@@ -28,13 +28,24 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into _oracle.so with gcc (plain -O2, no fast-math)."""
+    """Compile oracle.c into _oracle.so with gcc (plain -O2, no fast-math, no
+    contraction into FMAs), with OpenMP when the compiler has it."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-std=c99",
-                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-std=gnu99", "-shared", "-fPIC"]
+        try:
+            subprocess.check_call(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(t: int = 0) -> int:
+    """Threads of the oracle's parallel loops (t <= 0: the OpenMP default,
+    all cores unless OMP_NUM_THREADS says otherwise).  Results do not depend
+    on it.  Returns the thread count in effect."""
+    return int(_load().oracle_set_threads(int(t)))
 
 
 def _load():
@@ -50,6 +61,8 @@ def _load():
         lib.oracle_dmap.argtypes = [i, i, d, i, d, d, i]
         lib.oracle_dmap.restype = None
         lib.oracle_skew_eig.argtypes = [i, d, i, i, d, d, d, i]
+        lib.oracle_set_threads.argtypes = [i]
+        lib.oracle_set_threads.restype = i
         _lib = lib
     return _lib
 

@@ -31,8 +31,30 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define AT(M, i, j, ld) ((M)[(size_t)(j) * (size_t)(ld) + (size_t)(i)])
+#define ROWBLK 64   /* rows per thread task in the row sums of A22 v */
+
+/* Threads (OpenMP, when built with it): the level-2 loops of the
+ * tridiagonalisation, the bisection over eigenvalues, the D map and Q_trd over
+ * columns run in parallel.  Every floating-point sum keeps the order of the
+ * serial loop, so the results are the same for any thread count.  Inverse
+ * iteration stays serial (the Gram-Schmidt chain of a cluster is sequential).
+ * oracle_set_threads(t <= 0) leaves the OpenMP default; it returns the number
+ * of threads a parallel loop will use (1 without OpenMP).                  */
+int oracle_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+    return omp_get_max_threads();
+#else
+    (void)t;
+    return 1;
+#endif
+}
 
 /* ---------------------------------------------------------------------- */
 /* Householder reflector (Sec. 2.1: Q_i = I - tau_i v_i v_i^T, v stored in the
@@ -70,11 +92,15 @@ int oracle_tridiagonalize(int n, const double *A, int lda, double *alpha,
     if (n <= 0) return 0;
     double *L = (double *)malloc(sizeof(double) * (size_t)n * n);
     double *p = (double *)malloc(sizeof(double) * (size_t)n);
-    if (!L || !p) { free(L); free(p); return -1; }
-    for (int j = 0; j < n; j++)
-        for (int i = 0; i < n; i++)
+    double *s = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!L || !p || !s) { free(L); free(p); free(s); return -1; }
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < n; j++) {
+        for (int i = 0; i < n; i++) {
             AT(L, i, j, n) = (i > j) ? AT(A, i, j, lda) : 0.0;
-    memset(V, 0, sizeof(double) * (size_t)n * n);
+            AT(V, i, j, n) = 0.0;
+        }
+    }
     for (int c = 0; c + 2 < n; c++) {
         int m = n - c - 1;               /* length of x = L[c+1:n, c] */
         double *x = &AT(L, c + 1, c, n);
@@ -85,21 +111,34 @@ int oracle_tridiagonalize(int n, const double *A, int lda, double *alpha,
         AT(V, c + 1, c, n) = 1.0;
         for (int i = 1; i < m; i++) AT(V, c + 1 + i, c, n) = x[i];
         const double *v = &AT(V, c + 1, c, n);
-        /* p = tau * A22 v, A22 = L[c+1:, c+1:] - L[c+1:, c+1:]^T, accumulated
-         * column by column: entry (i, j), i > j, adds L_ij v_j to p_i and
-         * subtracts L_ij v_i from p_j */
-        for (int i = 0; i < m; i++) p[i] = 0.0;
+        /* p = tau * A22 v, A22 = L[c+1:, c+1:] - L[c+1:, c+1:]^T:
+         *   p_i = tau * (r_i - s_i),  r_i = sum_{j<i} L_ij v_j,
+         *                             s_i = sum_{j>i} L_ji v_j,
+         * each sum taken in ascending j.  s_i reads column i of L; r_i is
+         * accumulated over a block of rows, column by column, so that every
+         * read is a contiguous piece of a column.  The threads split columns
+         * (s) and row blocks (r); each sum keeps its order, so the result does
+         * not depend on the thread count. */
+#pragma omp parallel for schedule(dynamic, 16)
         for (int j = 0; j < m; j++) {
             const double *Lj = &AT(L, c + 1, c + 1 + j, n);
             double sj = 0.0;
-            for (int i = j + 1; i < m; i++) {
-                p[i] += Lj[i] * v[j];
-                sj += Lj[i] * v[i];
-            }
-            p[j] -= sj;
+            for (int i = j + 1; i < m; i++) sj += Lj[i] * v[i];
+            s[j] = sj;
         }
-        for (int i = 0; i < m; i++) p[i] *= t;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int i0 = 0; i0 < m; i0 += ROWBLK) {
+            const int i1 = (i0 + ROWBLK < m) ? i0 + ROWBLK : m;
+            for (int i = i0; i < i1; i++) p[i] = 0.0;
+            for (int j = 0; j + 1 < i1; j++) {
+                const double *Lj = &AT(L, c + 1, c + 1 + j, n);
+                const double vj = v[j];
+                for (int i = (j + 1 > i0) ? j + 1 : i0; i < i1; i++) p[i] += Lj[i] * vj;
+            }
+            for (int i = i0; i < i1; i++) p[i] = (p[i] - s[i]) * t;
+        }
         /* A22 <- A22 + v p^T - p v^T (strict lower part) */
+#pragma omp parallel for schedule(dynamic, 16)
         for (int j = 0; j < m; j++)
             for (int i = j + 1; i < m; i++)
                 AT(L, c + 1 + i, c + 1 + j, n) += v[i] * p[j] - p[i] * v[j];
@@ -111,6 +150,7 @@ int oracle_tridiagonalize(int n, const double *A, int lda, double *alpha,
     if (n >= 2) alpha[n - 2] = -AT(L, n - 1, n - 2, n);
     free(L);
     free(p);
+    free(s);
     return 0;
 }
 
@@ -124,6 +164,7 @@ void oracle_apply_q(int n, const double *V, const double *tau, int k, double *Z,
         if (t == 0.0) continue;
         const double *v = &AT(V, c + 1, c, n);
         int m = n - c - 1;
+#pragma omp parallel for schedule(static)
         for (int j = 0; j < k; j++) {
             double *z = &AT(Z, c + 1, j, ldz);
             double w = 0.0;
@@ -189,6 +230,7 @@ int oracle_bisect(int n, const double *alpha, int nev, double *lambda)
     }
     double glo = -g - 2.0 * DBL_EPSILON * g - pivmin;
     double ghi = g + 2.0 * DBL_EPSILON * g + pivmin;
+#pragma omp parallel for schedule(dynamic, 4)
     for (int k = 0; k < nev; k++) {
         int j = n - 1 - k;              /* 0-based ascending index */
         double lo = glo, hi = ghi;      /* count(lo) <= j < count(hi) */
@@ -330,6 +372,7 @@ int oracle_inverse_iteration(int n, const double *alpha, int nev,
 void oracle_dmap(int n, int k, const double *Q, int ldq, double *X, double *Y,
                  int ldz)
 {
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < k; j++)
         for (int r = 0; r < n; r++) {
             double q = AT(Q, r, j, ldq);

@@ -266,3 +266,17 @@ def test_metrics_definitions():
     assert oracle.orthogonality(X, Y) <= 1e-15
     assert oracle.residual(A, [2.0 + 1e-3], X, Y) == pytest.approx(1e-3, rel=1e-9)
     assert oracle.orthogonality(2 * X, 2 * Y) == pytest.approx(3.0, rel=1e-12)
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    # the parallel loops keep every sum in its serial order
+    A = inputs.bse(260, seed=17)
+    before = oracle.set_threads(1)
+    try:
+        r1 = oracle.skew_eig(A, 130)
+        oracle.set_threads(4)
+        r4 = oracle.skew_eig(A, 130)
+    finally:
+        oracle.set_threads(max(before, 1))
+    for a, b in zip(r1[:3], r4[:3]):
+        assert np.array_equal(a, b)
