@@ -82,9 +82,15 @@ typedef enum {
 } skew_mode;
 
 /* Fault hooks (host-side injection for tests; never fault the GPU). */
-#define SKEW_FAULT_NOMEM 1         /* pretend the workspace allocation failed */
+#define SKEW_FAULT_NOMEM 1         /* entry points that allocate (skew_eig_host,
+                                      skew_eig_batched) fail as if the pool had no
+                                      memory: SKEW_ERR_NOMEM, nothing launched */
 #define SKEW_FAULT_INVIT_NOCONV 2  /* give inverse iteration zero iterations */
-#define SKEW_FAULT_TINY_WAIT 4     /* make device waits give up at once */
+#define SKEW_FAULT_TINY_WAIT 4     /* the solve's waits between CTAs (panel-QR
+                                      grid barrier, bulge-chase progress flags)
+                                      give up after a few polls: a wait that is
+                                      not satisfied at once ends the kernel with
+                                      SKEW_ERR_DEVICE_TIMEOUT in the status */
 #define SKEW_FAULT_NO_REFINE 8     /* mixed modes: skip the FP64 refinement */
 
 typedef struct {
@@ -112,9 +118,19 @@ const char* skew_eig_strerror(int code);
 const char* skew_last_cuda_error(void);
 
 /*
+ * Memory of the allocating entry points (skew_eig, skew_eig_host,
+ * skew_eig_batched): stream-ordered allocations from a library-owned memory
+ * pool of the stream's device, created on first use, whose freed memory stays
+ * reserved for the next call (repeated solves of one size allocate nothing
+ * new).  skew_release_memory() returns the memory held by completed calls to
+ * the system.  The *_ex entry points take caller workspace and never allocate.
+ */
+void skew_release_memory(void);
+
+/*
  * Full solve, device buffers.  Eigenvalues lambda[0..nev-1] (descending,
  * >= 0) and, unless Z_re == Z_im == NULL, Z_re / Z_im (n x nev, leading
- * dimension n).  Allocates its workspace with cudaMallocAsync on `stream`,
+ * dimension n).  Takes its workspace from the library pool on `stream`,
  * synchronises `stream` at the end and returns the numerical status.
  * Arguments: 1 n >= 0, 2 A (n x n, ld lda), 3 lda >= max(1, n),
  * 4 0 <= nev <= n/2, 5 lambda (NULL only if nev == 0), 6/7 Z_re/Z_im (both
@@ -159,8 +175,8 @@ int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda,
  * inverse-iteration launch for all matrices, then back-transform launches),
  * always in FP64; larger orders run the two-step solve of skew_eig_ex one after
  * another in `opts`' mode.  Not in the paper (it solves one matrix per run).
- * Asynchronous on `stream`.  skew_eig_batched allocates its workspace with
- * cudaMallocAsync / cudaFreeAsync on the stream and reports no per-matrix
+ * Asynchronous on `stream`.  skew_eig_batched takes its workspace from the
+ * library pool (stream-ordered, freed on the stream) and reports no per-matrix
  * status; skew_eig_batched_ex takes a caller workspace of at least
  * skew_eig_batched_workspace_size(count, n, nev, opts) bytes and a device
  * array d_info[count] (may be NULL) that receives 0 or 1000 + j per matrix.
@@ -291,13 +307,19 @@ long long skew_launch_count(void);
 /* Kernel timing (diagnostics).  skew_kernel_timing(1) clears the record and
  * from then on brackets the library's launches (one record per launch or per
  * group of launches of one kind) with CUDA events on the stream they go to
- * (two event records each, at most 16384 records); skew_kernel_timing(0) stops.
- * Not thread-safe: one solving thread per process while it is on.
- * skew_kernel_timing_read sums, over the records of one kind, the
- * event-measured time (*ms), the algorithmic flops (*flops; for the two
- * product kinds: 2 M N K per kept slice or plane product over the outputs the
- * launch writes, 0 for the others) and the record count; it waits for the
- * recorded events.  Returns 0, -1 for an unknown kind, or SKEW_ERR_CUDA. */
+ * (two event records each); skew_kernel_timing(0) stops.  Records wait in a
+ * pool of 16384 until they are folded into per-kind totals: at the end of
+ * every skew_eig_profile call (its solve is then complete) and by each of the
+ * read functions below.  A launch that finds the pool full is not recorded and
+ * counted as dropped (skew_kernel_timing_dropped).  Not thread-safe: one
+ * solving thread per process while it is on.
+ * skew_kernel_timing_read folds the outstanding records (waiting for their
+ * events) and returns, summed over the records of one kind since timing was
+ * switched on, the event-measured time (*ms), the algorithmic flops (*flops;
+ * for the two product kinds: 2 M N K per kept slice or plane product over the
+ * outputs the launch writes, 0 for the others) and the record count.  Returns
+ * 0, -1 for an unknown kind, -2 when records were dropped (the totals miss
+ * them), or SKEW_ERR_CUDA. */
 #define SKEW_KERNEL_OZAKI 0        /* ozaki_gemm_kernel outside the refinement (reduction, Q_band) */
 #define SKEW_KERNEL_SPLIT 1        /* BF16x3 / BF16x6 split product (umma_gemm_kernel) */
 #define SKEW_KERNEL_OZAKI_REFINE 2 /* ozaki_gemm_kernel inside the refinement (n x n x n) */
@@ -313,12 +335,14 @@ long long skew_launch_count(void);
 #define SKEW_KERNEL_KINDS 12
 int skew_kernel_timing(int enable);
 int skew_kernel_timing_read(int kind, double* ms, double* flops, long long* launches);
-/* Timeline of the same records: for the first min(cap, records) records in
- * launch order, kinds[i] (SKEW_KERNEL_*), and the start and end of record i in
+long long skew_kernel_timing_dropped(void);
+/* Timeline of the records folded last (after a skew_eig_profile call: the
+ * records of that solve): for the first min(cap, records) records in launch
+ * order, kinds[i] (SKEW_KERNEL_*), and the start and end of record i in
  * milliseconds after the start of record 0 (events of different streams, as
- * the side stream of the band reduction, interleave).  Any output pointer may
- * be NULL.  Waits for the recorded events.  Returns the number of records
- * written, -1 for cap < 0, or SKEW_ERR_CUDA. */
+ * the side stream of the band reduction, interleave).  Folds the outstanding
+ * records first.  Any output pointer may be NULL.  Returns the number of
+ * records written, -1 for cap < 0, or SKEW_ERR_CUDA. */
 int skew_kernel_timeline(int cap, int* kinds, double* start_ms, double* end_ms);
 
 /* ------------------------------------------------------------------------
@@ -377,14 +401,17 @@ int skew_tridiag_eig(int n, const double* alpha, int nev, double* lambda,
  * holds until the process exits.  For callers that may not allocate device
  * memory (their application owns every allocation, or cudaMalloc's device
  * synchronisation is not allowed); the paper has no counterpart.
- * Limit: with Q, about 41 * n * nev + 8 n bytes must fit (e.g. n = 512,
- * nev = 256); larger sizes return SKEW_ERR_WORKSPACE.  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture.  All calls
- * share the array, which keeps the previous call's contents: calls that
- * overlap on the GPU race, so serialise them.  Arguments 1 n >= 1, 2 alpha
- * (device, n-1), 3 1 <= nev <= n, 4 lambda (device, nev), 5 Q (device or
- * NULL), 6 ldq >= n, 7 d_status (device int, zeroed by the caller), 8 stream.
+ * Limit: the call fits when skew_tridiag_ws(n, nev) <= SKEW_NOALLOC_SCRATCH_BYTES
+ * (with Q; about 41 * n * nev bytes for nev >= 64, e.g. n = 512, nev = 256);
+ * larger sizes return SKEW_ERR_WORKSPACE.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) and caches it; make
+ * that first call before any stream capture.  The address belongs to the
+ * current device: `stream` must be a stream of the current device (or NULL),
+ * otherwise SKEW_ERR_UNSUPPORTED.  All calls share the array, which keeps the
+ * previous call's contents: calls that overlap on the GPU race, so serialise
+ * them.  Arguments 1 n >= 1, 2 alpha (device, n-1; may be NULL when n = 1),
+ * 3 1 <= nev <= n, 4 lambda (device, nev), 5 Q (device or NULL), 6 ldq >= n,
+ * 7 d_status (device int, zeroed by the caller), 8 stream.
  */
 #define SKEW_NOALLOC_SCRATCH_BYTES (6u << 20)
 int skew_tridiag_eig_noalloc(int n, const double* alpha, int nev, double* lambda,

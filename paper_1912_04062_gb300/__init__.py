@@ -62,6 +62,8 @@ SIGNATURES = {
     "skew_refine_slices": (_i, [_p, _p, _i]),
     "skew_kernel_timing": (_i, [_i]),
     "skew_kernel_timing_read": (_i, [_i, _p, _p, _p]),
+    "skew_kernel_timing_dropped": (ctypes.c_longlong, []),
+    "skew_release_memory": (None, []),
     "skew_kernel_timeline": (_i, [_i, _p, _p, _p]),
     "skew_gemm_bf16x3_ws": (_sz, [_i, _i, _i]),
     "skew_gemm_f64acc_ws": (_sz, [_i, _i, _i]),
@@ -352,11 +354,16 @@ def kernel_timing(enable: bool) -> None:
 
 
 def kernel_timing_read(kind: int):
-    """(total ms, algorithmic flops, launches) recorded for one kernel kind."""
+    """(total ms, algorithmic flops, launches) recorded for one kernel kind
+    since timing was switched on.  Raises if any launch went unrecorded
+    (the record pool was full), since the totals would then be short."""
     ms = ctypes.c_double()
     fl = ctypes.c_double()
     k = ctypes.c_longlong()
     code = lib().skew_kernel_timing_read(kind, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(k))
+    if code == -2:
+        raise RuntimeError(f"kernel timing dropped {lib().skew_kernel_timing_dropped()} launches: "
+                           "the per-kind totals are incomplete")
     _check(code, "skew_kernel_timing_read")
     return ms.value, fl.value, k.value
 

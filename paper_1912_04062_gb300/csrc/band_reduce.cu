@@ -28,7 +28,7 @@ constexpr int QR_THREADS = 256;
 __global__ void __launch_bounds__(QR_THREADS, 1)
 panel_qr_kernel(int m, int nb, double* __restrict__ P, int ldp, double* __restrict__ tau,
                 double* __restrict__ part, double* __restrict__ rowbuf, unsigned* bar,
-                int* status, int rpc) {
+                int* status, int rpc, unsigned spin_cap) {
     extern __shared__ double smem[];
     double* S = smem;                      // rpc x nb, column-major (ld rpc)
     double* vs = S + (size_t)rpc * nb;     // rpc (scaled column i)
@@ -72,7 +72,7 @@ panel_qr_kernel(int m, int nb, double* __restrict__ P, int ldp, double* __restri
             for (int c = i + t; c < nb; c += QR_THREADS)
                 rowbuf[buf * nb + c] = S[(size_t)c * rpc + (i - r0)];
         }
-        if (!sk_grid_barrier(bar, epoch, status)) return;
+        if (!sk_grid_barrier(bar, epoch, status, spin_cap)) return;
         // ---- phase B: reduce partials, four threads per column over CTAs
         // q, q+4, .. (a fixed order: identical in all CTAs)
         for (int cb = i; cb < nb; cb += QR_THREADS / 4) {
@@ -289,6 +289,7 @@ constexpr int LAZY_G = 4;
 struct ReduceWs {
     double *V, *Pm, *Y, *X2, *Y2, *G, *C1, *C2, *tau, *part, *rowbuf;
     unsigned* bar;
+    unsigned spin_cap;  // polls of the panel QR's grid barrier before it gives up
     // tensor-core form: Z = [-C2/2; T], split-K partials of the main and side
     // streams, digit slices of V, P, [V P] and Z
     double *Z, *part_m, *part_s, *part_p;
@@ -423,7 +424,8 @@ int launch_panel_qr(cudaStream_t st, int n, int b, int p, double* W, int ldw, Re
     if (cudaMemsetAsync(w.bar, 0, sizeof(unsigned), st) != cudaSuccess) return SKEW_ERR_CUDA;
     int ldp = ldw, nbv = b, mm = m;
     double* taup = w.tau;
-    void* args[] = {&mm, &nbv, &panel, &ldp, &taup, &w.part, &w.rowbuf, &w.bar, &d_status, &rpc};
+    unsigned cap = w.spin_cap;
+    void* args[] = {&mm, &nbv, &panel, &ldp, &taup, &w.part, &w.rowbuf, &w.bar, &d_status, &rpc, &cap};
     KtScope kt(st, KT_PANEL_QR);
     if (cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st) != cudaSuccess)
         return SKEW_ERR_LAUNCH;
@@ -560,13 +562,14 @@ int band_reduce_f64acc(cudaStream_t st, int n, double* W, int ldw, int b, double
 }  // namespace
 
 int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac, void* ws,
-                size_t ws_bytes, int* d_status, int planes, int slices) {
+                size_t ws_bytes, int* d_status, int planes, int slices, unsigned spin_cap) {
     const bool mixed = planes > 0;
     if (b <= 0 || b % 64 != 0 || b > 128) return SKEW_ERR_UNSUPPORTED;
     const int P = num_panels(n, b);
     if (P == 0) return 0;
     Carve cv(ws, ws_bytes);
     ReduceWs w = carve_reduce(cv, n, b, planes == REDUCE_F64ACC);
+    w.spin_cap = spin_cap ? spin_cap : SK_SPIN_CAP;
     const size_t gsz = mixed ? mixed_gemm_ws(n, b, planes) : 0;
     void* gws = mixed ? cv.take<char>(gsz) : nullptr;
     if (!cv.ok) return SKEW_ERR_WORKSPACE;

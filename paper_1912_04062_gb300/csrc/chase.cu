@@ -126,7 +126,7 @@ __device__ bool chase_task(int n, int s, int k, int nsw, const int* __restrict__
                            double* __restrict__ Vtrd, double* __restrict__ tautrd, float* __restrict__ V32,
                            float* __restrict__ tau32, int nsw64, double* __restrict__ B, double* __restrict__ D,
                            double* __restrict__ C, bool have_b, bool keep_c, bool fix_e, bool defer_e,
-                           ChaseSmem& sm) {
+                           ChaseSmem& sm, unsigned spin_cap) {
     const int t = threadIdx.x, warp = t >> 5;
     const int r = s + 1 + k * CB;
     const int L = min(CB, n - r);
@@ -148,7 +148,7 @@ __device__ bool chase_task(int n, int s, int k, int nsw, const int* __restrict__
         if (want > 0) {
             unsigned polls = 0;
             while (sk_ld_acquire_s32(prog_prev) < want) {
-                if (++polls > SK_SPIN_CAP || *(volatile int*)status != 0) {
+                if (++polls > spin_cap || *(volatile int*)status != 0) {
                     ok = 0;
                     break;
                 }
@@ -282,7 +282,7 @@ __device__ bool chase_task(int n, int s, int k, int nsw, const int* __restrict__
 __global__ void __launch_bounds__(CH_THREADS)
 chase_kernel(int n, double* __restrict__ AB, int ldab, double* __restrict__ alpha,
              double* __restrict__ Vtrd, double* __restrict__ tautrd, float* __restrict__ V32,
-             float* __restrict__ tau32, int* prog, int* status) {
+             float* __restrict__ tau32, int* prog, int* status, unsigned spin_cap) {
     extern __shared__ __align__(16) unsigned char chase_raw[];
     ChaseSmem& sm = *reinterpret_cast<ChaseSmem*>(chase_raw);
     const int nsw = n - 2, nsw64 = (nsw + 63) / 64 * 64;
@@ -300,7 +300,7 @@ chase_kernel(int n, double* __restrict__ AB, int ldab, double* __restrict__ alph
             const int want = (s > 0) ? min(k + 2, nsp) : 0;
             const bool defer_e = s > 0 && n - (s + 1 + k * CB) >= 2 * CB && k + 2 < nsp;
             if (!chase_task(n, s, k, nsw, prog + (s > 0 ? s - 1 : 0), want, status, AB, ldab, alpha, Vtrd, tautrd,
-                            V32, tau32, nsw64, B, D, C, have_b, keep_c, fix_e, defer_e, sm))
+                            V32, tau32, nsw64, B, D, C, have_b, keep_c, fix_e, defer_e, sm, spin_cap))
                 return;
             // all stores of the step precede the release (bar.sync, then a
             // gpu-scope release by one thread)
@@ -330,7 +330,7 @@ size_t chase_ws(int n, int b) {
 
 int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha, double* Vtrd, double* tautrd,
           void* ws, size_t ws_bytes, int* d_status, unsigned spin_cap, float* V32, float* tau32) {
-    (void)spin_cap;
+    if (spin_cap == 0) spin_cap = SK_SPIN_CAP;
     if (b != CB) return SKEW_ERR_UNSUPPORTED;
     if (n < 2) return 0;
     if (ldab < 2 * b + 1) return SKEW_ERR_UNSUPPORTED;
@@ -347,7 +347,7 @@ int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha, do
         if (occ < 1) return SKEW_ERR_LAUNCH;
         int G = occ * device_sms();
         if (G > nsw) G = nsw;
-        void* args[] = {&n, &AB, &ldab, &alpha, &Vtrd, &tautrd, &V32, &tau32, &prog, &d_status};
+        void* args[] = {&n, &AB, &ldab, &alpha, &Vtrd, &tautrd, &V32, &tau32, &prog, &d_status, &spin_cap};
         KtScope kt(st, KT_CHASE);
         if (cudaLaunchCooperativeKernel((void*)chase_kernel, dim3(G), dim3(CH_THREADS), args, smem, st) != cudaSuccess)
             return SKEW_ERR_LAUNCH;

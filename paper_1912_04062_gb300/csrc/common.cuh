@@ -16,6 +16,9 @@
 #ifndef SK_SPIN_CAP
 #define SK_SPIN_CAP (1u << 24)
 #endif
+// Cap of the waits between CTAs under SKEW_FAULT_TINY_WAIT: a wait not
+// satisfied by its second poll gives up (tests of the timeout path).
+#define SK_TINY_SPIN_CAP 1u
 
 // Device-side status word: first error wins.
 SK_DEV void sk_set_error(int* status, int code) {
@@ -43,9 +46,9 @@ SK_DEV unsigned sk_atom_add_release(unsigned* p, unsigned v) {
 
 // Grid-wide barrier for cooperative launches (all CTAs co-resident).  The
 // counter grows monotonically; the caller tracks its own epoch.  Returns false
-// (and records SKEW_ERR_DEVICE_TIMEOUT) when the wait cap is reached or when
-// another CTA already reported an error.
-SK_DEV bool sk_grid_barrier(unsigned* counter, unsigned& epoch, int* status) {
+// (and records SKEW_ERR_DEVICE_TIMEOUT) when the wait cap (polls) is reached or
+// when another CTA already reported an error.
+SK_DEV bool sk_grid_barrier(unsigned* counter, unsigned& epoch, int* status, unsigned cap = SK_SPIN_CAP) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -57,7 +60,7 @@ SK_DEV bool sk_grid_barrier(unsigned* counter, unsigned& epoch, int* status) {
         int ok = 1;
         unsigned polls = 0;
         while (sk_ld_acquire(counter) < target) {
-            if (++polls > SK_SPIN_CAP || *(volatile int*)status != 0) {
+            if (++polls > cap || *(volatile int*)status != 0) {
                 ok = 0;
                 break;
             }

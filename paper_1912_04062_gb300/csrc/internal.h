@@ -42,9 +42,12 @@ cudaError_t gemm_lower_tiles(cudaStream_t st, int m, int k, const double* X, int
 // REDUCE_F64ACC: as FP64-accurate digit-slice tensor-core products.
 constexpr int REDUCE_F64ACC = 8;
 size_t band_reduce_ws(int n, int b, int planes = 0);
-// slices: digit slices of the REDUCE_F64ACC products (8: FP64-accurate)
+// slices: digit slices of the REDUCE_F64ACC products (8: FP64-accurate);
+// spin_cap: polls of the panel QR's grid barrier before it gives up with
+// SKEW_ERR_DEVICE_TIMEOUT (0: the default cap)
 int band_reduce(cudaStream_t st, int n, double* W, int ldw, int b, double* Tfac,
-                void* ws, size_t ws_bytes, int* d_status, int planes = 0, int slices = 8);
+                void* ws, size_t ws_bytes, int* d_status, int planes = 0, int slices = 8,
+                unsigned spin_cap = 0);
 cudaError_t band_pack(cudaStream_t st, int n, int b, const double* W, int ldw,
                       double* AB, int ldab);
 // Explicit V (m x b, ld ldv) of panel p from the reduced W.
@@ -58,7 +61,8 @@ size_t chase_ws(int n, int b);
 // Vtrd / tautrd (may be null): the reflectors in FP64, slot k nsw + s.  V32 /
 // tau32 (may be null): FP32 copies with the sweep stride padded to a multiple
 // of 64 (slot k nsw64 + s); slots of steps a sweep does not have are not
-// written.
+// written.  spin_cap: polls of a wait on the previous sweep's progress before
+// it gives up with SKEW_ERR_DEVICE_TIMEOUT (0: the default cap).
 int chase(cudaStream_t st, int n, int b, double* AB, int ldab, double* alpha,
           double* Vtrd, double* tautrd, void* ws, size_t ws_bytes, int* d_status,
           unsigned spin_cap, float* V32 = nullptr, float* tau32 = nullptr);

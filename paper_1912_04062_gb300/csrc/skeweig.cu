@@ -2,6 +2,8 @@
 // workspace carve-up and the stage sequence of Algorithm 1 (two-step form) on
 // one stream.
 #include <atomic>
+#include <cstdint>
+#include <mutex>
 #include <vector>
 #include <cmath>
 #include <cstdio>
@@ -186,6 +188,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
         if (!carve_plan(p, cv)) return SKEW_ERR_WORKSPACE;
     }
     const int maxit = (o && (o->fault & SKEW_FAULT_INVIT_NOCONV)) ? 0 : 5;
+    const unsigned spin_cap = (o && (o->fault & SKEW_FAULT_TINY_WAIT)) ? SK_TINY_SPIN_CAP : 0;
     last_refine_info() = RefineInfo{};  // iterations = 0 unless this solve refines
 
     mark(0);
@@ -198,7 +201,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     count_launch(2);
     mark(1);
     int rc = band_reduce(st, n, p.W, n, p.b, p.Tfac, p.ws_reduce, p.sz_reduce, p.status, p.reduce_prec,
-                         p.reduce_slices);
+                         p.reduce_slices, spin_cap);
     if (rc) return rc;
     mark(2);
     if (band_pack(st, n, p.b, p.W, n, p.AB, (int)p.ldab) != cudaSuccess) return SKEW_ERR_CUDA;
@@ -209,10 +212,11 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
         const size_t nsw64 = ((size_t)p.nsw + 63) / 64 * 64;
         if (const cudaError_t e = cudaMemsetAsync(p.tau32, 0, sizeof(float) * (size_t)p.K * nsw64, st))
             return cuda_fail(e);
-        rc = chase(st, n, p.b, p.AB, (int)p.ldab, p.alpha, nullptr, nullptr, p.ws_chase, p.sz_chase, p.status, 0,
-                   p.V32, p.tau32);
+        rc = chase(st, n, p.b, p.AB, (int)p.ldab, p.alpha, nullptr, nullptr, p.ws_chase, p.sz_chase, p.status,
+                   spin_cap, p.V32, p.tau32);
     } else {
-        rc = chase(st, n, p.b, p.AB, (int)p.ldab, p.alpha, p.Vtrd, p.tautrd, p.ws_chase, p.sz_chase, p.status, 0);
+        rc = chase(st, n, p.b, p.AB, (int)p.ldab, p.alpha, p.Vtrd, p.tautrd, p.ws_chase, p.sz_chase, p.status,
+                   spin_cap);
     }
     if (rc) return rc;
     mark(4);
@@ -297,12 +301,57 @@ struct KTimer {
     bool on = false;
     size_t used = 0;
     std::vector<KtRec> recs;  // events are created on first use and reused
+    // per-kind totals of the records folded so far (kt_fold)
+    double ms[KT_KINDS] = {}, fl[KT_KINDS] = {};
+    long long cnt[KT_KINDS] = {};
+    long long dropped = 0;  // launches not recorded because the pool was full
+    // timeline of the records folded last: kind, start and end (ms after the
+    // first of them)
+    std::vector<int> tl_kind;
+    std::vector<double> tl_a, tl_b;
+    void clear() {
+        used = 0;
+        for (int k = 0; k < KT_KINDS; k++) ms[k] = fl[k] = 0.0, cnt[k] = 0;
+        dropped = 0;
+        tl_kind.clear();
+        tl_a.clear();
+        tl_b.clear();
+    }
 };
 KTimer& ktimer() {
     static KTimer t;
     return t;
 }
 constexpr size_t KT_CAP = 16384;
+
+// Waits for the outstanding records, adds them to the per-kind totals, keeps
+// their timeline and frees the pool.  Returns 0 or SKEW_ERR_CUDA.
+int kt_fold() {
+    KTimer& t = ktimer();
+    if (t.used == 0) return 0;
+    t.tl_kind.clear();
+    t.tl_a.clear();
+    t.tl_b.clear();
+    const cudaEvent_t t0 = t.recs[0].a;
+    for (size_t i = 0; i < t.used; i++) {
+        const KtRec& r = t.recs[i];
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return SKEW_ERR_CUDA;
+        float e = 0.f, a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&e, r.a, r.b) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (cudaEventElapsedTime(&a, t0, r.a) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (cudaEventElapsedTime(&b, t0, r.b) != cudaSuccess) return SKEW_ERR_CUDA;
+        if (r.kind >= 0 && r.kind < KT_KINDS) {
+            t.ms[r.kind] += e;
+            t.fl[r.kind] += r.flops;
+            t.cnt[r.kind]++;
+        }
+        t.tl_kind.push_back(r.kind);
+        t.tl_a.push_back(a);
+        t.tl_b.push_back(b);
+    }
+    t.used = 0;
+    return 0;
+}
 }  // namespace
 
 int g_kt_ozaki_kind = KT_OZAKI;
@@ -319,7 +368,10 @@ int kt_begin(cudaStream_t st) {
     KTimer& t = ktimer();
     if (!t.on) return -1;
     if (t.used == t.recs.size()) {
-        if (t.recs.size() >= KT_CAP) return -1;
+        if (t.recs.size() >= KT_CAP) {
+            t.dropped++;
+            return -1;
+        }
         KtRec r{};
         if (cudaEventCreate(&r.a) != cudaSuccess) return -1;
         if (cudaEventCreate(&r.b) != cudaSuccess) {
@@ -346,7 +398,71 @@ void kt_end(cudaStream_t st, int slot, int kind, double flops) {
 
 using namespace sk;
 
+namespace {
+
+// Library-owned stream-ordered memory pools, one per device, created on first
+// use.  Their release threshold is unlimited: a workspace freed by a completed
+// call stays reserved for the next call on that device, so repeated solves do
+// not map tens of GB of fresh pages each time.  skew_release_memory() returns
+// the reserved memory.
+constexpr int MAX_POOL_DEVICES = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[MAX_POOL_DEVICES] = {};
+
+int stream_device(cudaStream_t st, int* dev) {
+    if (st) {
+        if (cudaStreamGetDevice(st, dev) == cudaSuccess) return 0;
+        cudaGetLastError();
+    }
+    return cudaGetDevice(dev) == cudaSuccess ? 0 : -1;
+}
+
+cudaMemPool_t lib_pool(int dev) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
+// Stream-ordered workspace for the allocating entry points: the device's
+// library pool (the default pool if it cannot be had).  SKEW_FAULT_NOMEM in
+// opts makes it fail without allocating (tests of the error path).
+int lib_alloc(void** ptr, size_t bytes, cudaStream_t st, const skew_opts* o) {
+    *ptr = nullptr;
+    if (o && (o->fault & SKEW_FAULT_NOMEM)) return SKEW_ERR_NOMEM;
+    int dev = -1;
+    cudaMemPool_t pool = nullptr;
+    if (stream_device(st, &dev) == 0 && dev >= 0 && dev < MAX_POOL_DEVICES) pool = lib_pool(dev);
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(ptr, bytes, pool, st) : cudaMallocAsync(ptr, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return SKEW_ERR_NOMEM;
+    }
+    return 0;
+}
+
+}  // namespace
+
 extern "C" {
+
+void skew_release_memory(void) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    for (int d = 0; d < MAX_POOL_DEVICES; d++)
+        if (g_pools[d]) cudaMemPoolTrimTo(g_pools[d], 0);
+}
 
 void skew_opts_default(skew_opts* opts) {
     if (!opts) return;
@@ -403,10 +519,7 @@ int skew_eig(int n, const double* A, int lda, int nev, double* lambda, double* Z
     const bool vectors = Z_re != nullptr;
     size_t bytes = plan_bytes(n, nev, nullptr, vectors);
     void* ws = nullptr;
-    if (cudaMallocAsync(&ws, bytes, st) != cudaSuccess) {
-        cudaGetLastError();
-        return SKEW_ERR_NOMEM;
-    }
+    if (const int arc = lib_alloc(&ws, bytes, st, nullptr)) return arc;
     // the last 256 bytes of the allocation (slack of plan_bytes) hold d_info
     int* d_info = reinterpret_cast<int*>(static_cast<char*>(ws) + bytes - 256);
     rc = run_solve(st, n, A, lda, nev, lambda, Z_re, Z_im, n, nullptr, ws, bytes - 256, d_info);
@@ -533,10 +646,7 @@ int skew_eig_batched(int count, const int* n, const double* const* A, const int*
     const size_t need = align_up(bp.small_bytes) + align_up(bp.large_bytes);
     if (need == 0) return 0;
     void* ws = nullptr;
-    if (cudaMallocAsync(&ws, need, st) != cudaSuccess) {
-        cudaGetLastError();
-        return SKEW_ERR_NOMEM;
-    }
+    if (const int arc = lib_alloc(&ws, need, st, opts)) return arc;
     rc = skew_eig_batched_ex(count, n, A, lda, nev, lambda, Z_re, Z_im, opts, ws, need, nullptr, stream);
     cudaFreeAsync(ws, st);
     return rc;
@@ -555,10 +665,7 @@ int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda, doub
     size_t io = align_up(sizeof(double) * nn * n) + align_up(sizeof(double) * nev) +
                 (vectors ? 2 * align_up(sizeof(double) * nn * nev) : 0) + 256;
     char* base = nullptr;
-    if (cudaMallocAsync((void**)&base, bytes + io, st) != cudaSuccess) {
-        cudaGetLastError();
-        return SKEW_ERR_NOMEM;
-    }
+    if (const int arc = lib_alloc((void**)&base, bytes + io, st, opts)) return arc;
     double* dA = reinterpret_cast<double*>(base + bytes);
     double* dl = reinterpret_cast<double*>(base + bytes + align_up(sizeof(double) * nn * n));
     double* dzr = vectors ? reinterpret_cast<double*>(reinterpret_cast<char*>(dl) + align_up(sizeof(double) * nev)) : nullptr;
@@ -609,6 +716,9 @@ int skew_eig_profile(int n, const double* A, int lda, int nev, double* lambda, d
     if (rc == 0)
         for (int i = 0; i < SKEW_NSTAGES; i++) cudaEventElapsedTime(&stage_ms[i], ev.ev[i], ev.ev[i + 1]);
     for (int i = 0; i <= SKEW_NSTAGES; i++) cudaEventDestroy(ev.ev[i]);
+    // kernel timing: the solve is complete, so its records can be folded into
+    // the per-kind totals (the pool then never fills across repeated solves)
+    if (rc == 0 && ktimer().on && kt_fold() != 0) rc = SKEW_ERR_CUDA;
     return rc ? rc : info;
 }
 
@@ -669,46 +779,32 @@ const char* skew_last_cuda_error(void) { return g_last_cuda_error.load(std::memo
 int skew_kernel_timing(int enable) {
     KTimer& t = ktimer();
     t.on = enable != 0;
-    t.used = 0;
+    t.clear();
     return 0;
 }
 
 int skew_kernel_timing_read(int kind, double* ms, double* flops, long long* launches) {
     if (kind < 0 || kind >= KT_KINDS) return -1;
     KTimer& t = ktimer();
-    double tm = 0.0, fl = 0.0;
-    long long k = 0;
-    for (size_t i = 0; i < t.used; i++) {
-        const KtRec& r = t.recs[i];
-        if (r.kind != kind) continue;
-        if (cudaEventSynchronize(r.b) != cudaSuccess) return SKEW_ERR_CUDA;
-        float e = 0.f;
-        if (cudaEventElapsedTime(&e, r.a, r.b) != cudaSuccess) return SKEW_ERR_CUDA;
-        tm += e;
-        fl += r.flops;
-        k++;
-    }
-    if (ms) *ms = tm;
-    if (flops) *flops = fl;
-    if (launches) *launches = k;
-    return 0;
+    if (kt_fold() != 0) return SKEW_ERR_CUDA;
+    if (ms) *ms = t.ms[kind];
+    if (flops) *flops = t.fl[kind];
+    if (launches) *launches = t.cnt[kind];
+    return t.dropped ? -2 : 0;
 }
+
+long long skew_kernel_timing_dropped(void) { return ktimer().dropped; }
 
 int skew_kernel_timeline(int cap, int* kinds, double* start_ms, double* end_ms) {
     if (cap < 0) return -1;
     KTimer& t = ktimer();
-    if (t.used == 0) return 0;
-    const int cnt = (int)(t.used < (size_t)cap ? t.used : (size_t)cap);
-    const cudaEvent_t t0 = t.recs[0].a;
+    if (kt_fold() != 0) return SKEW_ERR_CUDA;
+    const size_t have = t.tl_kind.size();
+    const int cnt = (int)(have < (size_t)cap ? have : (size_t)cap);
     for (int i = 0; i < cnt; i++) {
-        const KtRec& r = t.recs[i];
-        if (cudaEventSynchronize(r.b) != cudaSuccess) return SKEW_ERR_CUDA;
-        float a = 0.f, b = 0.f;
-        if (cudaEventElapsedTime(&a, t0, r.a) != cudaSuccess) return SKEW_ERR_CUDA;
-        if (cudaEventElapsedTime(&b, t0, r.b) != cudaSuccess) return SKEW_ERR_CUDA;
-        if (kinds) kinds[i] = r.kind;
-        if (start_ms) start_ms[i] = a;
-        if (end_ms) end_ms[i] = b;
+        if (kinds) kinds[i] = t.tl_kind[i];
+        if (start_ms) start_ms[i] = t.tl_a[i];
+        if (end_ms) end_ms[i] = t.tl_b[i];
     }
     return cnt;
 }

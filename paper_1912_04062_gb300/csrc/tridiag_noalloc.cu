@@ -29,10 +29,21 @@ void* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
 // Device address of g_noalloc_scratch on the current device (looked up once).
-int scratch_address(void** out) {
+// The address belongs to the current device only, so a stream of another
+// device is refused (SKEW_ERR_UNSUPPORTED) instead of being handed an address
+// it cannot use.
+int scratch_address(cudaStream_t st, void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SKEW_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return SKEW_ERR_UNSUPPORTED;
+    if (st) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return SKEW_ERR_CUDA;
+        }
+        if (sdev != dev) return SKEW_ERR_UNSUPPORTED;
+    }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
@@ -54,7 +65,7 @@ using namespace sk;
 extern "C" int skew_tridiag_eig_noalloc(int n, const double* alpha, int nev, double* lambda, double* Q, int ldq,
                                         int* d_status, void* stream) {
     if (n < 1) return -1;
-    if (!alpha) return -2;
+    if (!alpha && n > 1) return -2;  // n = 1: alpha has no elements
     if (nev < 1 || nev > n) return -3;
     if (!lambda) return -4;
     if (Q && ldq < n) return -6;
@@ -62,10 +73,10 @@ extern "C" int skew_tridiag_eig_noalloc(int n, const double* alpha, int nev, dou
     const size_t qbytes = Q ? align_up(sizeof(double) * (size_t)n * nev) : 0;
     const size_t tbytes = tridiag_ws(n, nev);
     if (qbytes + tbytes > (size_t)SKEW_NOALLOC_SCRATCH_BYTES) return SKEW_ERR_WORKSPACE;
-    void* base = nullptr;
-    int rc = scratch_address(&base);
-    if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* base = nullptr;
+    int rc = scratch_address(st, &base);
+    if (rc) return rc;
     Carve cv(base, SKEW_NOALLOC_SCRATCH_BYTES);
     double* Qi = Q ? cv.take<double>((size_t)n * nev) : nullptr;
     void* tws = cv.take<char>(tbytes);

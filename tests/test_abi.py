@@ -104,7 +104,31 @@ def test_kernel_timing_switch_is_host_side(sk):
     # no records yet: an empty timeline; a negative capacity is an argument error
     assert sk.kernel_timeline() == []
     assert L.skew_kernel_timeline(-1, None, None, None) == -1
+    assert L.skew_kernel_timing_dropped() == 0
     assert L.skew_kernel_timing(0) == 0
+
+
+def test_nomem_fault_fails_before_any_allocation(sk):
+    # SKEW_FAULT_NOMEM: the allocating entry points report SKEW_ERR_NOMEM
+    # before they touch the GPU, so this runs without one
+    L = sk.lib()
+    n, nev = 8, 4
+    A = (ctypes.c_double * (n * n))()
+    lam = (ctypes.c_double * nev)()
+    Zr = (ctypes.c_double * (n * nev))()
+    Zi = (ctypes.c_double * (n * nev))()
+    o = sk.Options(fault=sk.SKEW_FAULT_NOMEM).c()
+    nul = ctypes.c_void_p(0)
+    assert L.skew_eig_host(n, A, n, nev, lam, Zr, Zi, ctypes.byref(o), nul) == sk.SKEW_ERR_NOMEM
+    IA = ctypes.c_int * 2
+    PA = ctypes.c_void_p * 2
+    fake = PA(16, 16)
+    assert L.skew_eig_batched(2, IA(4, 4), fake, IA(4, 4), IA(1, 1), fake, fake, fake, ctypes.byref(o),
+                              nul) == sk.SKEW_ERR_NOMEM
+    # argument errors still come first
+    assert L.skew_eig_host(n, A, n - 1, nev, lam, Zr, Zi, ctypes.byref(o), nul) == -3
+    # releasing the (empty) pools is a no-op without a GPU
+    L.skew_release_memory()
 
 
 def test_batched_argument_checks_are_host_side(sk):

@@ -261,10 +261,79 @@ def test_failure_paths_report_status():
     # INT8 Ozaki mode: tcgen05 kind::i8 is not available on sm_103a
     opts = sk.Options(mode=sk.SKEW_MODE_MIXED_INT8)
     assert sk.skew_eig_ex(dA, nev, lam, Zr, Zi, ws, info, opts) == sk.SKEW_ERR_UNSUPPORTED
+    # allocation failure injected on the host
+    with pytest.raises(sk.SkewError) as e:
+        sk.skew_eig_host(torch.from_numpy(np.asfortranarray(A)), nev, opts=sk.Options(fault=sk.SKEW_FAULT_NOMEM))
+    assert e.value.code == sk.SKEW_ERR_NOMEM
     # the context is still usable afterwards
     lam2, X2, Y2 = gpu_solve(A, nev)
     m = oracle.scaled_metrics(A, lam2, X2, Y2)
     assert m["resid"] <= 50 and m["orth"] <= 50
+
+
+@pytest.mark.parametrize("mode", ["fp64", "refined"])
+def test_capped_waits_time_out_and_the_context_survives(mode):
+    # SKEW_FAULT_TINY_WAIT caps the waits between CTAs (the panel QR's grid
+    # barrier, the chase's wait on the previous sweep) at one poll, so waits
+    # that are not satisfied at once give up: the kernels record
+    # SKEW_ERR_DEVICE_TIMEOUT, every CTA returns, the later kernels run on
+    # whatever data there is, and the status reaches d_info.  A normal solve
+    # right after must still be correct.
+    import paper_1912_04062_gb300 as sk
+    torch = _torch()
+    n, nev = 400, 200
+    A = inputs.prescribed(n, seed=21)[0]
+    dA = to_dev(A)
+    m = sk.SKEW_MODE_FP64 if mode == "fp64" else sk.SKEW_MODE_MIXED_REFINED
+    ws = torch.empty(sk.workspace_size(n, nev, sk.Options(mode=m)), dtype=torch.uint8, device="cuda")
+    lam = torch.empty(nev, dtype=torch.float64, device="cuda")
+    Zr, Zi = sk.fortran_empty(n, nev), sk.fortran_empty(n, nev)
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    opts = sk.Options(mode=m, fault=sk.SKEW_FAULT_TINY_WAIT | sk.SKEW_FAULT_NO_REFINE)
+    assert sk.skew_eig_ex(dA, nev, lam, Zr, Zi, ws, info, opts) == 0
+    torch.cuda.synchronize()
+    assert int(info.item()) == sk.SKEW_ERR_DEVICE_TIMEOUT
+    # the same workspace, default caps: a correct solve
+    assert sk.skew_eig_ex(dA, nev, lam, Zr, Zi, ws, info, sk.Options(mode=m)) == 0
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    mm = oracle.scaled_metrics(A, lam.cpu().numpy(), Zr.cpu().numpy(), Zi.cpu().numpy())
+    assert mm["resid"] <= 50 and mm["orth"] <= 50
+
+
+def test_kernel_timing_folds_every_solve():
+    # per-kind kernel timing over many profiled solves: records are folded into
+    # the totals after each solve, so more launches than the 16384-record pool
+    # are all counted (nothing dropped) and the totals are additive
+    import paper_1912_04062_gb300 as sk
+    torch = _torch()
+    n, nev = 384, 192
+    A = to_dev(inputs.random_skew(n, seed=31))
+    opts = sk.Options()
+    ws = torch.empty(sk.workspace_size(n, nev, opts), dtype=torch.uint8, device="cuda")
+    lam = torch.empty(nev, dtype=torch.float64, device="cuda")
+    Zr, Zi = sk.fortran_empty(n, nev), sk.fortran_empty(n, nev)
+    sk.kernel_timing(True)
+    code, st = sk.skew_eig_profile(A, nev, lam, Zr, Zi, ws, opts)
+    assert code == 0
+    one = [sk.kernel_timing_read(k)[2] for k in range(len(sk.KERNEL_KINDS))]
+    per = sum(one)
+    assert per > 0
+    reps = min(400, 16384 // per + 2)
+    sk.kernel_timing(True)
+    stage = 0.0
+    for _ in range(reps):
+        code, st = sk.skew_eig_profile(A, nev, lam, Zr, Zi, ws, opts)
+        assert code == 0
+        stage += sum(st.values())
+    got = [sk.kernel_timing_read(k) for k in range(len(sk.KERNEL_KINDS))]
+    assert sk.lib().skew_kernel_timing_dropped() == 0
+    assert [g[2] for g in got] == [reps * c for c in one]
+    ms = sum(g[0] for g in got)
+    assert 0.3 * stage <= ms <= 1.5 * stage, (ms, stage)
+    # the timeline holds the records of the last profiled solve
+    assert len(sk.kernel_timeline()) == per
+    sk.kernel_timing(False)
 
 
 def test_device_metrics_match_definitions():
