@@ -6,12 +6,17 @@ Workload (one "step"): the BSE-shaped skew matrix of order n = 16384
 eigenpairs, solved through the C ABI (``skew_eig_profile`` = ``skew_eig_ex``
 plus per-stage CUDA events on the solve stream), inputs resident in HBM.
 A is 2.1 GB, far larger than the 129 MB L2, so no L2 flush is needed between
-steps.  ``e2e`` repeats the solve through ``skew_eig_host`` (pinned host
-buffers, host<->device copies inside the timed region).
+steps.  Per-launch kernel times come from CUDA events the library records on
+the launching streams during the timed steps; the roofline entry is the
+dominant kernel kind against the peak of its own arithmetic.  Accuracy (all
+columns, FP64 products) and the FP64 form's solve are measured after the timed
+region.  ``e2e`` repeats the solve through ``skew_eig_host`` (pinned host
+buffers, host<->device copies inside each call; one warm-up call first).
 
-``--impl reference`` times the FP64 CPU oracle (unblocked, single thread) on a
-bounded sample of the same workload (the same construction at order
---cpu-n) and scales it to order n by n^3.
+``cpu_baseline`` times the FP64 CPU oracle on all host cores on a bounded
+sample (the same construction at order --cpu-n, scaled to n by n^3), with
+the paper's comparison route (complex Hermitian LAPACK on iA) beside it.
+``--impl reference`` times the same oracle, one --ref-n sample per step.
 
 Multi-GPU: a single solve does not shard (the panel loop is sequential), so
 ``--gpus N`` under torchrun runs N independent replicas (one matrix per rank,
@@ -34,26 +39,123 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "n=16384 skew eigensolve time (nev=n/2): mixed+refined vs FP64 form, equal resid"
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz
+# Derived ALU peaks (unit counts x clock, GB300: 152 SMs at up to 2070 MHz):
+# FP64 2 FMA/clk/SM (the FP64 pipe is 1/64 of FP32), FP32 128 FMA/clk/SM.
+SM_COUNT, SM_MHZ = 152, 2070.0
+FP64_PEAK_TFLOPS = 2 * 2 * SM_COUNT * SM_MHZ * 1e6 / 1e12
+FP32_PEAK_TFLOPS = 2 * 128 * SM_COUNT * SM_MHZ * 1e6 / 1e12
 
 
 def _peaks():
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
-            return json.load(f)
+            d = json.load(f)
+        d["source"] = "of measured"
+        return d
     except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "of fallback"}
 
 
 PEAKS = _peaks()
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel from an ncu capture of the current kernel source; None when
-# the kernel changed after the capture.  ozaki_refine: 2.34 GB for a
-# 4096^3 product (profiles/ozaki_gemm_kernel_4096cube.md), scaled by the tiles x K
-# it processes to the refinement's n = 16384 launches (x64 for a full product,
-# half for the lower-triangle ones: two of each per iteration -> x48).
-TRAFFIC = {"ozaki_refine": 2.34e9 * 48, "ozaki_reduce": None, "split": None}
+
+# Kernel kinds of the library's per-launch timing (skew_kernel_timing) and what
+# bounds them.  "tensor": BF16 tcgen05 products, algorithmic flops = 2 M N K
+# per kept slice (or plane) product over the outputs written (reported by the
+# library per launch); "fp64" / "fp32": SIMT ALU work with the algorithmic
+# flops of one solve given by kind_flops().
+KIND_KERNELS = {
+    "ozaki_refine": ("tensor", "ozaki_gemm_kernel (refinement products, n x n x n)"),
+    "ozaki_product": ("tensor", "ozaki_gemm_kernel (band-reduction and Q_band products)"),
+    "split_product": ("tensor", "umma_gemm_kernel (BF16 plane products)"),
+    "gemm_f64": ("fp64", "gemm_kernel / lower_tiles_kernel (FP64 SYMM, rank-2k update, Q_band)"),
+    "qtrd": (None, None),  # by form: FP32 qtrd_slide_kernel (mixed) or FP64 qtrd_smem_kernel<double>
+    "chase": ("fp64", "chase_kernel"),
+    "panel_qr": ("fp64", "panel_qr_kernel"),
+}
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel from an ncu capture, valid while the kernel's source file is the one
+# captured (sha256 prefix); otherwise the traffic is reported as null.
+# ozaki_refine: one 4096^3 product (8 slices) read + wrote 2.34e9 B; an
+# n = 16384 refinement launch covers 64x the tiles x K of a full product (32x
+# for a lower-triangle one; two of each per iteration: x48 on average).
+TRAFFIC = {
+    "ozaki_refine": {"bytes": 2.34e9 * 48, "n": 16384, "file": "paper_1912_04062_gb300/csrc/ozaki_gemm.cu",
+                     "sha256_16": None,
+                     "how": "ncu capture of a 4096^3 product scaled by tiles x K (x48)"},
+}
+
+
+def _sha16(rel):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def kind_flops(kind, form, n, nev, b=64):
+    """Algorithmic flops of one solve for the kinds whose launches do not
+    carry them (SURVEY-style counts: Q_trd 4 n^2 nev, the FP64 form's
+    GEMM-type work 4/3 n^3 + 4 n^2 nev, the chase about 6 b n^2, the panel
+    QRs about b n^2); None where no count is defined."""
+    if kind == "qtrd":
+        return 4.0 * n * n * nev
+    if kind == "gemm_f64":
+        return 4.0 / 3.0 * n ** 3 + 4.0 * n * n * nev if form == "fp64" else None
+    if kind == "chase":
+        return 6.0 * b * n * n
+    if kind == "panel_qr":
+        return float(b) * n * n
+    return None
+
+
+def select_roofline(kinds, form, n, nev, solves, peaks=None, traffic=None):
+    """Roofline entry of the dominant kernel kind.
+
+    kinds: kind -> (total ms, total flops reported by the library, launches)
+    over `solves` solves.  The dominant kind is the one with the most kernel
+    time among those with a defined arithmetic; its achieved rate is its
+    algorithmic flops over its event-measured time, against the peak of its
+    own arithmetic: sustained BF16 (measured) for the tensor-core products,
+    the derived FP32 or FP64 ALU peak for SIMT kernels."""
+    peaks = peaks or PEAKS
+    per_ms = {k: v[0] / solves for k, v in kinds.items()}
+    order = sorted(per_ms, key=per_ms.get, reverse=True)
+    for k in order:
+        if k not in KIND_KERNELS or per_ms[k] <= 0:
+            continue
+        arith, name = KIND_KERNELS[k]
+        if k == "qtrd":
+            arith = "fp32" if form == "mixed" else "fp64"
+            name = "qtrd_slide_kernel (FP32)" if form == "mixed" else "qtrd_smem_kernel<double> (FP64)"
+        if arith == "tensor":
+            fl = kinds[k][1] / solves
+            peak, bound = peaks["bf16_tflops_sustained"], "tensor"
+            note = f"{peaks.get('source', 'of measured')}: cuBLAS bf16 sustained (kernel timed inside a long step)"
+        else:
+            fl = kind_flops(k, form, n, nev)
+            if fl is None:
+                continue
+            peak = FP32_PEAK_TFLOPS if arith == "fp32" else FP64_PEAK_TFLOPS
+            bound = "alu"
+            note = (f"derived {arith.upper()} ALU peak: "
+                    f"{'128' if arith == 'fp32' else '2'} FMA/clk/SM x {SM_COUNT} SMs x {SM_MHZ:.0f} MHz")
+        launches = kinds[k][2] / solves
+        ms = per_ms[k]
+        achieved = fl / (ms * 1e-3) / 1e12
+        tr = None
+        t = (traffic if traffic is not None else TRAFFIC).get(k)
+        if t and t.get("n") == n and t.get("sha256_16") and t["sha256_16"] == _sha16(t["file"]):
+            tr = t["bytes"]
+        return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": tr, "kernel": name, "kind": k, "launches_per_solve": launches,
+                "avg_launch_ms": ms / max(launches, 1e-9), "kernel_ms_per_solve": ms,
+                "flops_per_solve": fl, "peak_note": note,
+                "dominant_kind_overall": order[0] if order else None}
+    return None
 
 
 def parse():
@@ -64,12 +166,18 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--nev", type=int, default=0)
-    p.add_argument("--cpu-n", type=int, default=2048)
-    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--cpu-n", type=int, default=4096,
+                   help="order of the CPU baseline's sample (the same BSE construction), scaled to n by n^3")
+    p.add_argument("--ref-n", type=int, default=2048,
+                   help="order of the reference arm's per-step sample (the oracle on the host cores)")
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--accuracy", default="full", choices=["full", "sampled"],
+                   help="full: residual and orthogonality over all nev columns (FP64 products, outside the "
+                        "timed region); sampled: --sample-cols columns, scaled")
     p.add_argument("--sample-cols", type=int, default=128)
     p.add_argument("--form", default="mixed", choices=["mixed", "fp64"],
-                   help="mixed: BF16x6 tensor-core contractions + FP64 refinement; fp64: every step FP64")
+                   help="mixed: digit-slice tensor-core contractions + FP64 refinement; fp64: every step FP64")
     p.add_argument("--fp64-compare", type=int, default=1,
                    help="also time this many solves of the FP64 form (reported beside the mixed form)")
     p.add_argument("--workload", default="single", choices=["single", "batched", "gemm"],
@@ -173,40 +281,113 @@ def summarize_clocks(lines):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample(n_cpu: int, n_full: int, seed: int = 3):
-    """Time the oracle on the same construction at order n_cpu; scale by n^3."""
+def cpu_sample(n_cpu: int, n_full: int, seed: int = 3, lapack: bool = True):
+    """The FP64 oracle (all host cores) on the same construction at order
+    n_cpu, and the paper's comparison route -- the complex Hermitian solve of
+    iA for the nev largest eigenvalues and their vectors (LAPACK through
+    scipy) -- at the same order; both scaled to order n_full by n^3."""
     import inputs
     import oracle
     A = inputs.bse(n_cpu, seed=seed)
     oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
     t0 = time.perf_counter()
     lam, X, Y, info = oracle.skew_eig(A, n_cpu // 2)
     dt = time.perf_counter() - t0
     scale = (n_full / n_cpu) ** 3
-    return dt, dt * scale, scale
+    out = {"oracle_s": dt, "scale": scale, "cores": cores, "n": n_cpu}
+    if lapack:
+        import scipy.linalg as sla
+        t0 = time.perf_counter()
+        w, _ = sla.eigh(1j * A, subset_by_index=[n_cpu - n_cpu // 2, n_cpu - 1])
+        out["lapack_s"] = time.perf_counter() - t0
+        out["lapack_lambda_diff_rel"] = float(np.max(np.abs(np.sort(w)[::-1] - lam)) / lam[0])
+    return out
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the FP64 oracle (unblocked Householder
+    tridiagonalisation, bisection, inverse iteration, back-transformation) on
+    the host cores, each step one solve of the BSE construction at --ref-n
+    scaled to order n by n^3.  Under torchrun only rank 0 runs."""
     if rank != 0:
         return
     n = args.n
     for _ in range(args.warmup):
-        cpu_sample(args.cpu_n, n)
-    times = []
+        cpu_sample(args.ref_n, n, lapack=False)
+    times, cores = [], 1
     for _ in range(args.steps):
-        dt, scaled, scale = cpu_sample(args.cpu_n, n)
-        times.append(scaled)
+        r = cpu_sample(args.ref_n, n, lapack=False)
+        times.append(r["oracle_s"] * r["scale"])
+        cores = r["cores"]
     v = float(np.mean(times))
-    sample = (f"oracle.skew_eig (unblocked FP64 C, 1 thread) on the BSE construction at n={args.cpu_n}, "
-              f"nev={args.cpu_n // 2}; time x (n/{args.cpu_n})^3 = x{scale:.0f}")
+    sample = (f"oracle.skew_eig (unblocked FP64 C, OpenMP over its level-2 loops, {cores} threads) on the "
+              f"BSE construction at n={args.ref_n}, nev={args.ref_n // 2}; time x (n/{args.ref_n})^3 = "
+              f"x{(n / args.ref_n) ** 3:.0f}")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"BSE-shaped skew n={n} nev={n // 2}, FP64 CPU oracle (sampled)",
                       "n": n, "nev": n // 2, "parallelism": "replicas"},
-           "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def _accuracy(sk, A, lam, Zr, Zi, n, nev, mode, sample_cols):
+    """Scaled residual and orthogonality (Algorithm 1 "Ensure") on the device
+    with FP64 products: over all nev columns, or over a column sample scaled
+    to all columns."""
+    eps = np.finfo(np.float64).eps
+    if mode == "full":
+        res, orth, fro = sk.metrics(A, lam, Zr, Zi)
+        cols = nev
+        f = 1.0
+    else:
+        rng = np.random.default_rng(0)
+        c = np.sort(rng.choice(nev, size=min(sample_cols, nev), replace=False)).astype(np.int32)
+        res, orth, fro = sk.metrics(A, lam, Zr, Zi, cols=c)
+        cols = len(c)
+        f = np.sqrt(nev / cols)
+    return {"resid_scaled": res * f / (n * eps * fro), "orth_scaled": orth * f / (n * eps), "columns": int(cols),
+            "lambda_max": float(lam.max().item()), "lambda_min": float(lam.min().item())}
+
+
+def _oracle_golden(n, seed):
+    """The oracle's stored eigenvalues of the BSE workload (written on the CPU
+    by tests/golden/make_bse16384_golden.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"bse{n}_seed{seed}.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return np.asarray(d["lambda"], dtype=np.float64)
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def _timed_solves(sk, torch, A, nev, lam, Zr, Zi, work, opts, stream, steps, ws):
+    """steps profiled solves with per-launch kernel timing on; returns
+    (ms per solve over the whole region, stage ms per solve, kinds, launches)."""
+    stage_tot = {k: 0.0 for k in sk.STAGES}
+    sk.kernel_timing(True)
+    l0 = sk.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        code, st = sk.skew_eig_profile(A, nev, lam, Zr, Zi, work, opts)
+        if code != 0:
+            raise RuntimeError(f"solve failed: {code} {sk.strerror(code)}")
+        for k, v in st.items():
+            stage_tot[k] += v
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = sk.launch_count() - l0
+    kinds = {name: sk.kernel_timing_read(i) for i, name in enumerate(sk.KERNEL_KINDS)}
+    sk.kernel_timing(False)
+    ms = e0.elapsed_time(e1) / steps
+    return ms, {k: v / steps for k, v in stage_tot.items()}, kinds, launches
 
 
 def run_ours(args, ws, rank, local):
@@ -218,10 +399,11 @@ def run_ours(args, ws, rank, local):
     sk.lib()
     n = args.n
     nev = args.nev or n // 2
+    seed = 3 + rank
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    A = inputs.bse_device(n, seed=3 + rank, device=dev)
+    A = inputs.bse_device(n, seed=seed, device=dev)
     torch.cuda.synchronize()
 
     mixed = args.form == "mixed"
@@ -236,46 +418,17 @@ def run_ours(args, ws, rank, local):
         if code not in (0,):
             raise RuntimeError(f"warm-up solve failed: {code} {sk.strerror(code)}")
 
-    stage_tot = {k: 0.0 for k in sk.STAGES}
     clk = ClockSampler(local)
-    barrier(ws)
-    torch.cuda.synchronize()
     clk.start()
-    l0 = sk.launch_count()
-    # per-launch CUDA events around the tensor-core product kernels (recorded
-    # by the library on the solve stream)
-    sk.kernel_timing(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        code, st = sk.skew_eig_profile(A, nev, lam, Zr, Zi, work, opts)
-        if code != 0:
-            raise RuntimeError(f"solve failed: {code} {sk.strerror(code)}")
-        for k, v in st.items():
-            stage_tot[k] += v
-    e1.record(stream)
-    torch.cuda.synchronize()
-    launches = sk.launch_count() - l0
-    kinds = {name: sk.kernel_timing_read(i) for i, name in enumerate(sk.KERNEL_KINDS)}
-    ktime = {"ozaki_refine": kinds["ozaki_refine"], "ozaki_reduce": kinds["ozaki_product"],
-             "split": kinds["split_product"]}
-    sk.kernel_timing(False)
+    ms, stage_ms, kinds, launches = _timed_solves(sk, torch, A, nev, lam, Zr, Zi, work, opts, stream, args.steps, ws)
     clocks = clk.stop()
     barrier(ws)
-    ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ws, ms)
-    stage_ms = {k: v / args.steps for k, v in stage_tot.items()}
+    form = "mixed" if mixed else "fp64"
+    roof = select_roofline(kinds, form, n, nev, args.steps)
 
-    # ---- accuracy on sampled columns (device metrics kernels)
-    rng = np.random.default_rng(0)
-    cols = np.sort(rng.choice(nev, size=min(args.sample_cols, nev), replace=False)).astype(np.int32)
-    res, orth, fro = sk.metrics(A, lam, Zr, Zi, cols=cols)
-    eps = np.finfo(np.float64).eps
-    # sampled Frobenius norms scaled to the full set of columns
-    f = np.sqrt(nev / len(cols))
-    acc = {"resid_scaled": res * f / (n * eps * fro), "orth_scaled": orth * f / (n * eps),
-           "sampled_cols": int(len(cols)), "lambda_max": float(lam.max().item()),
-           "lambda_min": float(lam.min().item())}
+    # ---- accuracy (outside the timed region)
+    acc = _accuracy(sk, A, lam, Zr, Zi, n, nev, args.accuracy, args.sample_cols)
     if mixed:
         it, em, nc = sk.refine_stats()
         sl, su = sk.refine_slices()
@@ -283,7 +436,10 @@ def run_ours(args, ws, rank, local):
         acc["refine_max_correction"] = em
         acc["refine_slices"] = sl
         acc["refine_update_slices"] = su
-        lam_mixed = lam.clone()
+    gold = _oracle_golden(n, seed) if nev == n // 2 else None
+    if gold is not None:
+        acc["lambda_err_vs_oracle_rel"] = float(np.max(np.abs(lam.cpu().numpy() - gold)) / gold[0])
+    lam_main = lam.clone()
     del work
     torch.cuda.empty_cache()
 
@@ -293,61 +449,26 @@ def run_ours(args, ws, rank, local):
         o64 = sk.Options(mode=sk.SKEW_MODE_FP64)
         w64 = torch.empty(sk.workspace_size(n, nev, o64), dtype=torch.uint8, device=dev)
         l64 = torch.empty(nev, dtype=torch.float64, device=dev)
-        Xr64, Xi64 = sk.fortran_empty(n, nev, dev), sk.fortran_empty(n, nev, dev)
-        times = []
-        for _ in range(args.fp64_compare):
-            torch.cuda.synchronize()
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            code, st64 = sk.skew_eig_profile(A, nev, l64, Xr64, Xi64, w64, o64)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            if code != 0:
-                raise RuntimeError(f"FP64-form solve failed: {code}")
-            times.append(a0.elapsed_time(a1) / 1e3)
-        r64, o64n, _ = sk.metrics(A, l64, Xr64, Xi64, cols=cols)
-        fp64 = {"s": float(np.median(times)), "solves": len(times),
-                "resid_scaled": r64 * f / (n * eps * fro), "orth_scaled": o64n * f / (n * eps),
-                "max_lambda_diff_vs_mixed_rel": float(((l64 - lam_mixed).abs().max() / l64.abs().max()).item()),
+        X64, Y64 = sk.fortran_empty(n, nev, dev), sk.fortran_empty(n, nev, dev)
+        ms64, st64, kinds64, _ = _timed_solves(sk, torch, A, nev, l64, X64, Y64, w64, o64, stream,
+                                               args.fp64_compare, ws)
+        acc64 = _accuracy(sk, A, l64, X64, Y64, n, nev, args.accuracy, args.sample_cols)
+        fp64 = {"s": ms64 / 1e3, "solves": args.fp64_compare,
+                "resid_scaled": acc64["resid_scaled"], "orth_scaled": acc64["orth_scaled"],
+                "columns": acc64["columns"],
+                "max_lambda_diff_vs_mixed_rel": float(((l64 - lam_main).abs().max() / l64.abs().max()).item()),
                 "stages_ms": {k: round(v, 3) for k, v in st64.items()},
-                "speedup_mixed_over_fp64": float(np.median(times)) / (ms / 1e3)}
-        del w64, Xr64, Xi64
+                "kernels_ms_per_solve": {k: round(v[0] / args.fp64_compare, 3) for k, v in kinds64.items()},
+                "roofline": select_roofline(kinds64, "fp64", n, nev, args.fp64_compare),
+                "speedup_mixed_over_fp64": (ms64 / 1e3) / (ms / 1e3)}
+        if gold is not None:
+            fp64["lambda_err_vs_oracle_rel"] = float(np.max(np.abs(l64.cpu().numpy() - gold)) / gold[0])
+        del w64, X64, Y64
         torch.cuda.empty_cache()
-
-    # ---- roofline of the dominant kernel
-    # FP64 form: the single-launch stage kernels (time = stage time), FP64 ALU
-    # bound.  Mixed form: the tensor-core product kernels, timed per launch by
-    # CUDA events on the solve stream; algorithmic flops = 2 M N K per kept
-    # BF16 slice product over the outputs written.
-    F = {"band_reduce": 4.0 / 3.0 * n ** 3, "qtrd": 4.0 * n * n * nev, "qband": 4.0 * n * n * nev,
-         "chase": 12.0 * 64 * 64 * (n * n / (2 * 64))}
-    kern = {"band_reduce": "panel_qr_kernel + skew SYMM/rank-2k gemm_kernel/lower_tiles_kernel",
-            "qtrd": "qtrd_smem_kernel<double> (1 launch per solve)", "qband": "gemm_kernel (3 per panel)",
-            "chase": "chase_kernel (1 launch per solve)"}
-    kt_ms = {k: v[0] / args.steps for k, v in ktime.items()}
-    single = {k: stage_ms[k] for k in ("qtrd", "chase")}
-    if mixed and max(kt_ms.values()) > max(single.values()):
-        top = max(kt_ms, key=kt_ms.get)
-        tms, tfl, tl = ktime[top]
-        achieved = tfl / (tms * 1e-3) / 1e12
-        name = {"ozaki_refine": "ozaki_gemm_kernel (refinement products, n x n x n)",
-                "ozaki_reduce": "ozaki_gemm_kernel (band-reduction and Q_band products)",
-                "split": "umma_gemm_kernel (BF16 split products)"}[top]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": PEAKS["bf16_tflops_sustained"],
-                "unit": "TFLOP/s", "frac": achieved / PEAKS["bf16_tflops_sustained"],
-                "traffic": TRAFFIC.get(top) if n == 16384 else None, "kernel": name, "launches_per_step": tl / args.steps,
-                "avg_launch_ms": tms / tl, "kernel_ms_per_step": tms / args.steps,
-                "peak_note": "of measured: cuBLAS bf16 sustained (kernel timed inside a long step)",
-                "other_kernels_ms_per_step": {k: round(v, 3) for k, v in kt_ms.items() if k != top}}
-    else:
-        top = max(single, key=single.get) if mixed else max(F, key=lambda k: stage_ms[k])
-        achieved = F[top] / (stage_ms[top] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kern[top], "stage": top,
-                "peak_note": "FP64 ALU: 2 FMA/clk/SM x 152 SMs x 2070 MHz (derived; FFMA64 loop measured 1.008)"}
     total_F = 4.0 / 3.0 * n ** 3 + 8.0 * nev * n * n
 
-    # ---- end to end through the host-buffer entry point
+    # ---- end to end through the host-buffer entry point (pinned host
+    # memory; the copies in and out are inside each call)
     e2e = None
     if args.e2e_steps > 0:
         hA = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
@@ -355,30 +476,47 @@ def run_ours(args, ws, rank, local):
         hl = torch.empty(nev, dtype=torch.float64, pin_memory=True)
         hZr = torch.empty((nev, n), dtype=torch.float64, pin_memory=True).t()
         hZi = torch.empty((nev, n), dtype=torch.float64, pin_memory=True).t()
+        del A, Zr, Zi
+        torch.cuda.empty_cache()
         L = sk.lib()
-        torch.cuda.synchronize()
-        barrier(ws)
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            oc = opts.c()
+        oc = opts.c()
+
+        def host_solve():
             code = L.skew_eig_host(n, sk._ptr(hA), n, nev, sk._ptr(hl), sk._ptr(hZr), sk._ptr(hZi),
                                    sk.ctypes.byref(oc), sk._stream(stream))
             if code != 0:
                 raise RuntimeError(f"host solve failed: {code}")
+
+        host_solve()  # warm-up: the library pool reserves the workspace once
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            host_solve()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         e2e_s = max_over_ranks(ws, e2e_s)
+        sk.lib().skew_release_memory()
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n * n,
-               "d2h_bytes_per_step": 8 * (nev + 2 * n * nev), "entry": "skew_eig_host"}
+               "d2h_bytes_per_step": 8 * (nev + 2 * n * nev), "entry": "skew_eig_host",
+               "calls": args.e2e_steps, "warmup_calls": 1}
 
     cpu = None
     if rank == 0 and not args.no_cpu and ws == 1:
-        dt, scaled, scale = cpu_sample(args.cpu_n, n)
-        cpu = {"value": scaled, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": (f"oracle.skew_eig (unblocked FP64 C, 1 thread) on the BSE construction at "
-                          f"n={args.cpu_n}, nev={args.cpu_n // 2}: {dt:.2f} s, x (n/{args.cpu_n})^3 = x{scale:.0f}")}
+        r = cpu_sample(args.cpu_n, n)
+        cpu = {"value": r["oracle_s"] * r["scale"], "unit": "s", "cores": r["cores"], "kind": "oracle",
+               "sample": (f"oracle.skew_eig (unblocked FP64 C, OpenMP over its level-2 loops, {r['cores']} threads) "
+                          f"on the BSE construction at n={args.cpu_n}, nev={args.cpu_n // 2}: {r['oracle_s']:.2f} s, "
+                          f"x (n/{args.cpu_n})^3 = x{r['scale']:.0f}"),
+               "lapack_complex_route": {
+                   "value": r["lapack_s"] * r["scale"], "unit": "s", "cores": os.cpu_count(),
+                   "sample": (f"scipy.linalg.eigh(1j*A, subset_by_index=[n/2, n-1]) (complex Hermitian LAPACK, "
+                              f"the paper's comparison method) at n={args.cpu_n}: {r['lapack_s']:.2f} s, "
+                              f"x{r['scale']:.0f}"),
+                   "lambda_diff_vs_oracle_rel": r["lapack_lambda_diff_rel"]}}
 
     if rank == 0:
+        kms = {k: round(v[0] / args.steps, 3) for k, v in kinds.items()}
         out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -392,7 +530,8 @@ def run_ours(args, ws, rank, local):
                           "l2": "inputs larger than L2 (A = %.1f GB)" % (8 * n * n / 1e9),
                           "parallelism": "replicas" if ws > 1 else "single"},
                "tflops_nominal": total_F / (ms * 1e-3) / 1e12,
-               "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kinds.items()},
+               "kernels_ms_per_step": kms,
+               "kernels_sum_over_step": sum(kms.values()) / ms,
                "stages_ms": {k: round(v, 3) for k, v in stage_ms.items()},
                "accuracy": acc, "fp64_form": fp64, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clocks}

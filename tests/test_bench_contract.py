@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_json_line():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
-                        "--cpu-n", "96"], cwd=ROOT, capture_output=True, text=True, timeout=120)
+                        "--ref-n", "96"], cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     assert len(lines) == 1
@@ -26,6 +26,7 @@ def test_reference_arm_json_line():
     assert "workload" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert f"{cb['cores']} threads" in cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
@@ -85,3 +86,51 @@ def test_max_over_ranks_two_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res == [(0, 17.5), (1, 17.5)]
+
+
+def _kinds(**ms):
+    # kind -> (total ms, total flops, launches) with the library's kind names
+    import bench  # noqa: F401
+    names = ["ozaki_product", "split_product", "ozaki_refine", "slice_split", "panel_qr", "gemm_f64",
+             "chase", "bisect", "invit", "qtrd", "refine_aux", "other"]
+    out = {k: (0.0, 0.0, 0) for k in names}
+    out.update(ms)
+    return out
+
+
+def test_roofline_selection():
+    sys.path.insert(0, ROOT)
+    import bench
+    n, nev = 16384, 8192
+    peaks = {"bf16_tflops_sustained": 1674.1, "source": "of measured"}
+    # mixed step of two solves: the refinement products dominate -> tensor
+    # bound against the sustained BF16 peak, with the library's slice-pair flops
+    k = _kinds(ozaki_refine=(2 * 1900.0, 2 * 2.53e15, 24), qtrd=(2 * 436.0, 0.0, 2), chase=(2 * 351.0, 0.0, 2),
+               ozaki_product=(2 * 440.0, 2 * 3.0e14, 1000))
+    r = bench.select_roofline(k, "mixed", n, nev, 2, peaks)
+    assert r["kind"] == "ozaki_refine" and r["bound"] == "tensor" and r["peak"] == 1674.1
+    assert r["kernel"].startswith("ozaki_gemm_kernel")
+    assert abs(r["achieved"] - 2.53e15 / 1.9 / 1e12) < 1e-6 * r["achieved"]
+    assert 0.7 < r["frac"] < 0.85 and r["launches_per_solve"] == 12
+    # mixed, Q_trd dominant: the FP32 kernel that runs, against the FP32 peak
+    k = _kinds(qtrd=(436.0, 0.0, 1), ozaki_refine=(100.0, 1e14, 12))
+    r = bench.select_roofline(k, "mixed", n, nev, 1, peaks)
+    assert r["kernel"].startswith("qtrd_slide_kernel") and r["bound"] == "alu"
+    assert abs(r["peak"] - bench.FP32_PEAK_TFLOPS) < 1e-9 and r["frac"] < 1
+    # FP64 form: the FP64 Q_trd kernel against the FP64 ALU peak
+    k = _kinds(qtrd=(10390.0, 0.0, 1), gemm_f64=(9000.0, 0.0, 5000))
+    r = bench.select_roofline(k, "fp64", n, nev, 1, peaks)
+    assert r["kernel"].startswith("qtrd_smem_kernel<double>") and abs(r["peak"] - bench.FP64_PEAK_TFLOPS) < 1e-9
+    assert 0.5 < r["frac"] < 1
+    k = _kinds(qtrd=(10390.0, 0.0, 1), gemm_f64=(13500.0, 0.0, 5000))
+    r = bench.select_roofline(k, "fp64", n, nev, 1, peaks)
+    assert r["kind"] == "gemm_f64" and r["frac"] < 1
+    # a kind without a defined arithmetic never wins; the next one is taken
+    k = _kinds(other=(5000.0, 0.0, 10), ozaki_refine=(1000.0, 1.3e15, 12))
+    r = bench.select_roofline(k, "mixed", n, nev, 1, peaks)
+    assert r["kind"] == "ozaki_refine" and r["dominant_kind_overall"] == "other"
+    # traffic only while the captured kernel source is unchanged
+    t = {"ozaki_refine": {"bytes": 1e11, "n": n, "file": "bench.py", "sha256_16": "0" * 16}}
+    assert bench.select_roofline(k, "mixed", n, nev, 1, peaks, traffic=t)["traffic"] is None
+    t["ozaki_refine"]["sha256_16"] = bench._sha16("bench.py")
+    assert bench.select_roofline(k, "mixed", n, nev, 1, peaks, traffic=t)["traffic"] == 1e11
