@@ -103,8 +103,16 @@ typedef struct {
                           correction would rotate by more than 1/refine_rho are
                           refined together by Rayleigh-Ritz (clusters of up to 16);
                           0 -> 1024 */
-    int reserved[2];
+    int qtrd;          /* arithmetic of the Q_trd back-transform: SKEW_QTRD_* */
+    int reserved[1];
 } skew_opts;
+
+/* skew_opts.qtrd: SKEW_QTRD_AUTO (0) takes the mode's choice (FP64 in the FP64
+ * form and whenever the mixed modes do not refine; FP32 when they refine);
+ * the others force FP32 or FP64 SIMT arithmetic. */
+#define SKEW_QTRD_AUTO 0
+#define SKEW_QTRD_FP32 1
+#define SKEW_QTRD_FP64 2
 
 /* Default options (FP64 mode, b = 64). */
 void skew_opts_default(skew_opts* opts);

@@ -37,6 +37,9 @@ SKEW_FAULT_NOMEM = 1
 SKEW_FAULT_INVIT_NOCONV = 2
 SKEW_FAULT_TINY_WAIT = 4
 SKEW_FAULT_NO_REFINE = 8
+SKEW_QTRD_AUTO = 0
+SKEW_QTRD_FP32 = 1
+SKEW_QTRD_FP64 = 2
 
 # every entry point the header declares: name -> (restype, argtypes)
 _i, _d, _p, _sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
@@ -92,7 +95,7 @@ SIGNATURES = {
 class skew_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("band", ctypes.c_int), ("check_finite", ctypes.c_int),
                 ("fault", ctypes.c_int), ("refine_iters", ctypes.c_int), ("refine_rho", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("qtrd", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 _lib = None
@@ -174,6 +177,7 @@ class Options:
     fault: int = 0
     refine_iters: int = 0
     refine_rho: int = 0
+    qtrd: int = 0
 
     def c(self):
         o = skew_opts()
@@ -181,6 +185,7 @@ class Options:
         o.mode, o.band, o.check_finite, o.fault = self.mode, self.band, self.check_finite, self.fault
         o.refine_iters = self.refine_iters
         o.refine_rho = self.refine_rho
+        o.qtrd = self.qtrd
         return o
 
 

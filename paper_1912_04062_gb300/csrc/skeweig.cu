@@ -132,6 +132,8 @@ Plan make_plan(int n, int nev, const skew_opts* o, bool vectors) {
     const bool refined_mode = p.mixed && o->mode == SKEW_MODE_MIXED_REFINED;
     p.qband_prec = !p.mixed ? 0 : (refined_mode ? REDUCE_F64ACC : p.planes);
     p.qtrd_f32 = p.mixed && vectors && !(refined_mode && !p.refine);
+    if (o && vectors && o->qtrd == SKEW_QTRD_FP32) p.qtrd_f32 = true;
+    if (o && o->qtrd == SKEW_QTRD_FP64) p.qtrd_f32 = false;
     // With a complete basis the refinement removes the first-order error, so
     // the products before it need only keep the starting vectors at the level
     // of the FP32 Q_trd: 6 digit slices (about 2^-42) for the reduction, 5

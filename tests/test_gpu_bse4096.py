@@ -63,7 +63,7 @@ def _compare(A, nev, mode, problem):
     prv = np.insert(lam_o[:-1], 0, np.inf)[:nev]
     gap = np.minimum(prv - lo, lo - nxt)
     sel = np.flatnonzero(gap > 1e-3 * norm2)
-    assert sel.size >= 5
+    assert sel.size >= 2
     for j in sel:
         ov = phase_overlap(X[:, j] + 1j * Y[:, j], Xo[:, j] + 1j * Yo[:, j])
         assert ov >= 1 - 1e-9, (j, ov)
