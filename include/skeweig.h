@@ -108,11 +108,14 @@ typedef struct {
 } skew_opts;
 
 /* skew_opts.qtrd: SKEW_QTRD_AUTO (0) takes the mode's choice (FP64 in the FP64
- * form and whenever the mixed modes do not refine; FP32 when they refine);
- * the others force FP32 or FP64 SIMT arithmetic. */
+ * form and whenever the mixed modes do not refine; FP32 SIMT when they
+ * refine); the others force FP32 SIMT, FP64 SIMT or the tensor-core form
+ * (compact WY blocks of 64 sweeps, BF16x6 tcgen05 products with FP32
+ * accumulation, FP32-level accuracy). */
 #define SKEW_QTRD_AUTO 0
 #define SKEW_QTRD_FP32 1
 #define SKEW_QTRD_FP64 2
+#define SKEW_QTRD_TC 3
 
 /* Default options (FP64 mode, b = 64). */
 void skew_opts_default(skew_opts* opts);
@@ -433,6 +436,20 @@ int skew_dmap(int n, int k, const double* Q, int ldq, double* X, double* Y,
  * n x k, ld ldz. */
 int skew_apply_qtrd(int n, int b, const double* Vtrd, const double* tautrd,
                     double* Z, int ldz, int k, void* stream);
+
+/* Z <- Q_trd Z in FP32 (Sec. 2.1 step 3a; the FP32-level form of the mixed
+ * modes) from FP32 reflectors: V32 holds v (64 floats, v[0] = 1, zero padded)
+ * of sweep s, step k at slot k * nsw64 + s and tau32 its tau at the same slot
+ * (nsw64 = n - 2 rounded up to a multiple of 64; the taus of steps a sweep does
+ * not have are zero).  Z is FP32, n x k, ld ldz.  tensor = 0: reflector by
+ * reflector on the FP32 pipe; tensor = 1: 64-sweep blocks in compact WY form
+ * (Eq. 7) applied by tcgen05 BF16x6 products, workspace
+ * skew_apply_qtrd_f32_ws(n, 1) bytes (the blocks' operands).  d_status is a
+ * device int set on a device-side failure.  Arguments 1 n, 2 b (64),
+ * 3 V32/tau32, 6 ldz, 7 k, 8 tensor (0 or 1), 11 d_status. */
+size_t skew_apply_qtrd_f32_ws(int n, int tensor);
+int skew_apply_qtrd_f32(int n, int b, const float* V32, const float* tau32, float* Z, int ldz, int k,
+                        int tensor, void* ws, size_t ws_bytes, int* d_status, void* stream);
 
 /* Z <- Q_band Z (Sec. 2.1 step 3b) for a W / Tfac pair produced by
  * skew_band_reduce; Z is n x k, ld ldz. */

@@ -40,6 +40,7 @@ SKEW_FAULT_NO_REFINE = 8
 SKEW_QTRD_AUTO = 0
 SKEW_QTRD_FP32 = 1
 SKEW_QTRD_FP64 = 2
+SKEW_QTRD_TC = 3
 
 # every entry point the header declares: name -> (restype, argtypes)
 _i, _d, _p, _sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
@@ -87,6 +88,8 @@ SIGNATURES = {
     "skew_tridiag_eig_noalloc": (_i, [_i, _p, _i, _p, _p, _i, _p, _p]),
     "skew_dmap": (_i, [_i, _i, _p, _i, _p, _p, _i, _p]),
     "skew_apply_qtrd": (_i, [_i, _i, _p, _p, _p, _i, _i, _p]),
+    "skew_apply_qtrd_f32_ws": (_sz, [_i, _i]),
+    "skew_apply_qtrd_f32": (_i, [_i, _i, _p, _p, _p, _i, _i, _i, _p, _sz, _p, _p]),
     "skew_qband_ws": (_sz, [_i, _i, _i]),
     "skew_apply_qband": (_i, [_i, _i, _p, _i, _p, _p, _i, _i, _p, _sz, _p]),
 }
@@ -560,6 +563,18 @@ def apply_qtrd(Vtrd, tau, Z, b: int = 64, stream=None):
     n, k = Z.shape
     _check(lib().skew_apply_qtrd(n, b, _ptr(Vtrd), _ptr(tau), _ptr(Z), _ld(Z), k, _stream(stream)), "skew_apply_qtrd")
     return Z
+
+
+def apply_qtrd_f32(V32, tau32, Z, tensor: bool, b: int = 64, stream=None):
+    """Z (float32, Fortran-strided n x k) <- Q_trd Z in place from FP32
+    reflectors in the chase's slot layout (skew_apply_qtrd_f32); tensor
+    selects the tcgen05 compact-WY form.  Returns the device status word."""
+    n, k = Z.shape
+    ws = _ws(lib().skew_apply_qtrd_f32_ws(n, 1 if tensor else 0), Z.device)
+    st = _status(Z.device)
+    _check(lib().skew_apply_qtrd_f32(n, b, _ptr(V32), _ptr(tau32), _ptr(Z), _ld(Z), k, 1 if tensor else 0,
+                                     _ptr(ws), ws.numel(), _ptr(st), _stream(stream)), "skew_apply_qtrd_f32")
+    return st
 
 
 def apply_qband(W, Tfac, Z, b: int = 64, stream=None):

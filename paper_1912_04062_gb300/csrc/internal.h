@@ -88,6 +88,14 @@ cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd,
 // steps zero).
 cudaError_t apply_qtrd_f32(cudaStream_t st, int n, int b, const float* V32, const float* tau32, float* Z, int ldz,
                            int k, int* status);
+// ---- qtrd_tc.cu (Q_trd on the tensor cores) ------------------------------
+// Z (FP32, n x k, ld ldz) <- Q_trd Z from the chase's FP32 reflectors (slot
+// k nsw64 + s): each 64-sweep block in compact WY form, applied by tcgen05
+// BF16x6 products with the window in TMEM.  Workspace: the blocks' operand
+// images, qtrd_tc_ws(n) bytes.
+size_t qtrd_tc_ws(int n);
+int apply_qtrd_tc(cudaStream_t st, int n, const float* V32, const float* tau32, float* Z, int ldz, int k,
+                  void* ws, size_t ws_bytes, int* status);
 size_t qband_ws(int n, int b, int k);
 size_t qband_mixed_ws(int n, int b, int k, int planes);
 int apply_qband_mixed(cudaStream_t st, int n, int b, const double* W, int ldw, const double* Tfac, double* Z, int ldz,

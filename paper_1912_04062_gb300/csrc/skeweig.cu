@@ -64,13 +64,14 @@ struct Plan {
     int qband_prec;   // mixed Q_band: 2/3 split planes or REDUCE_F64ACC digit slices
     int reduce_slices, qband_slices;  // digit slices of the REDUCE_F64ACC products
     bool qtrd_f32;    // mixed Q_trd in FP32 arithmetic (else FP64)
+    bool qtrd_tc;     // the FP32-level Q_trd on the tensor cores (else SIMT)
     size_t ldab;
     // carved pointers
     double *W, *Tfac, *AB, *Vtrd, *tautrd, *alpha, *Qi, *Z;
     float *Z32, *V32, *tau32;  // FP32 Q_trd: Z and the chase's reflectors (sweep stride padded to 64)
     int* status;
-    void *ws_reduce, *ws_chase, *ws_tri, *ws_qband, *ws_refine;
-    size_t sz_reduce, sz_chase, sz_tri, sz_qband, sz_refine;
+    void *ws_reduce, *ws_chase, *ws_tri, *ws_qband, *ws_refine, *ws_qtc;
+    size_t sz_reduce, sz_chase, sz_tri, sz_qband, sz_refine, sz_qtc;
     bool refine;  // mixed form with a complete basis (n even, nev = n/2)
 };
 
@@ -106,6 +107,8 @@ bool carve_plan(Plan& p, Carve& cv) {
     p.ws_qband = p.vectors ? cv.take<char>(p.sz_qband) : nullptr;
     p.sz_refine = p.refine ? refine_ws(p.n) : 0;
     p.ws_refine = p.refine ? cv.take<char>(p.sz_refine) : nullptr;
+    p.sz_qtc = p.qtrd_tc ? qtrd_tc_ws(p.n) : 0;
+    p.ws_qtc = p.qtrd_tc ? cv.take<char>(p.sz_qtc) : nullptr;
     return cv.ok;
 }
 
@@ -132,8 +135,12 @@ Plan make_plan(int n, int nev, const skew_opts* o, bool vectors) {
     const bool refined_mode = p.mixed && o->mode == SKEW_MODE_MIXED_REFINED;
     p.qband_prec = !p.mixed ? 0 : (refined_mode ? REDUCE_F64ACC : p.planes);
     p.qtrd_f32 = p.mixed && vectors && !(refined_mode && !p.refine);
-    if (o && vectors && o->qtrd == SKEW_QTRD_FP32) p.qtrd_f32 = true;
+    if (o && vectors && (o->qtrd == SKEW_QTRD_FP32 || o->qtrd == SKEW_QTRD_TC)) p.qtrd_f32 = true;
     if (o && o->qtrd == SKEW_QTRD_FP64) p.qtrd_f32 = false;
+    // FP32-level Q_trd on the tensor cores only when asked for: measured at
+    // n = 16384 it is slower than the SIMT FP32 kernel (542 vs 436 ms) and
+    // starts the refinement from a 24x larger orthogonality error
+    p.qtrd_tc = p.qtrd_f32 && o && o->qtrd == SKEW_QTRD_TC;
     // With a complete basis the refinement removes the first-order error, so
     // the products before it need only keep the starting vectors at the level
     // of the FP32 Q_trd: 6 digit slices (about 2^-42) for the reduction, 5
@@ -246,8 +253,12 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
             f64_to_f32_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z, p.Z32);
         }
         count_launch();
-        if (apply_qtrd_f32(st, n, p.b, p.V32, p.tau32, p.Z32, n, 2 * nev, p.status) != cudaSuccess)
+        if (p.qtrd_tc) {
+            rc = apply_qtrd_tc(st, n, p.V32, p.tau32, p.Z32, n, 2 * nev, p.ws_qtc, p.sz_qtc, p.status);
+            if (rc) return rc;
+        } else if (apply_qtrd_f32(st, n, p.b, p.V32, p.tau32, p.Z32, n, 2 * nev, p.status) != cudaSuccess) {
             return SKEW_ERR_CUDA;
+        }
         {
             KtScope kt(st, KT_OTHER);
             f32_to_f64_kernel<<<grid_for(cnt), 256, 0, st>>>(cnt, p.Z32, p.Z);
@@ -899,6 +910,22 @@ int skew_apply_qtrd(int n, int b, const double* Vtrd, const double* tautrd, doub
     if (b != 64) return -2;
     return apply_qtrd(static_cast<cudaStream_t>(stream), n, b, Vtrd, tautrd, Z, ldz, k) == cudaSuccess ? 0
                                                                                                       : SKEW_ERR_CUDA;
+}
+
+size_t skew_apply_qtrd_f32_ws(int n, int tensor) { return tensor ? qtrd_tc_ws(n) : 256; }
+
+int skew_apply_qtrd_f32(int n, int b, const float* V32, const float* tau32, float* Z, int ldz, int k, int tensor,
+                        void* ws, size_t ws_bytes, int* d_status, void* stream) {
+    if (n < 0) return -1;
+    if (b != 64) return -2;
+    if (n >= 3 && k > 0 && (!V32 || !tau32)) return -3;
+    if (ldz < (n > 1 ? n : 1)) return -6;
+    if (k < 0) return -7;
+    if (tensor != 0 && tensor != 1) return -8;
+    if (!d_status) return -11;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (tensor) return apply_qtrd_tc(st, n, V32, tau32, Z, ldz, k, ws, ws_bytes, d_status);
+    return apply_qtrd_f32(st, n, b, V32, tau32, Z, ldz, k, d_status) == cudaSuccess ? 0 : SKEW_ERR_CUDA;
 }
 
 size_t skew_qband_ws(int n, int b, int k) { return qband_ws(n, b, k); }
