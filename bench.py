@@ -188,6 +188,8 @@ def parse():
     p.add_argument("--gemm", default="4096,4096,4096,8,0",
                    help="M,N,K,slices,lower of the gemm workload")
     p.add_argument("--batch-count", type=int, default=2000)
+    p.add_argument("--retune", action="store_true", help="batched: tune the launch on this batch")
+    p.add_argument("--tuning-out", default="", help="batched: record a fresh tuning in this JSON table")
     return p.parse_args()
 
 
@@ -542,12 +544,17 @@ def run_batched(args, ws, rank, local):
     """Batched workload: count matrices, n log-uniform in [32, 1024] (odd and
     even), prescribed spectra l ~ U(0.1, 10), Haar Q, all n/2 pairs, FP64; under
     torchrun each rank takes its longest-processing-time share (no collective
-    on the data path).  Times the batched entry against a loop of single solves
-    on the same device matrices; an accuracy sample is checked on device."""
+    on the data path).  The batch is one plan (skew_batched_plan_*): one
+    persistent launch, captured in a CUDA graph and replayed; its launch
+    configuration comes from the tuning table for this GPU, or is tuned on the
+    batch (--retune, or no entry).  Timed against a loop of single solves
+    (skew_eig_ex) on the same device matrices; an accuracy sample is checked on
+    the device."""
     import torch
 
     import inputs
     import paper_1912_04062_gb300 as sk
+    from paper_1912_04062_gb300 import tuning
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -558,24 +565,40 @@ def run_batched(args, ws, rank, local):
     mine_set = set(mine)
     mats = [sk.fortran(torch.from_numpy(np_a).to(dev)) for k, (np_a, _) in enumerate(items) if k in mine_set]
     nevs = [int(m.shape[0]) // 2 for m in mats]
+    my_sizes = [int(m.shape[0]) for m in mats]
     count = len(mats)
-    opts = sk.Options(mode=sk.SKEW_MODE_FP64)
-    _, As, lams, Zr, Zi, c = sk._batch_arrays(mats, nevs, True)
-    c_n, c_A, c_lda, c_nev, c_l, c_zr, c_zi = c
-    oc = opts.c()
-    nbytes = int(sk.lib().skew_eig_batched_workspace_size(count, c_n, c_nev, sk.ctypes.byref(oc)))
-    work = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
-    d_info = torch.zeros(max(count, 1), dtype=torch.int32, device=dev)
+    gpu = torch.cuda.get_device_name(local)
+    table = tuning.load()
+    tuned = None
+    if args.retune or gpu not in table:
+        plan = sk.BatchedPlan(mats, nevs)
+        best, cands = plan.tune()
+        tuned = {"best": best, "candidates_ms": cands, "bucket": tuning.bucket(my_sizes)}
+        if args.tuning_out:
+            tuning.record(gpu, my_sizes, best, cands, path=args.tuning_out)
+        cfg, source = best, "tuned on this batch"
+    else:
+        cfg, source = tuning.lookup(gpu, my_sizes, table), "tuning table"
+        plan = sk.BatchedPlan(mats, nevs, config=cfg)
+    # one persistent launch per batch, captured in a CUDA graph
+    l0 = sk.launch_count()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            plan.execute(stream=side)
+    stream.wait_stream(side)
+    launches = sk.launch_count() - l0
 
     def batched():
-        code = sk.lib().skew_eig_batched_ex(count, c_n, c_A, c_lda, c_nev, c_l, c_zr, c_zi, sk.ctypes.byref(oc),
-                                            sk._ptr(work), work.numel(), sk._ptr(d_info), sk._stream(stream))
-        if code != 0:
-            raise RuntimeError(f"batched solve failed: {code}")
+        graph.replay()
 
-    nmax = max(int(m.shape[0]) for m in mats)
+    opts = sk.Options(mode=sk.SKEW_MODE_FP64)
+    nmax = max(my_sizes)
     w1 = torch.empty(sk.workspace_size(nmax, nmax // 2, opts), dtype=torch.uint8, device=dev)
     i1 = torch.zeros(1, dtype=torch.int32, device=dev)
+    lams, Zr, Zi = plan.results()
 
     def loop():
         for m, l, zr, zi, nv in zip(mats, lams, Zr, Zi, nevs):
@@ -598,35 +621,35 @@ def run_batched(args, ws, rank, local):
         batched()
     clk = ClockSampler(local)
     clk.start()
-    l0 = sk.launch_count()
     t_batched = timed(batched, args.steps)
-    launches = (sk.launch_count() - l0) // max(args.steps, 1)
     clocks = clk.stop()
-    info_ok = bool((d_info[:count] == 0).all().item())
+    info_ok = bool((plan.info[:count] == 0).all().item())
     # accuracy sample: every 50th matrix of this rank's share
     worst = {"resid": 0.0, "orth": 0.0}
     eps = np.finfo(np.float64).eps
     for k in range(0, count, 50):
         n = int(mats[k].shape[0])
-        res, orth, fro = sk.metrics(mats[k], lams[k][:nevs[k]], Zr[k], Zi[k])
+        res, orth, fro = sk.metrics(mats[k], lams[k], Zr[k], Zi[k])
         worst["resid"] = max(worst["resid"], res / (n * eps * fro))
         worst["orth"] = max(worst["orth"], orth / (n * eps))
     loop()  # warm-up of the single-solve path
     t_loop = timed(loop, 1)
-    small = sum(1 for k in mine if sizes[k] <= 160)
+    flops = sum(4.0 / 3.0 * n ** 3 + 8.0 * (n // 2) * n * n for n in my_sizes)
     if rank == 0:
         out = {"metric": f"batched skew eigensolve time ({args.batch_count} matrices, n log-uniform in [32, 1024], "
                          "nev = n/2)", "value": t_batched, "unit": "s", "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_batched * 1e3, "higher_is_better": False, "scaling": "strong",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": "batched", "count": args.batch_count, "count_this_rank": count,
-                          "shared_memory_path": small, "two_step_path": count - small,
-                          "sum_n3": float(sum(float(sizes[k]) ** 3 for k in mine)),
+                          "sum_n3": float(sum(float(n) ** 3 for n in my_sizes)),
+                          "launch": {"ctas_per_sm": cfg[0], "smem_max_n": cfg[1], "source": source,
+                                     "kernels_per_batch": int(launches), "cuda_graph": True},
                           "parallelism": f"lpt-shard x{ws}" if ws > 1 else "single"},
+               "fp64_equiv_tflops": flops / t_batched / 1e12,
                "loop_of_single_solves_s": t_loop, "speedup_vs_loop": t_loop / t_batched,
                "accuracy_sample": {"matrices": len(range(0, count, 50)), "worst_resid_scaled": worst["resid"],
                                    "worst_orth_scaled": worst["orth"], "all_info_zero": info_ok},
-               "gpu_launches": launches, "clocks": clocks}
+               "tuning": tuned, "gpu_launches": int(launches) * args.steps, "clocks": clocks}
         print(json.dumps(out), flush=True)
 
 

@@ -180,12 +180,12 @@ int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda,
  * into device lambda[b], Z_re[b], Z_im[b] of leading dimension n[b]).  The
  * size arrays and the pointer arrays are host arrays; Z_re == Z_im == NULL
  * (the arrays) or Z_re[b] == Z_im[b] == NULL (one matrix) asks for
- * eigenvalues only.  Orders 2..1024 are solved together, one CTA per matrix
- * (unblocked Householder tridiagonalisation with the matrix in shared memory
- * up to n = 160 and in a global-memory copy above, then one bisection and one
- * inverse-iteration launch for all matrices, then back-transform launches),
- * always in FP64; larger orders run the two-step solve of skew_eig_ex one after
- * another in `opts`' mode.  Not in the paper (it solves one matrix per run).
+ * eigenvalues only.  Orders 2..1024 are solved together in one persistent
+ * launch (see skew_batched_config below: each CTA takes whole matrices,
+ * largest first, and runs unblocked Householder tridiagonalisation with the
+ * matrix in shared or global memory, bisection, inverse iteration and the
+ * back-transform), always in FP64; larger orders run the two-step solve of
+ * skew_eig_ex one after another in `opts`' mode.  Not in the paper (it solves one matrix per run).
  * Asynchronous on `stream`.  skew_eig_batched takes its workspace from the
  * library pool (stream-ordered, freed on the stream) and reports no per-matrix
  * status; skew_eig_batched_ex takes a caller workspace of at least
@@ -203,6 +203,54 @@ int skew_eig_batched_ex(int count, const int* n, const double* const* A, const i
                         const int* nev, double* const* lambda, double* const* Z_re,
                         double* const* Z_im, const skew_opts* opts, void* workspace,
                         size_t ws_bytes, int* d_info, void* stream);
+
+/*
+ * Batched solve as a plan: one persistent launch for the whole batch.
+ * Not in the paper (it solves one matrix per run; each matrix here follows
+ * Algorithm 1 in its one-step form: unblocked Householder tridiagonalisation,
+ * Lemma-1 link, bisection and inverse iteration, D map and back
+ * transformation, FP64 throughout).
+ *
+ * skew_batched_config sets the launch: ctas_per_sm (1..4) CTAs of 256 threads
+ * per SM take matrices from a device work counter, largest first; orders up to
+ * smem_max_n (0..160; capped by the shared memory of ctas_per_sm CTAs per SM)
+ * keep the working matrix in shared memory, larger ones in global memory.
+ * skew_batched_set_config / get_config hold the process-wide default used by
+ * skew_eig_batched(_ex) and by plans created with cfg == NULL (initially
+ * ctas_per_sm = 2, smem_max_n = 112).
+ *
+ * skew_batched_plan_create checks the batch (arguments as skew_eig_batched_ex:
+ * 2 n, 3 A, 4 lda, 5 nev, 6 lambda, 7 Z; every order must be <= 1024, else
+ * SKEW_ERR_UNSUPPORTED), lays the per-matrix descriptors out in the caller's
+ * workspace (at least skew_eig_batched_workspace_size bytes), uploads them on
+ * `stream` and synchronises it, and fixes the launch parameters.  The device
+ * buffers named in the call must stay valid while the plan is used.
+ * skew_batched_plan_exec then only clears d_info (may be NULL; per matrix 0 or
+ * 1000 + j) and the work counter and launches the persistent kernel: no host
+ * synchronisation and no allocation, so the call can be captured into a CUDA
+ * graph and replayed.  skew_batched_plan_tune times every candidate
+ * configuration on the plan's batch (one warm-up and two timed runs each, CUDA
+ * events on `stream`), keeps the fastest in the plan and returns it; cand_*
+ * (may be NULL) receive up to cap candidates and their times in ms; returns
+ * the number of candidates timed or a negative / SKEW_ERR_* code.
+ */
+typedef struct {
+    int ctas_per_sm;
+    int smem_max_n;
+    int reserved[2];
+} skew_batched_config;
+typedef struct skew_batched_plan skew_batched_plan;
+int skew_batched_set_config(const skew_batched_config* cfg);
+void skew_batched_get_config(skew_batched_config* cfg);
+int skew_batched_plan_create(int count, const int* n, const double* const* A, const int* lda, const int* nev,
+                             double* const* lambda, double* const* Z_re, double* const* Z_im,
+                             const skew_batched_config* cfg, void* workspace, size_t ws_bytes, int* d_info,
+                             void* stream, skew_batched_plan** plan);
+int skew_batched_plan_exec(skew_batched_plan* plan, void* stream);
+int skew_batched_plan_tune(skew_batched_plan* plan, skew_batched_config* best, int* cand_ctas,
+                           int* cand_smem, float* cand_ms, int cap, void* stream);
+void skew_batched_plan_get_config(const skew_batched_plan* plan, skew_batched_config* cfg);
+void skew_batched_plan_destroy(skew_batched_plan* plan);
 
 /* Stages timed by skew_eig_profile (Algorithm 1, two-step form):
  * 0 ingest (copy of the strict lower triangle), 1 full-to-band reduction,

@@ -88,6 +88,13 @@ SIGNATURES = {
     "skew_tridiag_eig_noalloc": (_i, [_i, _p, _i, _p, _p, _i, _p, _p]),
     "skew_dmap": (_i, [_i, _i, _p, _i, _p, _p, _i, _p]),
     "skew_apply_qtrd": (_i, [_i, _i, _p, _p, _p, _i, _i, _p]),
+    "skew_batched_set_config": (_i, [_p]),
+    "skew_batched_get_config": (None, [_p]),
+    "skew_batched_plan_create": (_i, [_i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p, _p, _p]),
+    "skew_batched_plan_exec": (_i, [_p, _p]),
+    "skew_batched_plan_tune": (_i, [_p, _p, _p, _p, _p, _i, _p]),
+    "skew_batched_plan_get_config": (None, [_p, _p]),
+    "skew_batched_plan_destroy": (None, [_p]),
     "skew_apply_qtrd_f32_ws": (_sz, [_i, _i]),
     "skew_apply_qtrd_f32": (_i, [_i, _i, _p, _p, _p, _i, _i, _i, _p, _sz, _p, _p]),
     "skew_qband_ws": (_sz, [_i, _i, _i]),
@@ -99,6 +106,10 @@ class skew_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("band", ctypes.c_int), ("check_finite", ctypes.c_int),
                 ("fault", ctypes.c_int), ("refine_iters", ctypes.c_int), ("refine_rho", ctypes.c_int),
                 ("qtrd", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+
+
+class skew_batched_config(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("smem_max_n", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -425,6 +436,76 @@ def skew_eig_batched(As, nevs, vectors: bool = True, opts: Options | None = None
     _check(code, "skew_eig_batched_ex")
     out = ([l[:nv] for l, nv in zip(lams, nevs)], Zr, Zi)
     return out + (d_info[:count],) if info else out
+
+
+def batched_set_config(ctas_per_sm: int, smem_max_n: int) -> None:
+    """Process-wide launch configuration of the batched solve."""
+    c = skew_batched_config(ctas_per_sm, smem_max_n)
+    _check(lib().skew_batched_set_config(ctypes.byref(c)), "skew_batched_set_config")
+
+
+def batched_get_config():
+    c = skew_batched_config()
+    lib().skew_batched_get_config(ctypes.byref(c))
+    return int(c.ctas_per_sm), int(c.smem_max_n)
+
+
+class BatchedPlan:
+    """A batch of problems (orders <= 1024) prepared once and solved by one
+    persistent launch per execute() (skew_batched_plan_*).  Holds its device
+    buffers; execute() does no host synchronisation and can be captured in a
+    CUDA graph."""
+
+    def __init__(self, As, nevs, vectors: bool = True, config=None, stream=None):
+        torch = _torch()
+        self.count, self.As, lams, self.Zr, self.Zi, self._c = _batch_arrays(As, nevs, vectors)
+        self.nevs = [int(v) for v in nevs]
+        self.lams = lams
+        c_n, c_A, c_lda, c_nev, c_l, c_zr, c_zi = self._c
+        dev = self.As[0].device if self.As else torch.device("cuda")
+        nbytes = int(lib().skew_eig_batched_workspace_size(self.count, c_n, c_nev, None))
+        self.ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+        self.info = torch.zeros(max(self.count, 1), dtype=torch.int32, device=dev)
+        cfg = skew_batched_config(*config) if config is not None else None
+        self._plan = ctypes.c_void_p()
+        code = lib().skew_batched_plan_create(self.count, c_n, c_A, c_lda, c_nev, c_l, c_zr, c_zi,
+                                              ctypes.byref(cfg) if cfg is not None else None, _ptr(self.ws),
+                                              self.ws.numel(), _ptr(self.info), _stream(stream),
+                                              ctypes.byref(self._plan))
+        _check(code, "skew_batched_plan_create")
+
+    def execute(self, stream=None):
+        _check(lib().skew_batched_plan_exec(self._plan, _stream(stream)), "skew_batched_plan_exec")
+
+    def tune(self, stream=None):
+        """Time every launch configuration on this batch; keep and return the
+        fastest as (ctas_per_sm, smem_max_n) with the list of
+        (ctas_per_sm, smem_max_n, ms) candidates."""
+        cap = 64
+        ca, cs = (ctypes.c_int * cap)(), (ctypes.c_int * cap)()
+        cm = (ctypes.c_float * cap)()
+        best = skew_batched_config()
+        k = lib().skew_batched_plan_tune(self._plan, ctypes.byref(best), ca, cs, cm, cap, _stream(stream))
+        if k < 0 or k > 10000:
+            _check(k, "skew_batched_plan_tune")
+        cands = [(int(ca[i]), int(cs[i]), float(cm[i])) for i in range(min(k, cap))]
+        return (int(best.ctas_per_sm), int(best.smem_max_n)), cands
+
+    def config(self):
+        c = skew_batched_config()
+        lib().skew_batched_plan_get_config(self._plan, ctypes.byref(c))
+        return int(c.ctas_per_sm), int(c.smem_max_n)
+
+    def results(self):
+        return [l[:nv] for l, nv in zip(self.lams, self.nevs)], self.Zr, self.Zi
+
+    def __del__(self):
+        try:
+            if self._plan:
+                lib().skew_batched_plan_destroy(self._plan)
+                self._plan = ctypes.c_void_p()
+        except Exception:
+            pass
 
 
 def shard_lpt(sizes, world: int):

@@ -1,17 +1,20 @@
 // batched.cu -- many independent skew eigenproblems of small and medium order
-// in a few launches (the paper solves one matrix per run; this is the batched
-// form of the same route for orders up to BATCH_MAX = 1024).
+// in ONE persistent launch (the paper solves one matrix per run; this is the
+// batched form of the same route for orders up to BATCH_MAX = 1024).
 //
-// Per matrix, one CTA tridiagonalises the whole skew matrix column by column
-// with Householder reflectors (dlarfg convention; the skew two-sided update
-// A <- A + v p^T - p v^T with p = tau A v, Eqs. 2-6 with u1 = -u2, whose
-// 1/2 tau^2 (v^T A v) v term is 0 for skew A), giving alpha_c = T[c, c+1]
-// (Lemma 1).  Orders up to BATCH_SMALL_MAX keep the matrix in shared memory;
-// larger ones work on a copy in global memory (L2), one CTA each, so that the
-// GPU runs as many matrices at a time as it has SMs.  One launch then bisects
-// every wanted eigenvalue of every matrix, one launch runs inverse iteration
-// for all of them (Sec. 3), and one CTA per matrix applies the D map
-// (Algorithm 1 step 3) and the reflectors in reverse order to the eigenvectors.
+// Every CTA of the launch (ctas_per_sm per SM) takes matrices from a device
+// work counter over a list sorted largest first (longest-processing-time
+// order) and runs the whole route for each one: it tridiagonalises the skew
+// matrix column by column with Householder reflectors (dlarfg convention; the
+// skew two-sided update A <- A + v p^T - p v^T with p = tau A v, Eqs. 2-6 with
+// u1 = -u2, whose 1/2 tau^2 (v^T A v) v term is 0 for skew A), giving
+// alpha_c = T[c, c+1] (Lemma 1); bisects every wanted eigenvalue and runs
+// inverse iteration (Sec. 3), one thread per eigenvalue; then applies the D
+// map (Algorithm 1 step 3) and the reflectors in reverse order to the
+// eigenvectors.  Orders up to smem_max_n keep the working matrix in shared
+// memory; larger ones work on a copy in global memory (L2).  ctas_per_sm and
+// smem_max_n are the launch's tunables (skew_batched_config; chosen per GPU by
+// timing the candidates on the batch, skew_batched_plan_tune).
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -28,7 +31,7 @@ constexpr int BT = 256;  // threads per CTA of the per-matrix kernels
 
 struct BItem {
     int n, nev, lda, vectors;
-    double* S;                   // global working matrix (n x n) for n > BATCH_SMALL_MAX
+    double* S;                   // global working matrix (n x n), used when n > the launch's smem_max_n
     const double* A;
     double *lambda, *Zre, *Zim;  // Z: n x nev, leading dimension n
     int* info;                   // caller's status word of this matrix (may be null)
@@ -62,18 +65,11 @@ __device__ double block_max(double v, double* red) {
     return s;
 }
 
-// One CTA per matrix (order[] lists the matrices, largest first).  G = false:
-// shared memory holds S (n x n, ld n + 1), v and p; G = true: S is the
-// matrix's global copy (ld n), v and p in shared memory.
-template <bool G>
-__global__ void __launch_bounds__(BT) bt_reduce_kernel(const BItem* __restrict__ items, const int* __restrict__ order) {
-    extern __shared__ double bsm[];
-    const BItem it = items[order[blockIdx.x]];
-    const int n = it.n, ld = G ? n : n + 1, t = threadIdx.x;
-    double* S = G ? it.S : bsm;
-    double* v = G ? bsm : S + (size_t)n * ld;
-    double* p = v + n;
-    double* red = p + n;
+// Tridiagonalisation of one matrix by the whole CTA.  S: the working matrix
+// (shared memory, ld n + 1, or the matrix's global copy, ld n); v, p: n
+// doubles of shared memory; red: 32 doubles of shared memory.
+__device__ void bt_reduce_body(const BItem& it, double* S, int ld, double* v, double* p, double* red) {
+    const int n = it.n, t = threadIdx.x;
     // S(i, j) = A(i, j) below the diagonal, -A(j, i) above: only the strict
     // lower triangle of A is read
     for (int e = t; e < n * n; e += BT) {
@@ -147,49 +143,17 @@ __global__ void __launch_bounds__(BT) bt_reduce_kernel(const BItem* __restrict__
         it.sc->pivmin = DBL_MIN * fmax(1.0, am);
         *it.fail = 0x7fffffff;
     }
+    __syncthreads();
 }
 
-// Matrix owning global eigenvalue index e (items sorted by e0).
-__device__ int item_of(const BItem* __restrict__ items, int count, long long e) {
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (items[mid].e0 <= e) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__global__ void bt_bisect_kernel(const BItem* __restrict__ items, int count, long long total) {
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= total) return;
-    const BItem& it = items[item_of(items, count, e)];
-    const int k = (int)(e - it.e0);
-    it.lambda[k] = tri::bisect_one(it.n, it.n - 1 - k, it.a2, it.sc->g, it.sc->pivmin);
-}
-
-__global__ void bt_invit_kernel(const BItem* __restrict__ items, int count, long long total, int maxit) {
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= total) return;
-    const BItem& it = items[item_of(items, count, e)];
-    if (!it.vectors) return;
-    const int k = (int)(e - it.e0);
-    const double ctol = fmin(1e-3, 10.0 / ((double)it.n * sqrt((double)it.n)));
-    tri::invit_cluster(it.n, it.nev, it.alpha, it.lambda, it.sc->g, ctol, maxit, it.bf, it.Qi, it.fail, k);
-}
-
-// One CTA per matrix: eigenvector k of S (interleaved Qi) -> D map -> X_k, Y_k,
-// then Z <- H_0 H_1 ... H_{n-3} Z.  Warp w takes columns w, w + 8, ... of
-// [X Y] and keeps one column in registers (lane l holds rows l + 32 r, r < BR).
-// G = false: the reflectors are staged in shared memory; G = true: read from
-// global memory (L2).
+// Eigenvector k of S (interleaved Qi) -> D map -> X_k, Y_k, then
+// Z <- H_0 H_1 ... H_{n-3} Z, by the whole CTA.  Warp w takes columns w,
+// w + 8, ... of [X Y] and keeps one column in registers (lane l holds rows
+// l + 32 r, r < BR).  G = false: the reflectors are staged in shared memory
+// (bsm, n^2 + n doubles); G = true: read from global memory (L2).
 template <int BR, bool G>
-__global__ void __launch_bounds__(BT) bt_back_kernel(const BItem* __restrict__ items, const int* __restrict__ order) {
-    extern __shared__ double bsm[];
-    const BItem it = items[order[blockIdx.x]];
+__device__ void bt_back_body(const BItem& it, double* bsm) {
     const int n = it.n, nev = it.nev, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (t == 0 && it.info) *it.info = (*it.fail < nev) ? SKEW_INFO_INVIT_BASE + *it.fail : 0;
-    if (!it.vectors || nev == 0) return;
     const double* Vs = it.V;  // n x n, reflector c in column c (rows c+1..)
     const double* ts = it.tau;
     if (!G) {
@@ -241,6 +205,53 @@ __global__ void __launch_bounds__(BT) bt_back_kernel(const BItem* __restrict__ i
     }
 }
 
+// The persistent launch: CTAs take matrices from *next over order[] (largest
+// first) until the list is exhausted; each matrix goes through the whole route
+// in one CTA.  MINB = CTAs per SM the registers are budgeted for.
+template <int MINB>
+__global__ void __launch_bounds__(BT, MINB)
+bt_persistent_kernel(const BItem* __restrict__ items, const int* __restrict__ order, int count,
+                     int* __restrict__ next, int smem_n, int maxit) {
+    extern __shared__ double bsm[];
+    __shared__ int s_q;
+    const int t = threadIdx.x;
+    for (;;) {
+        __syncthreads();  // the previous matrix is finished with shared memory and s_q
+        if (t == 0) s_q = atomicAdd(next, 1);
+        __syncthreads();
+        const int q = s_q;
+        if (q >= count) break;
+        const BItem it = items[order[q]];
+        const int n = it.n, nev = it.nev;
+        const bool in_smem = n <= smem_n;
+        if (in_smem) {
+            double* S = bsm;
+            double* v = S + (size_t)n * (n + 1);
+            bt_reduce_body(it, S, n + 1, v, v + n, v + 2 * n);
+        } else {
+            bt_reduce_body(it, it.S, n, bsm, bsm + n, bsm + 2 * n);
+        }
+        // every wanted eigenvalue of this matrix (Sturm bisection), then
+        // inverse iteration per cluster leader
+        for (int k = t; k < nev; k += BT) it.lambda[k] = tri::bisect_one(n, n - 1 - k, it.a2, it.sc->g, it.sc->pivmin);
+        __syncthreads();
+        if (it.vectors) {
+            const double ctol = fmin(1e-3, 10.0 / ((double)n * sqrt((double)n)));
+            for (int k = t; k < nev; k += BT)
+                tri::invit_cluster(n, nev, it.alpha, it.lambda, it.sc->g, ctol, maxit, it.bf, it.Qi, it.fail, k);
+        }
+        __syncthreads();
+        if (t == 0 && it.info) *it.info = (*it.fail < nev) ? SKEW_INFO_INVIT_BASE + *it.fail : 0;
+        if (it.vectors && nev > 0) {
+            if (in_smem) bt_back_body<(BATCH_SMALL_MAX + 31) / 32, false>(it, bsm);
+            else if (n <= BATCH_SMALL_MAX) bt_back_body<(BATCH_SMALL_MAX + 31) / 32, true>(it, bsm);
+            else if (n <= 256) bt_back_body<8, true>(it, bsm);
+            else if (n <= 512) bt_back_body<16, true>(it, bsm);
+            else bt_back_body<32, true>(it, bsm);
+        }
+    }
+}
+
 struct BCarve {
     std::vector<BItem> items;
     std::vector<int> order;
@@ -269,7 +280,9 @@ size_t carve_small(Carve& cv, int count, const BatchProblem* pr, BCarve* out) {
         it.Zre = q.Zre;
         it.Zim = q.Zim;
         it.info = q.info;
-        it.S = (q.n > BATCH_SMALL_MAX) ? cv.take<double>(n * n) : nullptr;
+        // global working copy: used whenever the launch keeps this order out
+        // of shared memory (the threshold is a launch parameter, 0..160)
+        it.S = cv.take<double>(n * n);
         it.V = cv.take<double>(n * n);
         it.tau = cv.take<double>(n);
         it.alpha = cv.take<double>(n);
@@ -297,89 +310,135 @@ size_t carve_small(Carve& cv, int count, const BatchProblem* pr, BCarve* out) {
 }
 
 size_t smem_reduce(int n) { return sizeof(double) * ((size_t)n * (n + 1) + 2 * (size_t)n + 32); }
-size_t smem_back(int n) { return sizeof(double) * ((size_t)n * n + (size_t)n); }
 
 }  // namespace
 
 size_t batched_small_ws(int count, const BatchProblem* pr) {
     Carve cv(nullptr, ~size_t(0));
     carve_small(cv, count, pr, nullptr);
+    cv.take<int>(1);  // work counter of the persistent launch
     return cv.off + 256;
 }
 
-int batched_small(cudaStream_t st, int count, const BatchProblem* pr, void* ws, size_t ws_bytes, int maxit) {
+namespace {
+
+// Largest order kept in shared memory for a given shared-memory budget per CTA.
+int smem_n_for(size_t budget) {
+    int n = 2;
+    while (n < BATCH_SMALL_MAX && smem_reduce(n + 1) <= budget) n++;
+    return n;
+}
+
+template <int MINB>
+int prepare_persistent(int smem_n, int nmax, int count, BatchLaunch* out) {
+    const size_t dyn_global = sizeof(double) * (2 * (size_t)nmax + 32);
+    const size_t dyn = smem_n >= 2 ? std::max(smem_reduce(smem_n), dyn_global) : dyn_global;
+    auto kern = bt_persistent_kernel<MINB>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+        return SKEW_ERR_LAUNCH;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT, dyn) != cudaSuccess || occ < 1)
+        return SKEW_ERR_LAUNCH;
+    const int per_sm = occ < MINB ? occ : MINB;
+    int grid = per_sm * device_sms();
+    if (grid > count) grid = count;
+    out->ctas = MINB;
+    out->grid = grid;
+    out->dyn = dyn;
+    out->smem_n = smem_n;
+    return 0;
+}
+
+}  // namespace
+
+skew_batched_config& batched_default_config() {
+    static skew_batched_config c{2, 112, {0, 0}};
+    return c;
+}
+
+int batched_config_check(const skew_batched_config& c) {
+    if (c.ctas_per_sm < 1 || c.ctas_per_sm > 4) return -1;
+    if (c.smem_max_n < 0 || c.smem_max_n > BATCH_SMALL_MAX) return -2;
+    return 0;
+}
+
+// Launch parameters of the persistent kernel for a configuration (sets the
+// kernel's shared-memory attribute; no stream work).
+int batched_prepare(const BatchPlanDev& d, const skew_batched_config& cfg, BatchLaunch* out) {
+    if (batched_config_check(cfg)) return SKEW_ERR_UNSUPPORTED;
+    // the shared-memory threshold cannot exceed what the per-SM budget allows
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const size_t budget = (size_t)smem_sm / (size_t)cfg.ctas_per_sm - 2048;
+    int smem_n = cfg.smem_max_n;
+    if (smem_n >= 2) smem_n = std::min(smem_n, smem_n_for(budget));
+    const int cnt = d.count > 0 ? d.count : 1;
+    switch (cfg.ctas_per_sm) {
+    case 1: return prepare_persistent<1>(smem_n, d.nmax, cnt, out);
+    case 2: return prepare_persistent<2>(smem_n, d.nmax, cnt, out);
+    case 3: return prepare_persistent<3>(smem_n, d.nmax, cnt, out);
+    default: return prepare_persistent<4>(smem_n, d.nmax, cnt, out);
+    }
+}
+
+// Stream work only: clear the work counter, launch (capturable).
+int batched_exec(cudaStream_t st, const BatchPlanDev& d, const BatchLaunch& L, int maxit) {
+    if (d.count <= 0) return 0;
+    if (cudaMemsetAsync(d.next, 0, sizeof(int), st) != cudaSuccess) return SKEW_ERR_CUDA;
+    const BItem* items = static_cast<const BItem*>(d.items);
+    switch (L.ctas) {
+    case 1: bt_persistent_kernel<1><<<L.grid, BT, L.dyn, st>>>(items, d.order, d.count, d.next, L.smem_n, maxit); break;
+    case 2: bt_persistent_kernel<2><<<L.grid, BT, L.dyn, st>>>(items, d.order, d.count, d.next, L.smem_n, maxit); break;
+    case 3: bt_persistent_kernel<3><<<L.grid, BT, L.dyn, st>>>(items, d.order, d.count, d.next, L.smem_n, maxit); break;
+    default: bt_persistent_kernel<4><<<L.grid, BT, L.dyn, st>>>(items, d.order, d.count, d.next, L.smem_n, maxit);
+    }
+    count_launch();
+    return cuda_ok(cudaGetLastError());
+}
+
+int batched_launch(cudaStream_t st, const BatchPlanDev& d, const skew_batched_config& cfg, int maxit) {
+    if (d.count <= 0) return 0;
+    BatchLaunch L{};
+    if (const int rc = batched_prepare(d, cfg, &L)) return rc;
+    return batched_exec(st, d, L, maxit);
+}
+
+// Places the item table in the workspace and uploads it (synchronously with
+// respect to the host buffers: pageable copies).
+int batched_upload(cudaStream_t st, int count, const BatchProblem* pr, void* ws, size_t ws_bytes, BatchPlanDev* out) {
     if (count <= 0) return 0;
     for (int b = 0; b < count; b++)
         if (pr[b].n < 2 || pr[b].n > BATCH_MAX) return SKEW_ERR_UNSUPPORTED;
     Carve cv(ws, ws_bytes);
     BCarve bc{};
     carve_small(cv, count, pr, &bc);
+    int* d_next = cv.take<int>(1);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
-    // per-matrix launches by class, each listing its matrices largest first:
-    // [0, n1) shared-memory path, then the global-memory path by rows per lane
-    // of the back-transform (8, 16, 32: n <= 256, 512, 1024)
+    // longest processing time first: largest order first
     bc.order.resize((size_t)count);
     for (int b = 0; b < count; b++) bc.order[(size_t)b] = b;
     std::stable_sort(bc.order.begin(), bc.order.end(), [&](int x, int y) { return pr[x].n > pr[y].n; });
-    auto cls = [&](int n) { return n <= BATCH_SMALL_MAX ? 0 : (n <= 256 ? 1 : (n <= 512 ? 2 : 3)); };
-    std::stable_sort(bc.order.begin(), bc.order.end(), [&](int x, int y) { return cls(pr[x].n) < cls(pr[y].n); });
-    int first[5] = {0, 0, 0, 0, 0};
-    for (int c = 0; c < 4; c++) {
-        first[c + 1] = first[c];
-        while (first[c + 1] < count && cls(pr[bc.order[(size_t)first[c + 1]]].n) == c) first[c + 1]++;
-    }
-    // pageable copies: the host vectors may go once the calls return
     if (const cudaError_t e = cudaMemcpyAsync(bc.d_items, bc.items.data(), sizeof(BItem) * (size_t)count,
                                               cudaMemcpyHostToDevice, st))
         return cuda_fail(e);
     if (const cudaError_t e = cudaMemcpyAsync(bc.d_order, bc.order.data(), sizeof(int) * (size_t)count,
                                               cudaMemcpyHostToDevice, st))
         return cuda_fail(e);
-    int nmax_small = 2, nmax = 2;
-    for (int b = 0; b < count; b++) {
-        nmax = pr[b].n > nmax ? pr[b].n : nmax;
-        if (pr[b].n <= BATCH_SMALL_MAX) nmax_small = pr[b].n > nmax_small ? pr[b].n : nmax_small;
-    }
-    const int nsmall = first[1], nlarge = count - first[1];
-    if (nsmall > 0) {
-        const size_t s1 = smem_reduce(nmax_small);
-        cudaFuncSetAttribute(bt_reduce_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
-        bt_reduce_kernel<false><<<nsmall, BT, s1, st>>>(bc.d_items, bc.d_order);
-        count_launch();
-    }
-    if (nlarge > 0) {
-        const size_t s1 = sizeof(double) * (2 * (size_t)nmax + 32);
-        cudaFuncSetAttribute(bt_reduce_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
-        bt_reduce_kernel<true><<<nlarge, BT, s1, st>>>(bc.d_items, bc.d_order + first[1]);
-        count_launch();
-    }
-    if (bc.total > 0) {
-        const unsigned g = (unsigned)((bc.total + 127) / 128);
-        bt_bisect_kernel<<<g, 128, 0, st>>>(bc.d_items, count, bc.total);
-        const unsigned g2 = (unsigned)((bc.total + 63) / 64);
-        bt_invit_kernel<<<g2, 64, 0, st>>>(bc.d_items, count, bc.total, maxit);
-        count_launch(2);
-    }
-    if (nsmall > 0) {
-        const size_t s2 = smem_back(nmax_small);
-        cudaFuncSetAttribute(bt_back_kernel<(BATCH_SMALL_MAX + 31) / 32, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
-        bt_back_kernel<(BATCH_SMALL_MAX + 31) / 32, false><<<nsmall, BT, s2, st>>>(bc.d_items, bc.d_order);
-        count_launch();
-    }
-    if (first[2] > first[1]) {
-        bt_back_kernel<8, true><<<first[2] - first[1], BT, 0, st>>>(bc.d_items, bc.d_order + first[1]);
-        count_launch();
-    }
-    if (first[3] > first[2]) {
-        bt_back_kernel<16, true><<<first[3] - first[2], BT, 0, st>>>(bc.d_items, bc.d_order + first[2]);
-        count_launch();
-    }
-    if (first[4] > first[3]) {
-        bt_back_kernel<32, true><<<first[4] - first[3], BT, 0, st>>>(bc.d_items, bc.d_order + first[3]);
-        count_launch();
-    }
-    return cuda_ok(cudaGetLastError());
+    out->items = bc.d_items;
+    out->order = bc.d_order;
+    out->next = d_next;
+    out->count = count;
+    out->nmax = 2;
+    for (int b = 0; b < count; b++) out->nmax = pr[b].n > out->nmax ? pr[b].n : out->nmax;
+    return 0;
+}
+
+int batched_small(cudaStream_t st, int count, const BatchProblem* pr, void* ws, size_t ws_bytes, int maxit) {
+    if (count <= 0) return 0;
+    BatchPlanDev d{};
+    if (const int rc = batched_upload(st, count, pr, ws, ws_bytes, &d)) return rc;
+    return batched_launch(st, d, batched_default_config(), maxit);
 }
 
 }  // namespace sk

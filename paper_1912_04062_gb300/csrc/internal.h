@@ -183,8 +183,28 @@ struct BatchProblem {
     int* info;                   // device status word of this matrix (may be null)
 };
 size_t batched_small_ws(int count, const BatchProblem* probs);
-// every n in [2, BATCH_MAX]; FP64 throughout
+// every n in [2, BATCH_MAX]; FP64 throughout; one persistent launch with the
+// process-wide default configuration
 int batched_small(cudaStream_t st, int count, const BatchProblem* probs, void* ws, size_t ws_bytes, int maxit);
+// The uploaded item table of a batch (device pointers into the workspace).
+struct BatchPlanDev {
+    const void* items;  // per-matrix descriptors (batched.cu's layout)
+    const int* order;   // matrices largest first
+    int* next;          // work counter of the persistent launch
+    int count, nmax;
+};
+struct BatchLaunch {
+    int ctas, grid;
+    size_t dyn;
+    int smem_n;
+};
+int batched_upload(cudaStream_t st, int count, const BatchProblem* probs, void* ws, size_t ws_bytes,
+                   BatchPlanDev* out);
+int batched_prepare(const BatchPlanDev& d, const skew_batched_config& cfg, BatchLaunch* out);
+int batched_exec(cudaStream_t st, const BatchPlanDev& d, const BatchLaunch& L, int maxit);
+int batched_launch(cudaStream_t st, const BatchPlanDev& d, const skew_batched_config& cfg, int maxit);
+skew_batched_config& batched_default_config();
+int batched_config_check(const skew_batched_config& c);
 
 // ---- metrics.cu -------------------------------------------------------------
 size_t metrics_ws(int n, int nev, int s);

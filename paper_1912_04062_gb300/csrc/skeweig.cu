@@ -648,6 +648,144 @@ int skew_eig_batched_ex(int count, const int* n, const double* const* A, const i
     return cuda_ok(cudaGetLastError());
 }
 
+}  // extern "C"
+
+struct skew_batched_plan {
+    BatchPlanDev d;
+    BatchLaunch launch;
+    skew_batched_config cfg;
+    int count;
+    int* d_info;
+};
+
+extern "C" {
+
+int skew_batched_set_config(const skew_batched_config* cfg) {
+    if (!cfg) return -1;
+    if (batched_config_check(*cfg)) return -1;
+    batched_default_config() = *cfg;
+    return 0;
+}
+
+void skew_batched_get_config(skew_batched_config* cfg) {
+    if (cfg) *cfg = batched_default_config();
+}
+
+int skew_batched_plan_create(int count, const int* n, const double* const* A, const int* lda, const int* nev,
+                             double* const* lambda, double* const* Z_re, double* const* Z_im,
+                             const skew_batched_config* cfg, void* workspace, size_t ws_bytes, int* d_info,
+                             void* stream, skew_batched_plan** plan) {
+    if (!plan) return -14;
+    *plan = nullptr;
+    int rc = batch_check(count, n, A, lda, nev, lambda, Z_re, Z_im, nullptr);
+    if (rc) return rc;
+    const skew_batched_config c = cfg ? *cfg : batched_default_config();
+    if (batched_config_check(c)) return -9;
+    for (int b = 0; b < count; b++)
+        if (n[b] > BATCH_MAX) return SKEW_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BatchPlan bp = plan_batch(count, n, A, lda, nev, lambda, Z_re, Z_im, nullptr, d_info);
+    if (bp.small_bytes && (!workspace || ws_bytes < bp.small_bytes)) return SKEW_ERR_WORKSPACE;
+    skew_batched_plan* p = new skew_batched_plan{};
+    p->count = count;
+    p->d_info = d_info;
+    p->cfg = c;
+    if (!bp.small.empty()) {
+        rc = batched_upload(st, (int)bp.small.size(), bp.small.data(), workspace, ws_bytes, &p->d);
+        if (!rc) rc = batched_prepare(p->d, c, &p->launch);
+    }
+    if (!rc) {
+        if (const cudaError_t e = cudaStreamSynchronize(st)) rc = cuda_fail(e);
+    }
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    *plan = p;
+    return 0;
+}
+
+int skew_batched_plan_exec(skew_batched_plan* p, void* stream) {
+    if (!p) return -1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->d_info && p->count > 0) {
+        if (const cudaError_t e = cudaMemsetAsync(p->d_info, 0, sizeof(int) * (size_t)p->count, st))
+            return cuda_fail(e);
+    }
+    return batched_exec(st, p->d, p->launch, 5);
+}
+
+void skew_batched_plan_get_config(const skew_batched_plan* p, skew_batched_config* cfg) {
+    if (p && cfg) *cfg = p->cfg;
+}
+
+void skew_batched_plan_destroy(skew_batched_plan* p) { delete p; }
+
+int skew_batched_plan_tune(skew_batched_plan* p, skew_batched_config* best, int* cand_ctas, int* cand_smem,
+                           float* cand_ms, int cap, void* stream) {
+    if (!p) return -1;
+    if (cap < 0) return -6;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->d.count <= 0) {
+        if (best) *best = p->cfg;
+        return 0;
+    }
+    static const int kSmem[] = {0, 48, 64, 80, 96, 112, 128, 160};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SKEW_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SKEW_ERR_CUDA;
+    }
+    int ncand = 0, rc = 0;
+    float best_ms = 0.f;
+    skew_batched_config best_cfg = p->cfg;
+    BatchLaunch best_launch = p->launch;
+    int last_smem = -1, last_ctas = -1;
+    for (int ctas = 1; ctas <= 4 && !rc; ctas++) {
+        for (int si = 0; si < (int)(sizeof(kSmem) / sizeof(kSmem[0])) && !rc; si++) {
+            const skew_batched_config c{ctas, kSmem[si], {0, 0}};
+            BatchLaunch L{};
+            if (batched_prepare(p->d, c, &L)) continue;
+            // thresholds the shared-memory budget caps to the same value time the same launch
+            if (L.ctas == last_ctas && L.smem_n == last_smem) continue;
+            last_ctas = L.ctas;
+            last_smem = L.smem_n;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3 && !rc; rep++) {
+                if (cudaEventRecord(e0, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+                if (!rc) rc = batched_exec(st, p->d, L, 5);
+                if (!rc && cudaEventRecord(e1, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
+                if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = SKEW_ERR_CUDA;
+                float t = 0.f;
+                if (!rc && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = SKEW_ERR_CUDA;
+                if (!rc && rep > 0 && t < ms) ms = t;  // the first run warms up
+            }
+            if (rc) break;
+            if (ncand < cap) {
+                if (cand_ctas) cand_ctas[ncand] = ctas;
+                if (cand_smem) cand_smem[ncand] = L.smem_n;
+                if (cand_ms) cand_ms[ncand] = ms;
+            }
+            if (ncand == 0 || ms < best_ms) {
+                best_ms = ms;
+                best_cfg = skew_batched_config{ctas, L.smem_n, {0, 0}};
+                best_launch = L;
+            }
+            ncand++;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    // keep the fastest (its kernel attribute is set again for the launch)
+    if (batched_prepare(p->d, best_cfg, &best_launch)) return SKEW_ERR_LAUNCH;
+    p->cfg = best_cfg;
+    p->launch = best_launch;
+    if (best) *best = best_cfg;
+    return ncand;
+}
+
 int skew_eig_batched(int count, const int* n, const double* const* A, const int* lda, const int* nev,
                      double* const* lambda, double* const* Z_re, double* const* Z_im, const skew_opts* opts,
                      void* stream) {

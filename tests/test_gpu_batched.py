@@ -106,3 +106,72 @@ def test_inverse_iteration_failure_is_reported_per_matrix():
     lam, Zr, Zi, info = _solve(mats, [20, 100], opts=opts)
     assert info[0] == 0
     assert info[1] >= sk.SKEW_INFO_INVIT_BASE
+
+
+def _plan_batch(seed=9):
+    import torch
+    import inputs
+    import paper_1912_04062_gb300 as sk
+    sizes = [2, 3, 33, 64, 90, 128, 160, 161, 250, 400, 700, 1024]
+    mats = [inputs.prescribed(int(n), seed=seed + k)[0] for k, n in enumerate(sizes)]
+    nevs = [int(n) // 2 for n in sizes]
+    dA = [sk.fortran(torch.from_numpy(np.asfortranarray(A)).cuda()) for A in mats]
+    return sk, mats, nevs, dA
+
+
+def test_persistent_launch_results_do_not_depend_on_the_configuration():
+    # one persistent launch per batch; where a matrix lives (shared or global
+    # memory) and how many CTAs share an SM change nothing in its arithmetic,
+    # so every configuration returns bit-identical results
+    import torch
+    sk, mats, nevs, dA = _plan_batch()
+    ref = None
+    for cfg in [(1, 160), (2, 112), (3, 64), (4, 0), (2, 0), (1, 48)]:
+        plan = sk.BatchedPlan(dA, nevs, config=cfg)
+        plan.execute()
+        torch.cuda.synchronize()
+        assert np.all(plan.info[: len(mats)].cpu().numpy() == 0)
+        lam, Zr, Zi = plan.results()
+        got = [(l.cpu().numpy(), zr.cpu().numpy(), zi.cpu().numpy()) for l, zr, zi in zip(lam, Zr, Zi)]
+        if ref is None:
+            ref = got
+            for A, nev, (l, zr, zi) in zip(mats, nevs, got):
+                _check(A, nev, torch.from_numpy(l), torch.from_numpy(zr), torch.from_numpy(zi))
+        else:
+            for (a, b, c), (x, y, z) in zip(ref, got):
+                assert np.array_equal(a, x) and np.array_equal(b, y) and np.array_equal(c, z), cfg
+
+
+def test_persistent_launch_in_a_cuda_graph_and_tuned():
+    # the plan's execute step is launch-only: captured in a CUDA graph and
+    # replayed it gives the direct results; tuning times the candidates, keeps
+    # the fastest, and the plan still returns the same results
+    import torch
+    sk, mats, nevs, dA = _plan_batch(seed=40)
+    plan = sk.BatchedPlan(dA, nevs)
+    plan.execute()
+    torch.cuda.synchronize()
+    lam0 = [l.clone() for l in plan.results()[0]]
+    Z0 = [z.clone() for z in plan.results()[1]]
+    for l in plan.results()[0]:
+        l.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.execute(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(lam0, plan.results()[0]):
+        assert torch.equal(a, b)
+    best, cands = plan.tune()
+    assert len(cands) >= 4 and best in [(c, s_) for c, s_, _ in cands]
+    assert all(t > 0 for _, _, t in cands)
+    assert plan.config() == best
+    plan.execute()
+    torch.cuda.synchronize()
+    for a, b in zip(Z0, plan.results()[1]):
+        assert torch.equal(a, b)
+    assert np.all(plan.info[: len(mats)].cpu().numpy() == 0)

@@ -66,3 +66,24 @@ def test_lpt_partition_edge_cases():
         sk.shard_lpt([1], 0)
     # the largest matrix goes first to rank 0
     assert 1 in sk.shard_lpt(np.array([5, 50, 7]), 2)[0]
+
+
+def test_tuning_table_lookup(tmp_path):
+    # the batched solve's tuned launch configurations: exact size class, the
+    # nearest recorded class on the same GPU, the default elsewhere, and a
+    # round trip through the JSON file
+    from paper_1912_04062_gb300 import tuning
+    assert tuning.bucket([32, 1024, 500]) == "nmax<=1024,count<=16"
+    assert tuning.bucket(list(range(2, 2002))) == "nmax<=inf,count<=8192"
+    assert tuning.bucket([40] * 200) == "nmax<=64,count<=1024"
+    path = str(tmp_path / "t.json")
+    t = tuning.record("GPU A", [32] * 2000 + [1024], (3, 96), [(1, 0, 9.0), (3, 96, 4.5)], path=path)
+    assert t["GPU A"]["nmax<=1024,count<=8192"]["ctas_per_sm"] == 3
+    tuning.record("GPU A", [50] * 10, (4, 64), [(4, 64, 1.0)], path=path)
+    table = tuning.load(path)
+    assert tuning.lookup("GPU A", [32] * 2000 + [1024], table) == (3, 96)
+    assert tuning.lookup("GPU A", [60] * 12, table) == (4, 64)
+    # nearest class: order class 1024 first, then the count class
+    assert tuning.lookup("GPU A", [900] * 100, table) == (3, 96)
+    assert tuning.lookup("GPU B", [900] * 100, table) == tuning.DEFAULT
+    assert tuning.lookup("GPU A", [], {}) == tuning.DEFAULT
