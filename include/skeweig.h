@@ -150,8 +150,11 @@ void skew_release_memory(void);
 int skew_eig(int n, const double* A, int lda, int nev, double* lambda,
              double* Z_re, double* Z_im, void* stream);
 
-/* Bytes of device workspace skew_eig_ex needs for (n, nev, opts). */
+/* Bytes of device workspace skew_eig_ex needs for (n, nev, opts), with
+ * eigenvectors; the _ex form takes vectors = 0 for an eigenvalues-only solve
+ * (Z_re == Z_im == NULL), which needs far less. */
 size_t skew_eig_workspace_size(int n, int nev, const skew_opts* opts);
+size_t skew_eig_workspace_size_ex(int n, int nev, const skew_opts* opts, int vectors);
 
 /*
  * Asynchronous full solve with caller workspace (>= skew_eig_workspace_size

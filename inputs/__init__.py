@@ -155,3 +155,39 @@ def bse_device(n: int, seed: int = 3, device="cuda"):
     del JL, L
     K = 0.5 * (K - K.T)
     return K.T.contiguous().T
+
+
+def clustered_device(n: int, seed: int = 4, frac: float = 0.05, group: int = 16, width: float = 1e-10,
+                     device="cuda"):
+    """``clustered(n, seed)`` with the orthogonal factor and the products on the
+    GPU: the same random draws (the spectrum, the cluster placement and the
+    N(0,1) matrix, drawn with numpy in the same order), then Q from the QR of
+    that matrix with the signs of diag(R) folded in, A = Q blockdiag Q^T and
+    A = (A - A^T)/2 in FP64 on the device.  Returns (A as a column-major CUDA
+    tensor, l)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    m = n // 2
+    l = np.exp(rng.uniform(np.log(1e-6), np.log(1.0), size=m))
+    nclu = int(frac * m) // group
+    idx = rng.permutation(m)[: nclu * group]
+    for g in range(nclu):
+        c = np.exp(rng.uniform(np.log(1e-6), np.log(1.0)))
+        l[idx[g * group:(g + 1) * group]] = c + rng.uniform(-0.5, 0.5, size=group) * width
+    G = torch.from_numpy(rng.standard_normal((n, n))).to(device)
+    Q, R = torch.linalg.qr(G)
+    del G
+    s = torch.sign(torch.diagonal(R))
+    s[s == 0] = 1.0
+    del R
+    Q *= s[None, :]
+    # Q blockdiag([0 l_j; -l_j 0]) scales and swaps column pairs: column 2j of
+    # the product is -l_j q_{2j+1}, column 2j+1 is l_j q_{2j}
+    lt = torch.from_numpy(l).to(device)
+    QB = torch.zeros_like(Q)
+    QB[:, 0:2 * m:2] = -Q[:, 1:2 * m:2] * lt[None, :]
+    QB[:, 1:2 * m:2] = Q[:, 0:2 * m:2] * lt[None, :]
+    A = QB @ Q.T
+    del QB, Q
+    A = 0.5 * (A - A.T)
+    return A.T.contiguous().T, l

@@ -50,6 +50,7 @@ SIGNATURES = {
     "skew_last_cuda_error": (ctypes.c_char_p, []),
     "skew_eig": (_i, [_i, _p, _i, _i, _p, _p, _p, _p]),
     "skew_eig_workspace_size": (_sz, [_i, _i, _p]),
+    "skew_eig_workspace_size_ex": (_sz, [_i, _i, _p, _i]),
     "skew_eig_ex": (_i, [_i, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
     "skew_eig_host": (_i, [_i, _p, _i, _i, _p, _p, _p, _p, _p]),
     "skew_eig_batched_workspace_size": (_sz, [_i, _p, _p, _p]),
@@ -216,9 +217,11 @@ def skew_eig(A, nev: int, vectors: bool = True, stream=None):
     return lam[:nev], Zr, Zi
 
 
-def workspace_size(n: int, nev: int, opts: Options | None = None) -> int:
+def workspace_size(n: int, nev: int, opts: Options | None = None, vectors: bool = True) -> int:
     o = (opts or Options()).c()
-    return int(lib().skew_eig_workspace_size(n, nev, ctypes.byref(o)))
+    if vectors:
+        return int(lib().skew_eig_workspace_size(n, nev, ctypes.byref(o)))
+    return int(lib().skew_eig_workspace_size_ex(n, nev, ctypes.byref(o), 0))
 
 
 def skew_eig_ex(A, nev: int, lam, Zr, Zi, workspace, d_info, opts: Options | None = None, stream=None) -> int:

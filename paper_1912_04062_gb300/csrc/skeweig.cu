@@ -505,6 +505,11 @@ size_t skew_eig_workspace_size(int n, int nev, const skew_opts* opts) {
     return plan_bytes(n, nev, opts, true);
 }
 
+size_t skew_eig_workspace_size_ex(int n, int nev, const skew_opts* opts, int vectors) {
+    if (n < 0 || nev < 0) return 0;
+    return plan_bytes(n, nev, opts, vectors != 0);
+}
+
 int skew_eig_ex(int n, const double* A, int lda, int nev, double* lambda, double* Z_re, double* Z_im, int ldz,
                 const skew_opts* opts, void* workspace, size_t ws_bytes, int* d_info, void* stream) {
     int rc = check_args(n, A, lda, nev, lambda, Z_re, Z_im);

@@ -103,3 +103,14 @@ def test_bse_device_follows_the_same_recipe():
     K = inputs.bse(n, seed=seed)
     assert np.array_equal(Kd, -Kd.T)
     assert np.max(np.abs(Kd - K)) <= 1e-13 * np.max(np.abs(K))
+
+
+def test_clustered_device_recipe_follows_the_numpy_one():
+    # the GPU-side construction of the clustered workload draws the same
+    # numbers in the same order; on torch's CPU backend it reproduces the
+    # numpy matrix to rounding and the spectrum exactly
+    A1, l1 = inputs.clustered(150, seed=4)
+    A2, l2 = inputs.clustered_device(150, seed=4, device="cpu")
+    assert np.array_equal(l1, l2)
+    assert np.max(np.abs(A1 - A2.numpy())) <= 1e-14
+    assert A2.stride(0) == 1  # column-major
