@@ -104,8 +104,17 @@ typedef struct {
                           refined together by Rayleigh-Ritz (clusters of up to 16);
                           0 -> 1024 */
     int qtrd;          /* arithmetic of the Q_trd back-transform: SKEW_QTRD_* */
-    int reserved[1];
+    int tridiag;       /* Sturm counts of the FP64 bisection: SKEW_TRIDIAG_* */
 } skew_opts;
+
+/* skew_opts.tridiag.  SKEW_TRIDIAG_AUTO (0): the FP64 bisection finish counts
+ * on the zero-diagonal form of tridiag(alpha, 0, alpha) (Sec. 2.2, remark
+ * after Algorithm 1): shuffled even-first it is [[0, B], [B^T, 0]] with B
+ * bidiagonal, its eigenvalues >= 0 are the square roots of those of B B^T, and
+ * the count of B B^T at x^2 (stationary qd transform) takes ceil(n/2) steps
+ * instead of n.  SKEW_TRIDIAG_FULL (1): the Sturm count of S itself. */
+#define SKEW_TRIDIAG_AUTO 0
+#define SKEW_TRIDIAG_FULL 1
 
 /* skew_opts.qtrd: SKEW_QTRD_AUTO (0) takes the mode's choice (FP64 in the FP64
  * form and whenever the mixed modes do not refine; FP32 SIMT when they

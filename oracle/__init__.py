@@ -61,6 +61,7 @@ def _load():
         lib.oracle_dmap.argtypes = [i, i, d, i, d, d, i]
         lib.oracle_dmap.restype = None
         lib.oracle_skew_eig.argtypes = [i, d, i, i, d, d, d, i]
+        lib.oracle_bidiag_bisect.argtypes = [i, d, i, d]
         lib.oracle_set_threads.argtypes = [i]
         lib.oracle_set_threads.restype = i
         _lib = lib
@@ -118,6 +119,23 @@ def bisect(alpha: np.ndarray, nev: int) -> np.ndarray:
     rc = _load().oracle_bisect(n, _p(a), nev, _p(lam))
     if rc != 0:
         raise RuntimeError(f"oracle_bisect failed: {rc}")
+    return lam[:nev].copy()
+
+
+def bidiag_bisect(alpha: np.ndarray, nev: int) -> np.ndarray:
+    """The nev largest eigenvalues (descending, nev <= n/2) of
+    tridiag(alpha, 0, alpha) from its zero-diagonal form: square roots of the
+    eigenvalues of B B^T, B the bidiagonal of the perfect-shuffled matrix
+    (Sec. 2.2, remark after Algorithm 1), by bisection with stationary-qd
+    counts over n/2 steps."""
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    n = alpha.size + 1
+    lam = np.zeros(max(nev, 1))
+    a = np.zeros(max(n, 1))
+    a[: alpha.size] = alpha
+    rc = _load().oracle_bidiag_bisect(n, _p(a), nev, _p(lam))
+    if rc != 0:
+        raise RuntimeError(f"oracle_bidiag_bisect failed: {rc}")
     return lam[:nev].copy()
 
 

@@ -249,6 +249,84 @@ int oracle_bisect(int n, const double *alpha, int nev, double *lambda)
     return 0;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Zero-diagonal form (the remark after Algorithm 1 in Sec. 2.2: a solver that
+ * uses the zero diagonal of tridiag(alpha, 0, alpha) may pay off).  Ordering
+ * the unknowns even indices first, odd second (a perfect shuffle), S becomes
+ * [[0, B], [B^T, 0]] with B lower bidiagonal, ceil(n/2) x floor(n/2):
+ *   B[i][i] = a_i = alpha_{2i},  B[i+1][i] = b_i = alpha_{2i+1}
+ * (alpha_j = 0 for j > n-2).  The eigenvalues of S are +-sigma(B), and 0 when
+ * n is odd, so its eigenvalues >= 0 are the square roots of the eigenvalues
+ * of B B^T (order ceil(n/2)).  B B^T = L D L^T with D_i = a_i^2 and the unit
+ * lower bidiagonal L of l_i = b_i / a_i; the stationary qd transform
+ * L D L^T - t I = L+ D+ L+^T gives, with s_0 = -t,
+ *   D+_i = a_i^2 + s_i,   s_{i+1} = b_i^2 s_i / D+_i - t,
+ * and the number of negative D+_i is the number of eigenvalues of B B^T below
+ * t (Sylvester's law of inertia).  Pivots of modulus below pivmin are replaced
+ * by -pivmin, as in the Sturm count above.  The counts work with squares, so
+ * singular values below about 1e-154 times the scale are resolved to absolute
+ * accuracy only (the full-length count has the same kind of floor).       */
+static int bidiag_count(int m, const double *a2, const double *b2, double pivmin, double t)
+{
+    int cnt = 0;
+    double sv = -t;
+    for (int i = 0; i < m; i++) {
+        double d = a2[i] + sv;
+        if (fabs(d) < pivmin) d = -pivmin;
+        if (d < 0.0) cnt++;
+        sv = b2[i] * sv / d - t;
+    }
+    return cnt;
+}
+
+/* The nev largest eigenvalues of S = tridiag(alpha, 0, alpha), descending,
+ * as sqrt of the eigenvalues of B B^T found by bisection on x in [0, g] with
+ * counts at t = x^2; same stopping rule as oracle_bisect.  nev <= n/2 (the
+ * nonnegative half; for odd n the zero eigenvalue is the (n+1)/2-th).      */
+int oracle_bidiag_bisect(int n, const double *alpha, int nev, double *lambda)
+{
+    if (n <= 0 || nev <= 0) return 0;
+    if (n == 1) { lambda[0] = 0.0; return 0; }
+    const int m = (n + 1) / 2;
+    double *a2 = (double *)malloc(sizeof(double) * (size_t)m);
+    double *b2 = (double *)malloc(sizeof(double) * (size_t)m);
+    if (!a2 || !b2) { free(a2); free(b2); return -1; }
+    double amax = 0.0;
+    for (int i = 0; i < m; i++) {
+        const double a = (2 * i <= n - 2) ? alpha[2 * i] : 0.0;
+        const double b = (2 * i + 1 <= n - 2) ? alpha[2 * i + 1] : 0.0;
+        a2[i] = a * a;
+        b2[i] = b * b;
+        if (a2[i] > amax) amax = a2[i];
+        if (b2[i] > amax) amax = b2[i];
+    }
+    const double pivmin = DBL_MIN * (amax > 1.0 ? amax : 1.0);
+    const double g = gersh(n, alpha);
+    if (g == 0.0) {
+        for (int k = 0; k < nev; k++) lambda[k] = 0.0;
+        free(a2); free(b2);
+        return 0;
+    }
+    const double ghi = g + 2.0 * DBL_EPSILON * g + pivmin;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int k = 0; k < nev; k++) {
+        const int j = m - 1 - k;        /* 0-based ascending index in B B^T */
+        double lo = 0.0, hi = ghi;      /* count(lo^2) <= j < count(hi^2) */
+        for (int it = 0; it < 4000; it++) {
+            double w = hi - lo;
+            double tol = 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_MIN;
+            if (w <= tol) break;
+            double mid = lo + 0.5 * w;
+            if (mid <= lo || mid >= hi) break;
+            if (bidiag_count(m, a2, b2, pivmin, mid * mid) <= j) lo = mid;
+            else hi = mid;
+        }
+        lambda[k] = lo + 0.5 * (hi - lo);
+    }
+    free(a2); free(b2);
+    return 0;
+}
+
 /* counter-based start vector: splitmix64 of (seed, index) -> uniform(-1,1) */
 static double start_entry(uint64_t seed, uint64_t i)
 {

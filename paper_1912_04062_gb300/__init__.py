@@ -41,6 +41,8 @@ SKEW_QTRD_AUTO = 0
 SKEW_QTRD_FP32 = 1
 SKEW_QTRD_FP64 = 2
 SKEW_QTRD_TC = 3
+SKEW_TRIDIAG_AUTO = 0
+SKEW_TRIDIAG_FULL = 1
 
 # every entry point the header declares: name -> (restype, argtypes)
 _i, _d, _p, _sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
@@ -106,7 +108,7 @@ SIGNATURES = {
 class skew_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("band", ctypes.c_int), ("check_finite", ctypes.c_int),
                 ("fault", ctypes.c_int), ("refine_iters", ctypes.c_int), ("refine_rho", ctypes.c_int),
-                ("qtrd", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("qtrd", ctypes.c_int), ("tridiag", ctypes.c_int)]
 
 
 class skew_batched_config(ctypes.Structure):
@@ -193,6 +195,7 @@ class Options:
     refine_iters: int = 0
     refine_rho: int = 0
     qtrd: int = 0
+    tridiag: int = 0
 
     def c(self):
         o = skew_opts()
@@ -201,6 +204,7 @@ class Options:
         o.refine_iters = self.refine_iters
         o.refine_rho = self.refine_rho
         o.qtrd = self.qtrd
+        o.tridiag = self.tridiag
         return o
 
 

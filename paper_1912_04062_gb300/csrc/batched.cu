@@ -37,6 +37,7 @@ struct BItem {
     int* info;                   // caller's status word of this matrix (may be null)
     // per-matrix scratch
     double *V, *tau, *alpha, *a2, *Qi;
+    double *a2e, *b2e;  // the bidiagonal of the zero-diagonal form, squared (ceil(n/2) each)
     tri::TriScalars* sc;
     tri::InvitBufs bf;
     int* fail;
@@ -136,6 +137,13 @@ __device__ void bt_reduce_body(const BItem& it, double* S, int ld, double* v, do
         gm = fmax(gm, fabs(al) + fabs(ap));
         am = fmax(am, al * al);
     }
+    // the zero-diagonal form's bidiagonal: a_i = alpha_{2i}, b_i = alpha_{2i+1}
+    for (int i = t; i < (n + 1) / 2; i += BT) {
+        const double a = (2 * i <= n - 2) ? it.alpha[2 * i] : 0.0;
+        const double b = (2 * i + 1 <= n - 2) ? it.alpha[2 * i + 1] : 0.0;
+        it.a2e[i] = a * a;
+        it.b2e[i] = b * b;
+    }
     gm = block_max(gm, red);
     am = block_max(am, red);
     if (t == 0) {
@@ -233,7 +241,9 @@ bt_persistent_kernel(const BItem* __restrict__ items, const int* __restrict__ or
         }
         // every wanted eigenvalue of this matrix (Sturm bisection), then
         // inverse iteration per cluster leader
-        for (int k = t; k < nev; k += BT) it.lambda[k] = tri::bisect_one(n, n - 1 - k, it.a2, it.sc->g, it.sc->pivmin);
+        // (counts on the zero-diagonal form: ceil(n/2) steps; nev <= n/2)
+        for (int k = t; k < nev; k += BT)
+            it.lambda[k] = tri::bisect_one_bd((n + 1) / 2, k, it.a2e, it.b2e, it.sc->g, it.sc->pivmin);
         __syncthreads();
         if (it.vectors) {
             const double ctol = fmin(1e-3, 10.0 / ((double)n * sqrt((double)n)));
@@ -287,6 +297,8 @@ size_t carve_small(Carve& cv, int count, const BatchProblem* pr, BCarve* out) {
         it.tau = cv.take<double>(n);
         it.alpha = cv.take<double>(n);
         it.a2 = cv.take<double>(n);
+        it.a2e = cv.take<double>(n / 2 + 1);
+        it.b2e = cv.take<double>(n / 2 + 1);
         it.sc = cv.take<tri::TriScalars>(1);
         it.fail = cv.take<int>(1);
         if (it.vectors) {

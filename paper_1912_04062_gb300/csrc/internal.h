@@ -73,8 +73,11 @@ size_t tridiag_ws(int n, int nev);
 // Vectors go to Qi in interleaved layout Qi[i * nev + k].
 // fp64 = false: eigenvalues to about 2^-42 ||S|| from double-float counts
 // only (a caller that refines them afterwards); otherwise finished in FP64.
+// bidiag: the FP64 bisection finish counts on the zero-diagonal form (B B^T
+// of the perfect-shuffled bidiagonal, half-length recurrences; nev <= n/2).
 int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* lambda,
-                double* Qi, void* ws, size_t ws_bytes, int* d_status, int maxit, bool fp64 = true);
+                double* Qi, void* ws, size_t ws_bytes, int* d_status, int maxit, bool fp64 = true,
+                bool bidiag = true);
 // Interleaved Qi -> column-major X (and Y) with optional D map.
 cudaError_t interleaved_to_colmajor(cudaStream_t st, int n, int nev, const double* Qi,
                                     double* X, double* Y, int ldz, bool dmap);

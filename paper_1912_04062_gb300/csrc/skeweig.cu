@@ -232,7 +232,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     // with refinement the eigenvalues are recomputed from the Rayleigh
     // quotients: the double-float brackets suffice to start from
     rc = tridiag_eig(st, n, p.alpha, nev, lambda, vectors ? p.Qi : nullptr, p.ws_tri, p.sz_tri, p.status, maxit,
-                     !p.refine);
+                     !p.refine, !(o && o->tridiag == SKEW_TRIDIAG_FULL));
     if (rc) return rc;
     mark(5);
     if (vectors) {

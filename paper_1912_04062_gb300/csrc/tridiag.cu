@@ -47,7 +47,15 @@ using namespace tri;
 
 __global__ void tri_prep_kernel(int n, const double* __restrict__ alpha, double* __restrict__ a2,
                                 float* __restrict__ a2s, float* __restrict__ a2l, float* __restrict__ alh,
-                                float* __restrict__ all_, TriScalars* sc) {
+                                float* __restrict__ all_, TriScalars* sc, double* __restrict__ a2e,
+                                double* __restrict__ b2e) {
+    // the bidiagonal of the zero-diagonal form: a_i = alpha_{2i}, b_i = alpha_{2i+1}
+    for (int i = threadIdx.x; i < (n + 1) / 2; i += blockDim.x) {
+        const double a = (2 * i <= n - 2) ? alpha[2 * i] : 0.0;
+        const double b = (2 * i + 1 <= n - 2) ? alpha[2 * i + 1] : 0.0;
+        a2e[i] = a * a;
+        b2e[i] = b * b;
+    }
     __shared__ double red[32];
     double gmax = 0.0, amax = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -215,20 +223,28 @@ constexpr double DF_SLACK = 1.0 / 68719476736.0;  // 2^-36: widening of a double
 // the start is the double-float bracket (units of g) widened by DF_SLACK g
 // once its ends pass the FP64 counts count(lo) <= j < count(hi); a bracket
 // that fails is widened eightfold, up to the whole Gershgorin interval.
-template <int L>
+// BD: counts from the zero-diagonal form (B B^T at x^2, m = ceil(n/2) steps;
+// the wanted eigenvalues are >= 0, so the search stays in [0, g]).
+template <int L, bool BD = false>
 __global__ void bisect_kernel(int n, int nev, const double* __restrict__ a2, const TriScalars* sc,
-                              const double* __restrict__ lohi, double* __restrict__ lambda) {
+                              const double* __restrict__ lohi, double* __restrict__ lambda,
+                              const double* __restrict__ a2e = nullptr, const double* __restrict__ b2e = nullptr) {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gt / L, q = gt % L, lane = threadIdx.x & 31;
     if (k >= nev) return;  // whole lane groups leave together (blockDim is a multiple of L)
     const unsigned gmask = (L == 1) ? (1u << lane) : (((1u << L) - 1u) << (lane & ~(L - 1)));
     const double g = sc->g, pivmin = sc->pivmin;
-    const int j = n - 1 - k;  // ascending index of the wanted eigenvalue
+    const int m = (n + 1) / 2;
+    const int j = BD ? m - 1 - k : n - 1 - k;  // ascending index of the wanted eigenvalue
+    // count(x) <= j: the wanted eigenvalue is >= x
+    auto below = [&](double x) -> bool {
+        return BD ? bd_count(m, a2e, b2e, pivmin, x * x) <= j : sturm(n, a2, pivmin, x) <= j;
+    };
     if (n == 1 || g == 0.0) {
         if (q == 0) lambda[k] = 0.0;
         return;
     }
-    const double glo = -g - 2.0 * DBL_EPSILON * g - pivmin, ghi = g + 2.0 * DBL_EPSILON * g + pivmin;
+    const double glo = BD ? 0.0 : -g - 2.0 * DBL_EPSILON * g - pivmin, ghi = g + 2.0 * DBL_EPSILON * g + pivmin;
     double lo = glo, hi = ghi;
     if (lohi) {
         double slack = DF_SLACK * g;
@@ -236,12 +252,12 @@ __global__ void bisect_kernel(int n, int nev, const double* __restrict__ a2, con
             const double a = fmax(glo, lohi[2 * k] * g - slack), b = fmin(ghi, lohi[2 * k + 1] * g + slack);
             bool ok;
             if (L == 1) {
-                ok = (a == glo || sturm(n, a2, pivmin, a) <= j) && (b == ghi || sturm(n, a2, pivmin, b) > j);
+                ok = (a == glo || below(a)) && (b == ghi || !below(b));
             } else {
                 // lane 0 checks the lower end, lane 1 the upper one
                 bool mine = true;
-                if (q == 0) mine = (a == glo) || sturm(n, a2, pivmin, a) <= j;
-                if (q == 1) mine = (b == ghi) || sturm(n, a2, pivmin, b) > j;
+                if (q == 0) mine = (a == glo) || below(a);
+                if (q == 1) mine = (b == ghi) || !below(b);
                 ok = (__ballot_sync(gmask, !mine) & gmask) == 0u;
             }
             if (ok) {
@@ -258,7 +274,7 @@ __global__ void bisect_kernel(int n, int nev, const double* __restrict__ a2, con
         if (w <= tol) break;
         const double step = w / (double)(L + 1);
         const double x = lo + (double)(q + 1) * step;
-        const bool le = (x > lo && x < hi) ? (sturm(n, a2, pivmin, x) <= j) : (x <= lo);
+        const bool le = (x > lo && x < hi) ? below(x) : (x <= lo);
         // counts grow with x: the lanes with lambda_j >= x_q are a prefix
         const int nle = (L == 1) ? (le ? 1 : 0) : __popc(__ballot_sync(gmask, le) & gmask);
         const double nlo = (nle > 0) ? lo + (double)nle * step : lo;
@@ -338,6 +354,7 @@ __global__ void dmap_colmajor_kernel(int n, int k, const double* __restrict__ Q,
 
 struct TriWs {
     double* a2;
+    double *a2e, *b2e;  // alpha_{2i}^2, alpha_{2i+1}^2 (zero-diagonal form, ceil(n/2) each)
     float *a2s, *a2l;  // alpha^2 / g^2 as an FP32 pair (bracketing passes)
     float *alh, *all_;  // alpha as an FP32 pair (double-float inverse iteration)
     double* lohi;   // FP32 brackets, 2 per wanted eigenvalue
@@ -350,6 +367,8 @@ TriWs carve_tri(Carve& cv, int n, int nev) {
     TriWs w{};
     size_t nn = (size_t)(n > 0 ? n : 1), ne = (size_t)(nev > 0 ? nev : 1);
     w.a2 = cv.take<double>(nn);
+    w.a2e = cv.take<double>(nn / 2 + 1);
+    w.b2e = cv.take<double>(nn / 2 + 1);
     w.a2s = cv.take<float>(nn);
     w.a2l = cv.take<float>(nn);
     w.alh = cv.take<float>(nn);
@@ -374,19 +393,24 @@ size_t tridiag_ws(int n, int nev) {
 }
 
 int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* lambda, double* Qi, void* ws,
-                size_t ws_bytes, int* d_status, int maxit, bool fp64) {
+                size_t ws_bytes, int* d_status, int maxit, bool fp64, bool bidiag) {
     if (n <= 0 || nev <= 0) return 0;
     Carve cv(ws, ws_bytes);
     TriWs w = carve_tri(cv, n, nev);
     if (!cv.ok) return SKEW_ERR_WORKSPACE;
-    tri_prep_kernel<<<1, 1024, 0, st>>>(n, alpha, w.a2, w.a2s, w.a2l, w.alh, w.all_, w.sc);
+    tri_prep_kernel<<<1, 1024, 0, st>>>(n, alpha, w.a2, w.a2s, w.a2l, w.alh, w.all_, w.sc, w.a2e, w.b2e);
     count_launch();
     {
         KtScope kt(st, KT_BISECT);
         bisect32_kernel<<<(4 * nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2s, w.sc, w.lohi);
         bisect_df_kernel<<<(4 * nev + 127) / 128, 128, 0, st>>>(n, nev, w.a2s, w.a2l, w.sc, w.lohi, lambda);
         count_launch(2);
-        if (fp64) {
+        if (fp64 && bidiag && 2 * nev <= n) {
+            // FP64 finish on the zero-diagonal form (half-length counts)
+            bisect_kernel<BISECT_LANES, true><<<(BISECT_LANES * nev + 63) / 64, 64, 0, st>>>(
+                n, nev, w.a2, w.sc, w.lohi, lambda, w.a2e, w.b2e);
+            count_launch();
+        } else if (fp64) {
             bisect_kernel<BISECT_LANES><<<(BISECT_LANES * nev + 63) / 64, 64, 0, st>>>(n, nev, w.a2, w.sc, w.lohi,
                                                                                         lambda);
             count_launch();

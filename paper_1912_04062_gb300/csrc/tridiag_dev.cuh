@@ -45,6 +45,46 @@ __device__ __forceinline__ double bisect_one(int n, int j, const double* __restr
     return lo + 0.5 * (hi - lo);
 }
 
+// Zero-diagonal form (Sec. 2.2, remark after Algorithm 1): with the unknowns
+// shuffled even first, S = [[0, B], [B^T, 0]], B lower bidiagonal with
+// diagonal a_i = alpha_{2i} and subdiagonal b_i = alpha_{2i+1}; the
+// eigenvalues >= 0 of S are the square roots of those of B B^T (order
+// m = ceil(n/2)).  Number of eigenvalues of B B^T below t from the stationary
+// qd transform of its L D L^T form (D_i = a_i^2, l_i = b_i / a_i):
+// D+_i = a_i^2 + s_i, s_{i+1} = b_i^2 s_i / D+_i - t, s_0 = -t (one division per
+// step over m steps, against n steps of the full Sturm count).
+__device__ __forceinline__ int bd_count(int m, const double* __restrict__ a2e, const double* __restrict__ b2e,
+                                        double pivmin, double t) {
+    int cnt = 0;
+    double sv = -t;
+    for (int i = 0; i < m; i++) {
+        double d = a2e[i] + sv;
+        if (fabs(d) < pivmin) d = -pivmin;
+        cnt += (d < 0.0);
+        sv = b2e[i] * sv / d - t;
+    }
+    return cnt;
+}
+
+// The k-th largest eigenvalue (k < n/2) of S by bisection on x in [0, g] with
+// counts of B B^T at t = x^2 (ascending index m - 1 - k there).
+__device__ __forceinline__ double bisect_one_bd(int m, int k, const double* __restrict__ a2e,
+                                                const double* __restrict__ b2e, double g, double pivmin) {
+    if (m <= 1 || g == 0.0) return 0.0;
+    const int j = m - 1 - k;
+    double lo = 0.0, hi = g + 2.0 * DBL_EPSILON * g + pivmin;
+    for (int it = 0; it < 4000; it++) {
+        double w = hi - lo;
+        double tol = 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_MIN;
+        if (w <= tol) break;
+        double mid = lo + 0.5 * w;
+        if (mid <= lo || mid >= hi) break;
+        if (bd_count(m, a2e, b2e, pivmin, mid * mid) <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo + 0.5 * (hi - lo);
+}
+
 __device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long i) {
     // splitmix64 (Steele, Lea, Flood 2014) of seed * golden + i -> uniform(-1, 1)
     unsigned long long z = seed * 0x9E3779B97F4A7C15ULL + i + 0x632BE59BD9B4E019ULL;

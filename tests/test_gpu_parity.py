@@ -360,3 +360,39 @@ def test_device_metrics_match_definitions():
     G = (Xp[:, cols].T @ Xp + Y[:, cols].T @ Y) - np.eye(nev)[cols]
     H = Xp[:, cols].T @ Y - Y[:, cols].T @ Xp
     assert o2 == pytest.approx(np.sqrt(np.sum(G * G) + np.sum(H * H)), rel=1e-6)
+
+
+@pytest.mark.parametrize("n", [3, 64, 65, 301, 1000])
+def test_zero_diagonal_bisection_matches_oracle(n):
+    # the FP64 bisection finish on the zero-diagonal form (counts of B B^T,
+    # ceil(n/2) steps) against the oracle's zero-diagonal bisection and its
+    # full-length one; the whole solve with either count gives the same
+    # eigenvalues to a few units of rounding
+    import paper_1912_04062_gb300 as sk
+    torch = _torch()
+    rng = np.random.default_rng(5100 + n)
+    a = rng.uniform(-2, 2, n - 1)
+    nev = n // 2
+    lam, Q, st = sk.tridiag_eig(torch.from_numpy(a).cuda(), nev)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    lam = lam.cpu().numpy()
+    scale = np.max(np.abs(lam))
+    assert np.max(np.abs(lam - oracle.bidiag_bisect(a, nev))) <= 4 * EPS * scale
+    assert np.max(np.abs(lam - oracle.bisect(a, nev))) <= 4 * EPS * scale
+    A = inputs.random_skew(n, seed=5200 + n)
+    out = {}
+    for mode in (sk.SKEW_TRIDIAG_AUTO, sk.SKEW_TRIDIAG_FULL):
+        opts = sk.Options(tridiag=mode)
+        dA = to_dev(A)
+        ws = torch.empty(sk.workspace_size(n, nev, opts), dtype=torch.uint8, device="cuda")
+        lm = torch.empty(nev, dtype=torch.float64, device="cuda")
+        Zr, Zi = sk.fortran_empty(n, nev), sk.fortran_empty(n, nev)
+        info = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        assert sk.skew_eig_ex(dA, nev, lm, Zr, Zi, ws, info, opts) == 0
+        torch.cuda.synchronize()
+        assert int(info.item()) == 0
+        out[mode] = lm.cpu().numpy()
+        m = oracle.scaled_metrics(A, out[mode], Zr.cpu().numpy(), Zi.cpu().numpy())
+        assert m["resid"] <= 50 and m["orth"] <= 50
+    assert np.max(np.abs(out[0] - out[1])) <= 4 * EPS * np.max(np.abs(out[1]))

@@ -280,3 +280,52 @@ def test_oracle_results_do_not_depend_on_the_thread_count():
         oracle.set_threads(max(before, 1))
     for a, b in zip(r1[:3], r4[:3]):
         assert np.array_equal(a, b)
+
+
+# --- zero-diagonal form (Sec. 2.2, remark after Algorithm 1) ----------------------
+def _shuffled_bidiagonal(alpha):
+    n = alpha.size + 1
+    m = (n + 1) // 2
+    B = np.zeros((m, n // 2))
+    for i in range(m):
+        if 2 * i <= n - 2:
+            B[i, i] = alpha[2 * i]
+        if 2 * i + 1 <= n - 2 and i + 1 < m:
+            B[i + 1, i] = alpha[2 * i + 1]
+    return B
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 16, 17, 100, 101])
+def test_bidiag_bisect_unit_closed_form(n):
+    # tridiag(1, 0, 1): eigenvalues 2 cos(k pi / (n + 1)), k = 1..n
+    lam = oracle.bidiag_bisect(np.ones(n - 1), n // 2)
+    ref = np.sort(2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))[::-1][: n // 2]
+    assert np.max(np.abs(lam - ref)) <= 8 * EPS * 2
+
+
+@pytest.mark.parametrize("n", [3, 8, 63, 64, 257, 600])
+def test_bidiag_bisect_matches_bisection_and_lapack_svd(n):
+    rng = np.random.default_rng(900 + n)
+    a = rng.uniform(-2, 2, n - 1)
+    nev = n // 2
+    lam = oracle.bidiag_bisect(a, nev)
+    assert np.all(np.diff(lam) <= 0) and lam[-1] >= 0
+    # the full-length Sturm bisection of the same matrix
+    assert np.max(np.abs(lam - oracle.bisect(a, nev))) <= 4 * EPS * np.max(np.abs(lam))
+    # singular values of the perfect-shuffled bidiagonal (LAPACK)
+    sv = np.sort(np.linalg.svd(_shuffled_bidiagonal(a), compute_uv=False))[::-1][:nev]
+    assert np.max(np.abs(lam - sv)) <= 50 * n * EPS * np.max(np.abs(lam))
+
+
+def test_bidiag_bisect_split_matrix_is_exact_to_relative_rounding():
+    # alpha with zeros at odd positions: S splits into 2 x 2 blocks
+    # [[0, a], [a, 0]] with eigenvalues +-|a|; the counts work with squares,
+    # so down to |a| ~ 1e-150 (squares above the smallest normal double) the
+    # relative stopping rule returns each to a few units of relative rounding
+    vals = np.array([1e-100, 3e-60, 2.5, 7e-8, 1.0, 4e-140])
+    n = 2 * vals.size
+    alpha = np.zeros(n - 1)
+    alpha[0::2] = vals * np.array([1, -1, 1, -1, 1, 1])
+    lam = oracle.bidiag_bisect(alpha, vals.size)
+    ref = np.sort(vals)[::-1]
+    assert np.all(np.abs(lam - ref) <= 4 * EPS * ref)
