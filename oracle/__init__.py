@@ -62,6 +62,7 @@ def _load():
         lib.oracle_dmap.restype = None
         lib.oracle_skew_eig.argtypes = [i, d, i, i, d, d, d, i]
         lib.oracle_bidiag_bisect.argtypes = [i, d, i, d]
+        lib.oracle_bidiag_vectors.argtypes = [i, d, i, d, d, i]
         lib.oracle_set_threads.argtypes = [i]
         lib.oracle_set_threads.restype = i
         _lib = lib
@@ -137,6 +138,23 @@ def bidiag_bisect(alpha: np.ndarray, nev: int) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"oracle_bidiag_bisect failed: {rc}")
     return lam[:nev].copy()
+
+
+def bidiag_vectors(alpha: np.ndarray, lam: np.ndarray):
+    """Eigenvectors of tridiag(alpha, 0, alpha) for eigenvalues lam > 0
+    (descending) from the zero-diagonal form: inverse iteration on B B^T for
+    the even rows u, v = B^T u / lambda on the odd rows.  Returns (Q, info)."""
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    n = alpha.size + 1
+    nev = lam.size
+    a = np.zeros(max(n, 1))
+    a[: alpha.size] = alpha
+    Q = np.zeros((n, max(nev, 1)), order="F")
+    info = _load().oracle_bidiag_vectors(n, _p(a), nev, _p(lam), _p(Q), n)
+    if info < 0:
+        raise RuntimeError(f"oracle_bidiag_vectors failed: {info}")
+    return Q[:, :nev], int(info)
 
 
 def inverse_iteration(alpha: np.ndarray, lam: np.ndarray):

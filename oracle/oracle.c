@@ -444,6 +444,127 @@ int oracle_inverse_iteration(int n, const double *alpha, int nev,
     return info;
 }
 
+/* Eigenvectors from the zero-diagonal form: for lambda = sigma > 0 of S,
+ * B v = sigma u and B^T u = sigma v, so q = [u; v] / sqrt(2) in the shuffled
+ * order (u on the even rows, v on the odd rows) and S q = sigma q.  u comes
+ * from inverse iteration on B B^T - sigma^2 I (order ceil(n/2), the symmetric
+ * tridiagonal with diagonal a_i^2 + b_{i-1}^2 and off-diagonal a_i b_i) by
+ * oracle_inverse_iteration's steps (LU with partial pivoting, seeded start,
+ * at most 5 solves, Gram-Schmidt within clusters of the squared values),
+ * then v = B^T u / sigma, and q is normalised with its largest-modulus entry
+ * positive.  lambda[0..nev-1] > 0, descending.  Q is n x nev, ld ldq.
+ * Returns 0 or 1000 + k for the first vector whose iteration did not
+ * converge; -1 for lambda <= 0 or on allocation failure.                   */
+int oracle_bidiag_vectors(int n, const double *alpha, int nev, const double *lambda,
+                          double *Q, int ldq)
+{
+    if (n <= 0 || nev <= 0) return 0;
+    const int m = (n + 1) / 2;
+    for (int k = 0; k < nev; k++)
+        if (!(lambda[k] > 0.0)) return -1;
+    double *a = malloc(sizeof(double) * (size_t)m), *b = malloc(sizeof(double) * (size_t)m);
+    double *dd = malloc(sizeof(double) * (size_t)m), *ee = malloc(sizeof(double) * (size_t)m);
+    double *u0 = malloc(sizeof(double) * (size_t)m), *u1 = malloc(sizeof(double) * (size_t)m);
+    double *u2 = malloc(sizeof(double) * (size_t)m), *ml = malloc(sizeof(double) * (size_t)m);
+    double *y = malloc(sizeof(double) * (size_t)m), *U = malloc(sizeof(double) * (size_t)m * nev);
+    char *sw = malloc((size_t)m);
+    if (!a || !b || !dd || !ee || !u0 || !u1 || !u2 || !ml || !y || !U || !sw) {
+        free(a); free(b); free(dd); free(ee); free(u0); free(u1); free(u2); free(ml); free(y); free(U); free(sw);
+        return -1;
+    }
+    for (int i = 0; i < m; i++) {
+        a[i] = (2 * i <= n - 2) ? alpha[2 * i] : 0.0;
+        b[i] = (2 * i + 1 <= n - 2) ? alpha[2 * i + 1] : 0.0;
+    }
+    /* B B^T: diagonal a_i^2 + b_{i-1}^2, off-diagonal a_i b_i */
+    double gs = 0.0;
+    for (int i = 0; i < m; i++) {
+        dd[i] = a[i] * a[i] + (i > 0 ? b[i - 1] * b[i - 1] : 0.0);
+        ee[i] = (i + 1 < m) ? a[i] * b[i] : 0.0;
+        double r = fabs(dd[i]) + fabs(ee[i]) + (i > 0 ? fabs(ee[i - 1]) : 0.0);
+        if (r > gs) gs = r;
+    }
+    const double eps = DBL_EPSILON;
+    const double ptol = eps * (gs > 0.0 ? gs : 1.0);
+    const double ortol = 1e-3 * gs;
+    const double grow = 1.0 / (100.0 * sqrt((double)m) * eps * (gs > 0.0 ? gs : 1.0));
+    int info = 0, cstart = 0;
+    for (int k = 0; k < nev; k++) {
+        const double mu = lambda[k] * lambda[k];
+        if (k > 0 && lambda[k - 1] * lambda[k - 1] - mu > ortol) cstart = k;
+        /* LU with partial pivoting of B B^T - mu I (rows i: ee[i-1], dd[i]-mu, ee[i]) */
+        double p0 = dd[0] - mu, p1 = (m > 1) ? ee[0] : 0.0;
+        for (int i = 0; i < m - 1; i++) {
+            double l = ee[i];
+            double dn = dd[i + 1] - mu;
+            double un = (i + 2 < m) ? ee[i + 1] : 0.0;
+            if (fabs(p0) >= fabs(l)) {
+                double piv = p0;
+                if (fabs(piv) < ptol) piv = (piv < 0.0) ? -ptol : ptol;
+                u0[i] = piv; u1[i] = p1; u2[i] = 0.0; sw[i] = 0;
+                ml[i] = l / piv;
+                p0 = dn - ml[i] * p1;
+                p1 = un;
+            } else {
+                u0[i] = l; u1[i] = dn; u2[i] = un; sw[i] = 1;
+                ml[i] = p0 / l;
+                double np0 = p1 - ml[i] * dn;
+                p1 = -ml[i] * un;
+                p0 = np0;
+            }
+        }
+        if (fabs(p0) < ptol) p0 = (p0 < 0.0) ? -ptol : ptol;
+        u0[m - 1] = p0; u1[m - 1] = 0.0; u2[m - 1] = 0.0;
+        double *u = &U[(size_t)k * m];
+        for (int i = 0; i < m; i++) u[i] = start_entry((uint64_t)k + 1, (uint64_t)i);
+        double nrm = 0.0;
+        for (int i = 0; i < m; i++) nrm += u[i] * u[i];
+        nrm = sqrt(nrm);
+        for (int i = 0; i < m; i++) u[i] /= nrm;
+        int conv = 0, done = 0;
+        for (int it = 0; it < 5 && !done; it++) {
+            for (int i = 0; i < m; i++) y[i] = u[i];
+            for (int i = 0; i < m - 1; i++) {
+                if (sw[i]) { double t = y[i]; y[i] = y[i + 1]; y[i + 1] = t; }
+                y[i + 1] -= ml[i] * y[i];
+            }
+            y[m - 1] /= u0[m - 1];
+            if (m >= 2) y[m - 2] = (y[m - 2] - u1[m - 2] * y[m - 1]) / u0[m - 2];
+            for (int i = m - 3; i >= 0; i--)
+                y[i] = (y[i] - u1[i] * y[i + 1] - u2[i] * y[i + 2]) / u0[i];
+            for (int pc = cstart; pc < k; pc++) {
+                const double *up = &U[(size_t)pc * m];
+                double dt = 0.0;
+                for (int i = 0; i < m; i++) dt += up[i] * y[i];
+                for (int i = 0; i < m; i++) y[i] -= dt * up[i];
+            }
+            nrm = 0.0;
+            for (int i = 0; i < m; i++) nrm += y[i] * y[i];
+            nrm = sqrt(nrm);
+            if (!(nrm > 0.0) || !isfinite(nrm)) break;
+            for (int i = 0; i < m; i++) u[i] = y[i] / nrm;
+            if (conv) done = 1;
+            else if (nrm >= grow) conv = 1;
+        }
+        if (!conv && info == 0) info = 1000 + k;
+        /* q: u on the even rows, v = B^T u / sigma on the odd rows */
+        double *q = &AT(Q, 0, k, ldq);
+        for (int i = 0; i < m; i++) q[2 * i] = u[i];
+        for (int i = 0; 2 * i + 1 < n; i++)
+            q[2 * i + 1] = (a[i] * u[i] + (i + 1 < m ? b[i] * u[i + 1] : 0.0)) / lambda[k];
+        nrm = 0.0;
+        for (int i = 0; i < n; i++) nrm += q[i] * q[i];
+        nrm = sqrt(nrm);
+        int imax = 0;
+        for (int i = 1; i < n; i++)
+            if (fabs(q[i]) > fabs(q[imax])) imax = i;
+        const double sgn = (q[imax] < 0.0) ? -1.0 : 1.0;
+        for (int i = 0; i < n; i++) q[i] *= sgn / nrm;
+    }
+    free(a); free(b); free(dd); free(ee); free(u0); free(u1); free(u2); free(ml); free(y); free(U); free(sw);
+    return info;
+}
+
 /* Algorithm 1 step 3: z_k = D q_k, D = diag(i^r), r = 0..n-1, split into
  * real and imaginary parts (Sec. 2.3): r mod 4 = 0 -> re = q, 1 -> im = q,
  * 2 -> re = -q, 3 -> im = -q; the other part is 0.                        */

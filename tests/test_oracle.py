@@ -329,3 +329,36 @@ def test_bidiag_bisect_split_matrix_is_exact_to_relative_rounding():
     lam = oracle.bidiag_bisect(alpha, vals.size)
     ref = np.sort(vals)[::-1]
     assert np.all(np.abs(lam - ref) <= 4 * EPS * ref)
+
+
+@pytest.mark.parametrize("n", [4, 9, 40, 41])
+def test_bidiag_vectors_unit_closed_form(n):
+    # tridiag(1, 0, 1): eigenvector k is sin((j+1) k pi / (n+1)), j = 0..n-1
+    a = np.ones(n - 1)
+    lam = oracle.bidiag_bisect(a, n // 2)
+    Q, info = oracle.bidiag_vectors(a, lam)
+    assert info == 0
+    j = np.arange(1, n + 1)[:, None]
+    k = np.arange(1, n // 2 + 1)[None, :]
+    ref = np.sin(j * k * np.pi / (n + 1))
+    ref /= np.linalg.norm(ref, axis=0)
+    assert np.max(np.abs(np.abs(np.sum(Q * ref, axis=0)) - 1.0)) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [6, 65, 200])
+def test_bidiag_vectors_are_eigenvectors_of_s(n):
+    rng = np.random.default_rng(4400 + n)
+    a = rng.uniform(0.5, 2.0, n - 1)
+    lam = oracle.bidiag_bisect(a, n // 2)
+    Q, info = oracle.bidiag_vectors(a, lam)
+    assert info == 0
+    S = np.diag(a, 1) + np.diag(a, -1)
+    nS = np.max(np.abs(lam))
+    assert np.linalg.norm(S @ Q - Q * lam) <= 10 * n * EPS * nS
+    assert np.linalg.norm(Q.T @ Q - np.eye(n // 2)) <= 100 * n * EPS
+    # the inverse iteration on S itself gives the same vectors where the
+    # eigenvalue gaps make them well conditioned
+    Qo, _ = oracle.inverse_iteration(a, lam)
+    gap = np.minimum(np.abs(np.diff(lam, prepend=np.inf)), np.abs(np.diff(lam, append=-lam[-1])))
+    sel = gap > 1e-2 * nS
+    assert np.all(np.abs(np.sum(Q[:, sel] * Qo[:, sel], axis=0)) >= 1 - 1e-9)
