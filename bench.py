@@ -82,8 +82,9 @@ KIND_KERNELS = {
 # for a lower-triangle one; two of each per iteration: x48 on average).
 TRAFFIC = {
     "ozaki_refine": {"bytes": 2.34e9 * 48, "n": 16384, "file": "paper_1912_04062_gb300/csrc/ozaki_gemm.cu",
-                     "sha256_16": None,
-                     "how": "ncu capture of a 4096^3 product scaled by tiles x K (x48)"},
+                     "sha256_16": "4a236564973d3593",
+                     "how": "ncu capture of a 4096^3 product (2.34e9 B, profiles/ozaki_gemm_kernel_4096cube.md) "
+                            "scaled by tiles x K (x48)"},
 }
 
 
