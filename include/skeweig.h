@@ -54,6 +54,7 @@ extern "C" {
 #define SKEW_ERR_NONFINITE 2005        /* A holds NaN or Inf (check_finite) */
 #define SKEW_ERR_WORKSPACE 2006        /* caller workspace too small */
 #define SKEW_ERR_LAUNCH 2007           /* cooperative launch could not fit */
+#define SKEW_ERR_NOT_DEFINITE 2008     /* skew_bse_solve: M = J H is not positive definite */
 
 typedef enum {
     SKEW_MODE_FP64 = 0,            /* every step in FP64 */
@@ -263,6 +264,34 @@ int skew_batched_plan_tune(skew_batched_plan* plan, skew_batched_config* best, i
                            int* cand_smem, float* cand_ms, int cap, void* stream);
 void skew_batched_plan_get_config(const skew_batched_plan* plan, skew_batched_config* cfg);
 void skew_batched_plan_destroy(skew_batched_plan* plan);
+
+/*
+ * The Bethe-Salpeter eigenproblem around the skew solver (Sec. 3, Theorem 1,
+ * the four steps of the structure-preserving method):
+ *   H_BS = [[A, B], [-conj(B), -conj(A)]],  A = A^H, B = B^T (h x h complex),
+ * definite (Omega = [[A, B], [conj(B), conj(A)]] positive definite).  Step 1
+ * forms M = J H = [[Re(A+B), Im(A-B)], [-Im(A+B), Re(A-B)]] (2h x 2h, real
+ * symmetric positive definite, Eq. SymmetricM), step 2 its Cholesky factor
+ * M = L L^T, step 3 solves the skew-symmetric eigenproblem of K = L^T J L
+ * (J = [[0, I], [-I, 0]]) with skew_eig_ex in opts' mode, step 4 transforms
+ * back: x = L^-T z and psi = Q x with the unitary Q = [[I, -iI], [I, iI]] /
+ * sqrt(2) of Theorem 1.  Returns the nev largest positive eigenvalues of H_BS
+ * (descending) in lambda and psi = psi_re + i psi_im (2h x nev, ld ldpsi)
+ * with H_BS psi = psi diag(lambda) and psi^H S psi = I, S = diag(I, -I).
+ * All matrices are device, column-major FP64; A and B are given as real and
+ * imaginary parts (ld lda / ldb; A is read whole, B whole).  Asynchronous on
+ * `stream`; the numerical status goes to *d_info: 0, SKEW_ERR_NOT_DEFINITE
+ * (a Cholesky pivot not positive), 1000 + j (inverse iteration), or
+ * SKEW_ERR_*.  Workspace: skew_bse_workspace_size(h, nev, opts) bytes.
+ * Arguments: 1 h >= 1, 2-3 A_re / A_im, 4 lda >= h, 5-6 B_re / B_im,
+ * 7 ldb >= h, 8 1 <= nev <= h, 9 lambda, 10-11 psi_re / psi_im,
+ * 12 ldpsi >= 2h, 14 workspace, 16 d_info.
+ */
+size_t skew_bse_workspace_size(int h, int nev, const skew_opts* opts);
+int skew_bse_solve(int h, const double* A_re, const double* A_im, int lda, const double* B_re,
+                   const double* B_im, int ldb, int nev, double* lambda, double* psi_re, double* psi_im,
+                   int ldpsi, const skew_opts* opts, void* workspace, size_t ws_bytes, int* d_info,
+                   void* stream);
 
 /* Stages timed by skew_eig_profile (Algorithm 1, two-step form):
  * 0 ingest (copy of the strict lower triangle), 1 full-to-band reduction,

@@ -26,6 +26,7 @@ SKEW_ERR_UNSUPPORTED = 2004
 SKEW_ERR_NONFINITE = 2005
 SKEW_ERR_WORKSPACE = 2006
 SKEW_ERR_LAUNCH = 2007
+SKEW_ERR_NOT_DEFINITE = 2008
 
 SKEW_MODE_FP64 = 0
 SKEW_MODE_MIXED_BF16X3 = 1
@@ -98,6 +99,8 @@ SIGNATURES = {
     "skew_batched_plan_tune": (_i, [_p, _p, _p, _p, _p, _i, _p]),
     "skew_batched_plan_get_config": (None, [_p, _p]),
     "skew_batched_plan_destroy": (None, [_p]),
+    "skew_bse_workspace_size": (_sz, [_i, _i, _p]),
+    "skew_bse_solve": (_i, [_i, _p, _p, _i, _p, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
     "skew_apply_qtrd_f32_ws": (_sz, [_i, _i]),
     "skew_apply_qtrd_f32": (_i, [_i, _i, _p, _p, _p, _i, _i, _i, _p, _sz, _p, _p]),
     "skew_qband_ws": (_sz, [_i, _i, _i]),
@@ -443,6 +446,29 @@ def skew_eig_batched(As, nevs, vectors: bool = True, opts: Options | None = None
     _check(code, "skew_eig_batched_ex")
     out = ([l[:nv] for l, nv in zip(lams, nevs)], Zr, Zi)
     return out + (d_info[:count],) if info else out
+
+
+def bse_solve(A, B, nev: int, opts: Options | None = None, stream=None):
+    """The Bethe-Salpeter eigenproblem H_BS = [[A, B], [-conj(B), -conj(A)]]
+    (A Hermitian, B complex symmetric, h x h complex128 CUDA tensors) through
+    skew_bse_solve (Sec. 3): the nev largest positive eigenvalues (descending)
+    and psi (2h x nev complex128) with H_BS psi = psi diag(lam) and
+    psi^H S psi = I.  Returns (lam, psi, status)."""
+    torch = _torch()
+    h = A.shape[0]
+    dev = A.device
+    Ar, Ai = fortran(A.real.contiguous()), fortran(A.imag.contiguous())
+    Br, Bi = fortran(B.real.contiguous()), fortran(B.imag.contiguous())
+    o = (opts or Options()).c()
+    ws = _ws(lib().skew_bse_workspace_size(h, nev, ctypes.byref(o)), dev)
+    lam = torch.empty(nev, dtype=torch.float64, device=dev)
+    Pr, Pi = fortran_empty(2 * h, nev, dev), fortran_empty(2 * h, nev, dev)
+    st = _status(dev)
+    code = lib().skew_bse_solve(h, _ptr(Ar), _ptr(Ai), _ld(Ar), _ptr(Br), _ptr(Bi), _ld(Br), nev, _ptr(lam),
+                                _ptr(Pr), _ptr(Pi), 2 * h, ctypes.byref(o), _ptr(ws), ws.numel(), _ptr(st),
+                                _stream(stream))
+    _check(code, "skew_bse_solve")
+    return lam, torch.complex(Pr, Pi), st
 
 
 def batched_set_config(ctas_per_sm: int, smem_max_n: int) -> None:

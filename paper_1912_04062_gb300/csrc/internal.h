@@ -209,6 +209,15 @@ int batched_launch(cudaStream_t st, const BatchPlanDev& d, const skew_batched_co
 skew_batched_config& batched_default_config();
 int batched_config_check(const skew_batched_config& c);
 
+// ---- bse.cu (the Bethe-Salpeter driver's steps around the skew solver) ------
+cudaError_t bse_build_m(cudaStream_t st, int h, const double* Ar, const double* Ai, int lda, const double* Br,
+                        const double* Bi, int ldb, double* M, int ldm);
+cudaError_t cholesky_lower(cudaStream_t st, int N, double* M, int ld, double* NP, int* status);
+cudaError_t bse_jl(cudaStream_t st, int h, double* L, int ld, double* JL, int ldj);
+cudaError_t trsm_lower_t(cudaStream_t st, int N, const double* L, int ld, double* X, int ldx, int ncols);
+cudaError_t bse_psi(cudaStream_t st, int h, int nev, const double* Xr, const double* Xi, int ldx,
+                    const double* lambda, double* Pr, double* Pi, int ldp);
+
 // ---- metrics.cu -------------------------------------------------------------
 size_t metrics_ws(int n, int nev, int s);
 int metrics(cudaStream_t st, int n, const double* A, int lda, int nev, const double* lambda, const double* X,

@@ -51,6 +51,11 @@ __global__ void zero_int_kernel(int* p) {
     if (threadIdx.x == 0) *p = 0;
 }
 
+// d_info = the first nonzero of status[0] (driver) and status[1] (skew solve)
+__global__ void bse_status_kernel(const int* status, int* d_info) {
+    if (threadIdx.x == 0) *d_info = status[0] ? status[0] : status[1];
+}
+
 inline int grid_for(size_t total) {
     size_t g = (total + 255) / 256;
     return (int)(g > 16384 ? 16384 : (g == 0 ? 1 : g));
@@ -496,6 +501,7 @@ const char* skew_eig_strerror(int code) {
     case SKEW_ERR_NONFINITE: return "input holds NaN or Inf";
     case SKEW_ERR_WORKSPACE: return "workspace too small";
     case SKEW_ERR_LAUNCH: return "cooperative launch does not fit on this GPU";
+    case SKEW_ERR_NOT_DEFINITE: return "the Bethe-Salpeter matrix is not definite (Cholesky of J H failed)";
     default: return "unknown status code";
     }
 }
@@ -876,6 +882,76 @@ int skew_eig_profile(int n, const double* A, int lda, int nev, double* lambda, d
     // the per-kind totals (the pool then never fills across repeated solves)
     if (rc == 0 && ktimer().on && kt_fold() != 0) rc = SKEW_ERR_CUDA;
     return rc ? rc : info;
+}
+
+namespace {
+struct BseWs {
+    double *M, *JL, *K, *NP;
+    int* status;
+    void* solve;
+    size_t solve_bytes;
+};
+bool carve_bse(Carve& cv, int h, int nev, const skew_opts* o, BseWs* w) {
+    const size_t N = 2 * (size_t)h;
+    w->status = cv.take<int>(16);
+    w->M = cv.take<double>(N * N);
+    w->JL = cv.take<double>(N * N);  // J L, later the eigenvectors z of K (N x 2 nev)
+    w->K = cv.take<double>(N * N);
+    w->NP = cv.take<double>(N * 64);
+    w->solve_bytes = plan_bytes((int)N, nev, o, true);
+    w->solve = cv.take<char>(w->solve_bytes);
+    return cv.ok;
+}
+}  // namespace
+
+size_t skew_bse_workspace_size(int h, int nev, const skew_opts* opts) {
+    if (h < 1 || nev < 1) return 0;
+    Carve cv(nullptr, ~size_t(0));
+    BseWs w{};
+    carve_bse(cv, h, nev, opts, &w);
+    return cv.off + 256;
+}
+
+int skew_bse_solve(int h, const double* A_re, const double* A_im, int lda, const double* B_re, const double* B_im,
+                   int ldb, int nev, double* lambda, double* psi_re, double* psi_im, int ldpsi, const skew_opts* opts,
+                   void* workspace, size_t ws_bytes, int* d_info, void* stream) {
+    if (h < 1) return -1;
+    if (!A_re || !A_im) return -2;
+    if (lda < h) return -4;
+    if (!B_re || !B_im) return -5;
+    if (ldb < h) return -7;
+    if (nev < 1 || nev > h) return -8;
+    if (!lambda) return -9;
+    if (!psi_re || !psi_im) return -10;
+    if (ldpsi < 2 * h) return -12;
+    if (!workspace) return -14;
+    if (!d_info) return -16;
+    if (opts && opts->mode == SKEW_MODE_MIXED_INT8) return SKEW_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Carve cv(workspace, ws_bytes);
+    BseWs w{};
+    if (!carve_bse(cv, h, nev, opts, &w)) return SKEW_ERR_WORKSPACE;
+    const int N = 2 * h;
+    zero_int_kernel<<<1, 32, 0, st>>>(w.status);
+    count_launch();
+    // 1. M = J H; 2. M = L L^T
+    if (const cudaError_t e = bse_build_m(st, h, A_re, A_im, lda, B_re, B_im, ldb, w.M, N)) return cuda_fail(e);
+    if (const cudaError_t e = cholesky_lower(st, N, w.M, N, w.NP, w.status)) return cuda_fail(e);
+    // 3. K = L^T (J L), then the skew solve (its lower triangle is read)
+    if (const cudaError_t e = bse_jl(st, h, w.M, N, w.JL, N)) return cuda_fail(e);
+    if (const cudaError_t e = gemm(st, true, false, N, N, N, 1.0, w.M, N, w.JL, N, 0.0, w.K, N))
+        return cuda_fail(e);
+    double* Zr = w.JL;
+    double* Zi = w.JL + (size_t)N * nev;
+    int rc = run_solve(st, N, w.K, N, nev, lambda, Zr, Zi, N, opts, w.solve, w.solve_bytes, w.status + 1);
+    if (rc) return rc;
+    // 4. x = L^-T z (real and imaginary parts), psi = Q x sqrt(lambda)
+    if (const cudaError_t e = trsm_lower_t(st, N, w.M, N, Zr, N, 2 * nev)) return cuda_fail(e);
+    if (const cudaError_t e = bse_psi(st, h, nev, Zr, Zi, N, lambda, psi_re, psi_im, ldpsi)) return cuda_fail(e);
+    // status: the Cholesky's, else the skew solve's
+    bse_status_kernel<<<1, 32, 0, st>>>(w.status, d_info);
+    count_launch();
+    return cuda_ok(cudaGetLastError());
 }
 
 size_t skew_refine_ws(int n) { return refine_ws(n) + align_up(sizeof(double) * (size_t)n * n) + 256; }

@@ -70,7 +70,7 @@ __device__ __forceinline__ int bd_count(int m, const double* __restrict__ a2e, c
 // counts of B B^T at t = x^2 (ascending index m - 1 - k there).
 __device__ __forceinline__ double bisect_one_bd(int m, int k, const double* __restrict__ a2e,
                                                 const double* __restrict__ b2e, double g, double pivmin) {
-    if (m <= 1 || g == 0.0) return 0.0;
+    if (m < 1 || g == 0.0) return 0.0;  // m = 1 (n = 2): the eigenvalue |alpha_0|
     const int j = m - 1 - k;
     double lo = 0.0, hi = g + 2.0 * DBL_EPSILON * g + pivmin;
     for (int it = 0; it < 4000; it++) {
