@@ -203,7 +203,7 @@ cudaError_t cholesky_lower(cudaStream_t st, int N, double* M, int ld, double* NP
         chol_panel_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, kb, D, ld, P, NP, m);
         count_launch();
         // A22 += P (-P)^T on the lower 64-tiles
-        if (const cudaError_t e = gemm_lower_tiles(st, m, kb, P, ld, NP, m, D + kb + (size_t)kb * ld, ld))
+        if (const cudaError_t e = gemm_lower_tiles(st, m, kb, P, ld, NP, m, D + kb + (size_t)kb * ld, ld, false))
             return e;
     }
     return cudaGetLastError();

@@ -176,9 +176,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(int M, int N, int K, double al
 
 // Lower-tile-only C += X Y^T (K = k).  Block b enumerates tiles (I, J),
 // I >= J, row-major over the lower triangle of the tile grid.
+// zero_diag: the skew rank-2k update (its diagonal is exactly 0); otherwise the
+// diagonal is updated like every other entry (symmetric updates)
 __global__ void __launch_bounds__(NT) lower_tiles_kernel(int m, int k, const double* __restrict__ X,
                                                          int ldx, const double* __restrict__ Y,
-                                                         int ldy, double* __restrict__ C, int ldc) {
+                                                         int ldy, double* __restrict__ C, int ldc, int zero_diag) {
     // invert t = I (I + 1) / 2 + J
     const long long t = blockIdx.x;
     int I = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(NT) lower_tiles_kernel(int m, int k, const dou
             int gi = i0 + tx + 16 * r;
             if (gi >= m) continue;
             double* p = C + (size_t)gj * ldc + gi;
-            *p = (gi == gj) ? 0.0 : (*p + acc[r][c]);
+            *p = (gi == gj && zero_diag) ? 0.0 : (*p + acc[r][c]);
         }
     }
 }
@@ -327,11 +329,11 @@ cudaError_t skew_symm(cudaStream_t st, int m, int nb, const double* W, int ldw, 
 }
 
 cudaError_t gemm_lower_tiles(cudaStream_t st, int m, int k, const double* X, int ldx, const double* Y,
-                             int ldy, double* C, int ldc) {
+                             int ldy, double* C, int ldc, bool zero_diag) {
     if (m <= 0 || k <= 0) return cudaSuccess;
     const long long T = (m + BM - 1) / BM;
     const long long nt = T * (T + 1) / 2;
-    lower_tiles_kernel<<<(unsigned)nt, NT, 0, st>>>(m, k, X, ldx, Y, ldy, C, ldc);
+    lower_tiles_kernel<<<(unsigned)nt, NT, 0, st>>>(m, k, X, ldx, Y, ldy, C, ldc, zero_diag ? 1 : 0);
     count_launch();
     return cudaGetLastError();
 }

@@ -32,9 +32,10 @@ cudaError_t skew_symm(cudaStream_t st, int m, int nb, const double* W, int ldw,
 
 // Lower 64 x 64 tiles (diagonal tiles complete) of C[m x m] +=
 // X[m x k] Y[m x k]^T.  Used for the skew rank-2k update with
-// X = [V W], Y = [W -V].
+// X = [V W], Y = [W -V] (zero_diag: the diagonal set to 0, exact for a skew
+// result) and for the Cholesky's symmetric trailing update (zero_diag false).
 cudaError_t gemm_lower_tiles(cudaStream_t st, int m, int k, const double* X, int ldx,
-                             const double* Y, int ldy, double* C, int ldc);
+                             const double* Y, int ldy, double* C, int ldc, bool zero_diag = true);
 
 // ---- band_reduce.cu --------------------------------------------------------
 // planes > 0: the skew SYMM and the rank-2k update run as split-BF16 tensor-core
