@@ -79,7 +79,7 @@ typedef enum {
                                       Without such a complete basis (nev < n/2,
                                       odd n) nothing is refined: all products
                                       keep 8 slices (FP64-accurate) and Q_trd
-                                      runs in FP64 */
+                                      runs in double-float (SKEW_QTRD_DF) */
 } skew_mode;
 
 /* Fault hooks (host-side injection for tests; never fault the GPU). */
@@ -118,14 +118,18 @@ typedef struct {
 #define SKEW_TRIDIAG_FULL 1
 
 /* skew_opts.qtrd: SKEW_QTRD_AUTO (0) takes the mode's choice (FP64 in the FP64
- * form and whenever the mixed modes do not refine; FP32 SIMT when they
- * refine); the others force FP32 SIMT, FP64 SIMT or the tensor-core form
- * (compact WY blocks of 64 sweeps, BF16x6 tcgen05 products with FP32
- * accumulation, FP32-level accuracy). */
+ * form; FP32 SIMT when the mixed modes refine; double-float when the refined
+ * mode cannot refine (nev < n/2, odd n) and FP64 in the split modes then);
+ * the others force FP32 SIMT, FP64 SIMT, the tensor-core form (compact WY
+ * blocks of 64 sweeps, BF16x6 tcgen05 products with FP32 accumulation,
+ * FP32-level accuracy) or double-float (every value a pair of FP32 numbers,
+ * exact two-product and two-sum on the FP32 pipe: about 2^-46 per operation,
+ * FP64-level accuracy for the bounds at several times the FP64 pipe's rate). */
 #define SKEW_QTRD_AUTO 0
 #define SKEW_QTRD_FP32 1
 #define SKEW_QTRD_FP64 2
 #define SKEW_QTRD_TC 3
+#define SKEW_QTRD_DF 4
 
 /* Default options (FP64 mode, b = 64). */
 void skew_opts_default(skew_opts* opts);
@@ -539,6 +543,14 @@ int skew_apply_qtrd(int n, int b, const double* Vtrd, const double* tautrd,
 size_t skew_apply_qtrd_f32_ws(int n, int tensor);
 int skew_apply_qtrd_f32(int n, int b, const float* V32, const float* tau32, float* Z, int ldz, int k,
                         int tensor, void* ws, size_t ws_bytes, int* d_status, void* stream);
+
+/* Z <- Q_trd Z (Sec. 2.1 step 3a) in double-float arithmetic on the FP32 pipe
+ * (SKEW_QTRD_DF) from the FP64 reflectors of skew_band_to_tridiag (layout of
+ * skew_apply_qtrd); Z is FP64, n x k, ld ldz.  d_status is a device int set
+ * on a device-side failure (SKEW_ERR_DEVICE_TIMEOUT).  Arguments 1 n, 2 b (64),
+ * 3 Vtrd/tautrd, 6 ldz, 7 k, 8 d_status. */
+int skew_apply_qtrd_df(int n, int b, const double* Vtrd, const double* tautrd, double* Z, int ldz, int k,
+                       int* d_status, void* stream);
 
 /* Z <- Q_band Z (Sec. 2.1 step 3b) for a W / Tfac pair produced by
  * skew_band_reduce; Z is n x k, ld ldz. */

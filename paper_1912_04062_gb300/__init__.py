@@ -42,6 +42,7 @@ SKEW_QTRD_AUTO = 0
 SKEW_QTRD_FP32 = 1
 SKEW_QTRD_FP64 = 2
 SKEW_QTRD_TC = 3
+SKEW_QTRD_DF = 4
 SKEW_TRIDIAG_AUTO = 0
 SKEW_TRIDIAG_FULL = 1
 
@@ -103,6 +104,7 @@ SIGNATURES = {
     "skew_bse_solve": (_i, [_i, _p, _p, _i, _p, _p, _i, _i, _p, _p, _p, _i, _p, _p, _sz, _p, _p]),
     "skew_apply_qtrd_f32_ws": (_sz, [_i, _i]),
     "skew_apply_qtrd_f32": (_i, [_i, _i, _p, _p, _p, _i, _i, _i, _p, _sz, _p, _p]),
+    "skew_apply_qtrd_df": (_i, [_i, _i, _p, _p, _p, _i, _i, _p, _p]),
     "skew_qband_ws": (_sz, [_i, _i, _i]),
     "skew_apply_qband": (_i, [_i, _i, _p, _i, _p, _p, _i, _i, _p, _sz, _p]),
 }
@@ -173,7 +175,11 @@ def _ptr(t):
 
 
 def _ld(t):
-    return max(1, t.stride(1)) if t.dim() == 2 else max(1, t.shape[0])
+    # one column: torch may keep any stride for the size-1 dimension, and the
+    # leading dimension is then only required to cover the rows
+    if t.dim() == 2 and t.shape[1] > 1:
+        return max(1, t.stride(1))
+    return max(1, t.shape[0])
 
 
 def _stream(stream=None):
@@ -688,6 +694,16 @@ def apply_qtrd_f32(V32, tau32, Z, tensor: bool, b: int = 64, stream=None):
     st = _status(Z.device)
     _check(lib().skew_apply_qtrd_f32(n, b, _ptr(V32), _ptr(tau32), _ptr(Z), _ld(Z), k, 1 if tensor else 0,
                                      _ptr(ws), ws.numel(), _ptr(st), _stream(stream)), "skew_apply_qtrd_f32")
+    return st
+
+
+def apply_qtrd_df(Vtrd, tau, Z, b: int = 64, stream=None):
+    """Z (float64, Fortran-strided n x k) <- Q_trd Z in place in double-float
+    arithmetic (skew_apply_qtrd_df).  Returns the device status word."""
+    n, k = Z.shape
+    st = _status(Z.device)
+    _check(lib().skew_apply_qtrd_df(n, b, _ptr(Vtrd), _ptr(tau), _ptr(Z), _ld(Z), k, _ptr(st), _stream(stream)),
+           "skew_apply_qtrd_df")
     return st
 
 

@@ -197,7 +197,9 @@ qtrd_slide_kernel(int n, const float* __restrict__ V32, const float* __restrict_
 // FP64 variant: the window stays in shared memory (ld QLD, conflict-free for
 // doubles); thread (c, q) owns rows 4i + q of column c for each reflector.  On
 // this part the FP64 pipe is the limit, and the shared-memory form keeps it
-// busier than the register-resident one.
+// busier than the register-resident one.  The CTA has 4 threads per column
+// of its slab (rounded up to whole warps): threads past the slab would spend
+// the FP64 pipe on padding.
 template <typename T>
 __global__ void __launch_bounds__(QT)
 qtrd_smem_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ tautrd, T* __restrict__ Z,
@@ -218,7 +220,7 @@ qtrd_smem_kernel(int n, const double* __restrict__ Vtrd, const double* __restric
             const int top = s0 + 1 + k * QB;
             if (top >= n) break;
             const int H = min(QH, n - top);
-            for (int e = t; e < H * nc; e += QT) {
+            for (int e = t; e < H * nc; e += blockDim.x) {
                 int i = e % H, cc = e / H;
                 zw[cc * QLD + i] = Z[(size_t)(c0 + cc) * ldz + top + i];
             }
@@ -254,7 +256,7 @@ qtrd_smem_kernel(int n, const double* __restrict__ Vtrd, const double* __restric
                 }
             }
             __syncthreads();
-            for (int e = t; e < H * nc; e += QT) {
+            for (int e = t; e < H * nc; e += blockDim.x) {
                 int i = e % H, cc = e / H;
                 Z[(size_t)(c0 + cc) * ldz + top + i] = zw[cc * QLD + i];
             }
@@ -303,8 +305,9 @@ cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd, const 
     const int slab = qtrd_slab(k, &grid);
     const size_t smem = sizeof(double) * (size_t)QLD * 64;
     cudaFuncSetAttribute(qtrd_smem_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int threads = (4 * slab + 31) / 32 * 32;
     KtScope kt(st, KT_QTRD);
-    qtrd_smem_kernel<double><<<grid, QT, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
+    qtrd_smem_kernel<double><<<grid, threads, smem, st>>>(n, Vtrd, tautrd, Z, ldz, k, slab);
     count_launch();
     return cudaGetLastError();
 }

@@ -92,6 +92,12 @@ cudaError_t apply_qtrd(cudaStream_t st, int n, int b, const double* Vtrd,
 // steps zero).
 cudaError_t apply_qtrd_f32(cudaStream_t st, int n, int b, const float* V32, const float* tau32, float* Z, int ldz,
                            int k, int* status);
+// ---- qtrd_df.cu (Q_trd in double-float on the FP32 pipe) -----------------
+// Z (FP64, n x k, ld ldz) <- Q_trd Z from the chase's FP64 reflectors (layout
+// of apply_qtrd), about 2^-46 accurate per operation; status receives
+// SKEW_ERR_DEVICE_TIMEOUT if a copy never lands.
+cudaError_t apply_qtrd_df(cudaStream_t st, int n, int b, const double* Vtrd, const double* tautrd, double* Z,
+                          int ldz, int k, int* status);
 // ---- qtrd_tc.cu (Q_trd on the tensor cores) ------------------------------
 // Z (FP32, n x k, ld ldz) <- Q_trd Z from the chase's FP32 reflectors (slot
 // k nsw64 + s): each 64-sweep block in compact WY form, applied by tcgen05

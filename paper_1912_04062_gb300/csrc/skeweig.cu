@@ -70,6 +70,7 @@ struct Plan {
     int reduce_slices, qband_slices;  // digit slices of the REDUCE_F64ACC products
     bool qtrd_f32;    // mixed Q_trd in FP32 arithmetic (else FP64)
     bool qtrd_tc;     // the FP32-level Q_trd on the tensor cores (else SIMT)
+    bool qtrd_df;     // Q_trd in double-float on the FP32 pipe (FP64 data)
     size_t ldab;
     // carved pointers
     double *W, *Tfac, *AB, *Vtrd, *tautrd, *alpha, *Qi, *Z;
@@ -135,8 +136,8 @@ Plan make_plan(int n, int nev, const skew_opts* o, bool vectors) {
     // back-transforms: split products and FP32 Q_trd in the split modes; the
     // refined mode takes Q_band as FP64-accurate digit-slice products (the
     // refinement starts from vectors about 100x more orthogonal and saves an
-    // iteration) and Q_trd in FP32, or in FP64 when there is no complete
-    // basis to refine (nev < n/2, odd n)
+    // iteration) and Q_trd in FP32, or in double-float (FP64-accurate) when
+    // there is no complete basis to refine (nev < n/2, odd n)
     const bool refined_mode = p.mixed && o->mode == SKEW_MODE_MIXED_REFINED;
     p.qband_prec = !p.mixed ? 0 : (refined_mode ? REDUCE_F64ACC : p.planes);
     p.qtrd_f32 = p.mixed && vectors && !(refined_mode && !p.refine);
@@ -146,6 +147,14 @@ Plan make_plan(int n, int nev, const skew_opts* o, bool vectors) {
     // n = 16384 it is slower than the SIMT FP32 kernel (542 vs 436 ms) and
     // starts the refinement from a 24x larger orthogonality error
     p.qtrd_tc = p.qtrd_f32 && o && o->qtrd == SKEW_QTRD_TC;
+    // without refinement the refined mode needs an FP64-accurate Q_trd: the
+    // double-float kernel gives it on the FP32 pipe (the FP64 kernel on
+    // request)
+    if (o && vectors && o->qtrd == SKEW_QTRD_DF) {
+        p.qtrd_df = true;
+        p.qtrd_f32 = p.qtrd_tc = false;
+    }
+    if (vectors && refined_mode && !p.refine && (!o || o->qtrd == SKEW_QTRD_AUTO)) p.qtrd_df = true;
     // With a complete basis the refinement removes the first-order error, so
     // the products before it need only keep the starting vectors at the level
     // of the FP32 Q_trd: 6 digit slices (about 2^-42) for the reduction, 5
@@ -248,7 +257,10 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
             return SKEW_ERR_CUDA;
     }
     mark(6);
-    if (vectors && !p.qtrd_f32) {
+    if (vectors && p.qtrd_df) {
+        if (apply_qtrd_df(st, n, p.b, p.Vtrd, p.tautrd, p.Z, n, 2 * nev, p.status) != cudaSuccess)
+            return SKEW_ERR_CUDA;
+    } else if (vectors && !p.qtrd_f32) {
         if (apply_qtrd(st, n, p.b, p.Vtrd, p.tautrd, p.Z, n, 2 * nev) != cudaSuccess) return SKEW_ERR_CUDA;
     } else if (vectors) {
         // mixed form: Q_trd in FP32 arithmetic (the chase's FP32 reflector copies)
@@ -1145,6 +1157,19 @@ int skew_apply_qtrd_f32(int n, int b, const float* V32, const float* tau32, floa
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (tensor) return apply_qtrd_tc(st, n, V32, tau32, Z, ldz, k, ws, ws_bytes, d_status);
     return apply_qtrd_f32(st, n, b, V32, tau32, Z, ldz, k, d_status) == cudaSuccess ? 0 : SKEW_ERR_CUDA;
+}
+
+int skew_apply_qtrd_df(int n, int b, const double* Vtrd, const double* tautrd, double* Z, int ldz, int k,
+                       int* d_status, void* stream) {
+    if (n < 0) return -1;
+    if (b != 64) return -2;
+    if (n >= 3 && k > 0 && (!Vtrd || !tautrd)) return -3;
+    if (ldz < (n > 1 ? n : 1)) return -6;
+    if (k < 0) return -7;
+    if (!d_status) return -8;
+    return apply_qtrd_df(static_cast<cudaStream_t>(stream), n, b, Vtrd, tautrd, Z, ldz, k, d_status) == cudaSuccess
+               ? 0
+               : SKEW_ERR_CUDA;
 }
 
 size_t skew_qband_ws(int n, int b, int k) { return qband_ws(n, b, k); }
