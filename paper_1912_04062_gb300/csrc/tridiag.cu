@@ -20,14 +20,17 @@
 //   * Inverse iteration: Gaussian elimination with partial pivoting of
 //     S - lambda I (pivots below eps g raised to eps g), a counter-based
 //     (splitmix64) start vector, at most maxit solves, one extra solve after
-//     the growth test passes.  Eigenvalues closer than ctol form a cluster; one
-//     thread handles a whole cluster and orthogonalises (modified Gram-Schmidt)
-//     each new vector against the cluster's earlier vectors after every solve.
+//     the growth test passes.  Eigenvalues closer than ctol form a cluster: a
+//     lone eigenvalue's vector is one thread's work; a cluster's members
+//     iterate in lockstep (each member's solves on its own thread, then the
+//     cluster's CTA orthogonalises them in index order by modified
+//     Gram-Schmidt, normalises them and applies the growth test).
 //     The largest-modulus entry of each vector is made positive.  When the
 //     vectors are refined afterwards, the same steps run in double-float
 //     arithmetic (eps = 2^-44).
 // Vectors are kept interleaved, Q[i * nev + k], so consecutive threads
 // (consecutive k) touch consecutive addresses in every sweep over i.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -286,12 +289,303 @@ __global__ void bisect_kernel(int n, int nev, const double* __restrict__ a2, con
     if (q == 0) lambda[k] = lo + 0.5 * (hi - lo);
 }
 
+// ---- lockstep inverse iteration of clusters ---------------------------------
+// A cluster (two or more eigenvalues closer than ctol) is iterated in lockstep
+// rather than by one thread: in every iteration each member solves with its
+// own LU on its own thread, then the cluster's CTA orthogonalises the members
+// in index order (modified Gram-Schmidt, parallel over the rows), normalises
+// them and applies the growth test to each; the cluster stops one iteration
+// after all its members passed.  The vectors are an orthonormal basis of the
+// same invariant subspace, and the critical path is one member's solves
+// instead of the whole cluster's (16 x at the 1e-10 clusters of a clustered
+// spectrum).  Singletons keep the one-thread path.
+constexpr int CLU_T = 256;
+
+__global__ void clu_list_kernel(int nev, const double* __restrict__ lambda, const TriScalars* sc, double ctol_rel,
+                                int2* __restrict__ list, int* __restrict__ count, int* __restrict__ state) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double ctol = ctol_rel * sc->g;
+    int c = 0, k0 = 0;
+    for (int k = 1; k <= nev; k++) {
+        if (k == nev || starts_cluster(lambda, k, ctol)) {
+            if (k - k0 >= 2) {
+                list[c] = make_int2(k0, k - k0);
+                state[c] = 0;
+                c++;
+            }
+            k0 = k;
+        }
+    }
+    *count = c;
+}
+
+// Row of the largest abs(x_i) (the lowest on ties), CTA-wide.
+template <class F>
+__device__ __forceinline__ int block_argmax(int n, F absval, double* rv, int* ri) {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double a = absval(i);
+        if (a > best) {
+            best = a;
+            bi = i;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        rv[warp] = best;
+        ri[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; w++)
+            if (rv[w] > rv[0] || (rv[w] == rv[0] && ri[w] < ri[0])) {
+                rv[0] = rv[w];
+                ri[0] = ri[w];
+            }
+    }
+    __syncthreads();
+    const int r = ri[0];
+    __syncthreads();
+    return r < n ? r : 0;
+}
+
+// Decision after an iteration: state 0 iterating, 1 all members passed (one
+// more iteration), 2 done.  ff = first member that failed the growth test
+// (m if none), bad = a member's norm was zero or not finite.
+__device__ __forceinline__ int clu_next_state(int st, int ff, int m, int bad, int it, int maxit, bool& fin,
+                                              bool& failed) {
+    int nst = (st == 1) ? 2 : (ff == m ? 1 : 0);
+    if (bad) nst = 0;
+    fin = bad || nst == 2 || it == maxit - 1;
+    failed = fin && nst == 0;
+    return nst;
+}
+
+__global__ void __launch_bounds__(CLU_T)
+invit_clu_kernel(int n, int nev, const double* __restrict__ alpha, const double* __restrict__ lambda,
+                 const TriScalars* sc, int maxit, int it, InvitBufs bf, double* __restrict__ Q,
+                 const int2* __restrict__ list, const int* __restrict__ count, int* __restrict__ state,
+                 int* __restrict__ fail) {
+    __shared__ double red[32];
+    __shared__ int redi[32];
+    __shared__ int s_ff, s_bad;
+    const int nc = *count;
+    const double g = sc->g;
+    const size_t ld = (size_t)nev;
+    const double eps = DBL_EPSILON, ptol = eps * g;
+    const double grow = 1.0 / (100.0 * sqrt((double)n) * eps * g);
+    const int t = threadIdx.x, T = blockDim.x;
+    for (int b = blockIdx.x; b < nc; b += gridDim.x) {
+        const int2 cl = list[b];
+        const int k0 = cl.x, m = cl.y;
+        const int st = state[b];
+        if (st == 2) continue;
+        if (n == 1 || g == 0.0) {
+            for (int e = t; e < m * n; e += T) {
+                const int j = e / n, i = e % n;
+                Q[i * ld + k0 + j] = (i == k0 + j) ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            if (t == 0) state[b] = 2;
+            continue;
+        }
+        // the members' solves, one thread each
+        for (int j = t; j < m; j += T) {
+            const int k = k0 + j;
+            if (it == 0) {
+                invit_lu(n, alpha, lambda[k], ptol, bf, ld, k);
+                invit_start(n, Q, ld, k);
+            }
+            invit_solve(n, bf, Q, ld, k);
+        }
+        if (t == 0) {
+            s_ff = m;
+            s_bad = 0;
+        }
+        __syncthreads();
+        // modified Gram-Schmidt in index order, normalisation, growth test
+        for (int j = 0; j < m; j++) {
+            double* qj = Q + k0 + j;
+            for (int p = 0; p < j; p++) {
+                const double* qp = Q + k0 + p;
+                double d = 0.0;
+                for (int i = t; i < n; i += T) d = fma(qp[i * ld], qj[i * ld], d);
+                d = sk_block_sum(d, red);
+                for (int i = t; i < n; i += T) qj[i * ld] = fma(-d, qp[i * ld], qj[i * ld]);
+                __syncthreads();
+            }
+            double s = 0.0;
+            for (int i = t; i < n; i += T) s = fma(qj[i * ld], qj[i * ld], s);
+            const double nrm = sqrt(sk_block_sum(s, red));
+            if (!(nrm > 0.0) || !isfinite(nrm)) {
+                if (t == 0) {
+                    s_bad = 1;
+                    s_ff = min(s_ff, j);
+                }
+            } else {
+                const double inv = 1.0 / nrm;
+                for (int i = t; i < n; i += T) qj[i * ld] *= inv;
+                if (t == 0 && !(nrm >= grow)) s_ff = min(s_ff, j);
+            }
+            __syncthreads();
+        }
+        bool fin, failed;
+        const int nst = clu_next_state(st, s_ff, m, s_bad, it, maxit, fin, failed);
+        if (failed && t == 0) atomicMin(fail, k0 + s_ff);
+        if (fin) {
+            // largest-modulus entry of each vector positive (lowest index on ties)
+            for (int j = 0; j < m; j++) {
+                double* qj = Q + k0 + j;
+                const int imax = block_argmax(n, [&](int i) { return fabs(qj[i * ld]); }, red, redi);
+                const bool neg = qj[imax * ld] < 0.0;  // read by all before any flip
+                __syncthreads();
+                if (neg)
+                    for (int i = t; i < n; i += T) qj[i * ld] = -qj[i * ld];
+                __syncthreads();
+            }
+        }
+        if (t == 0) state[b] = fin ? 2 : nst;
+        __syncthreads();
+    }
+}
+
+// CTA-wide double-float sum (fixed order: deterministic).
+__device__ __forceinline__ Df df_block_sum(Df v, float* rh, float* rl) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = df_add(v, Df{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        rh[warp] = v.h;
+        rl[warp] = v.l;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Df s = {rh[0], rl[0]};
+        for (int w = 1; w < nw; w++) s = df_add(s, Df{rh[w], rl[w]});
+        rh[0] = s.h;
+        rl[0] = s.l;
+    }
+    __syncthreads();
+    const Df r = {rh[0], rl[0]};
+    __syncthreads();
+    return r;
+}
+
+// The lockstep cluster iteration in double-float (the vectors refined
+// afterwards); the members are converted to FP64 when the cluster is done.
+__global__ void __launch_bounds__(CLU_T)
+invit_clu_df_kernel(int n, int nev, const float* __restrict__ alh, const float* __restrict__ all_,
+                    const double* __restrict__ lambda, const TriScalars* sc, int maxit, int it, InvitBufs bf,
+                    double* __restrict__ Q, const int2* __restrict__ list, const int* __restrict__ count,
+                    int* __restrict__ state, int* __restrict__ fail) {
+    __shared__ float rh[32], rl[32];
+    __shared__ double red[32];
+    __shared__ int redi[32];
+    __shared__ int s_ff, s_bad;
+    const int nc = *count;
+    const double g = sc->g;
+    const size_t ld = (size_t)nev;
+    const double eps = 1.0 / 17592186044416.0;  // 2^-44
+    const float ptol = (float)(eps * g);
+    const float grow = (float)(1.0 / (100.0 * sqrt((double)n) * eps * g));
+    const InvitDf v = invit_df_view(bf, Q);
+    Df* Qd = v.Qd;
+    const int t = threadIdx.x, T = blockDim.x;
+    for (int b = blockIdx.x; b < nc; b += gridDim.x) {
+        const int2 cl = list[b];
+        const int k0 = cl.x, m = cl.y;
+        const int st = state[b];
+        if (st == 2) continue;
+        if (n == 1 || g == 0.0) {
+            for (int e = t; e < m * n; e += T) {
+                const int j = e / n, i = e % n;
+                Q[i * ld + k0 + j] = (i == k0 + j) ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            if (t == 0) state[b] = 2;
+            continue;
+        }
+        for (int j = t; j < m; j += T) {
+            const int k = k0 + j;
+            if (it == 0) {
+                invit_lu_df(n, alh, all_, lambda[k], ptol, v, ld, k);
+                invit_start_df(n, Qd, ld, k);
+            }
+            invit_solve_df(n, v, ld, k);
+        }
+        if (t == 0) {
+            s_ff = m;
+            s_bad = 0;
+        }
+        __syncthreads();
+        for (int j = 0; j < m; j++) {
+            Df* qj = Qd + k0 + j;
+            for (int p = 0; p < j; p++) {
+                const Df* qp = Qd + k0 + p;
+                Df d = {0.f, 0.f};
+                for (int i = t; i < n; i += T) d = df_add(d, df_mul(qp[i * ld], qj[i * ld]));
+                const Df md = df_neg(df_block_sum(d, rh, rl));
+                for (int i = t; i < n; i += T) qj[i * ld] = df_add(qj[i * ld], df_mul(md, qp[i * ld]));
+                __syncthreads();
+            }
+            float s = 0.f;
+            for (int i = t; i < n; i += T) {
+                const float y = qj[i * ld].h;
+                s = fmaf(y, y, s);
+            }
+            const float nrm = sqrtf(sk_block_sum(s, rh));
+            if (!(nrm > 0.f) || !isfinite(nrm)) {
+                if (t == 0) {
+                    s_bad = 1;
+                    s_ff = min(s_ff, j);
+                }
+            } else {
+                const Df sc1 = {1.0f / nrm, 0.f};
+                for (int i = t; i < n; i += T) qj[i * ld] = df_mul(qj[i * ld], sc1);
+                if (t == 0 && !(nrm >= grow)) s_ff = min(s_ff, j);
+            }
+            __syncthreads();
+        }
+        bool fin, failed;
+        const int nst = clu_next_state(st, s_ff, m, s_bad, it, maxit, fin, failed);
+        if (failed && t == 0) atomicMin(fail, k0 + s_ff);
+        if (fin) {
+            for (int j = 0; j < m; j++) {
+                Df* qj = Qd + k0 + j;
+                const int imax = block_argmax(n, [&](int i) { return (double)fabsf(qj[i * ld].h); }, red, redi);
+                const bool neg = qj[imax * ld].h < 0.f;  // read by all before any flip
+                __syncthreads();
+                for (int i = t; i < n; i += T) {
+                    const Df y = qj[i * ld];
+                    Q[i * ld + k0 + j] = df_to_double(neg ? df_neg(y) : y);
+                }
+                __syncthreads();
+            }
+        }
+        if (t == 0) state[b] = fin ? 2 : nst;
+        __syncthreads();
+    }
+}
+
 __global__ void invit_df_kernel(int n, int nev, const float* __restrict__ alh, const float* __restrict__ all_,
                                 const double* __restrict__ lambda, const TriScalars* sc, double ctol_rel, int maxit,
                                 InvitBufs bf, double* __restrict__ Q, int* __restrict__ fail) {
     const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (k0 >= nev) return;
-    invit_cluster_df(n, nev, alh, all_, lambda, sc->g, ctol_rel, maxit, bf, Q, fail, k0);
+    invit_cluster_df(n, nev, alh, all_, lambda, sc->g, ctol_rel, maxit, bf, Q, fail, k0, true);
 }
 
 __global__ void invit_kernel(int n, int nev, const double* __restrict__ alpha,
@@ -299,7 +593,7 @@ __global__ void invit_kernel(int n, int nev, const double* __restrict__ alpha,
                              int maxit, InvitBufs bf, double* __restrict__ Q, int* __restrict__ fail) {
     const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (k0 >= nev) return;
-    invit_cluster(n, nev, alpha, lambda, sc->g, ctol_rel, maxit, bf, Q, fail, k0);
+    invit_cluster(n, nev, alpha, lambda, sc->g, ctol_rel, maxit, bf, Q, fail, k0, true);
 }
 
 __global__ void set_int_kernel(int* p, int v) {
@@ -361,6 +655,8 @@ struct TriWs {
     TriScalars* sc;
     int* fail;
     InvitBufs bf;
+    int2* clist;  // clusters of two or more: (first index, size)
+    int *ccount, *cstate;
 };
 
 TriWs carve_tri(Carve& cv, int n, int nev) {
@@ -381,6 +677,9 @@ TriWs carve_tri(Carve& cv, int n, int nev) {
     w.bf.u2 = cv.take<double>(nn * ne);
     w.bf.ml = cv.take<double>(nn * ne);
     w.bf.sw = cv.take<unsigned char>(nn * ne);
+    w.clist = cv.take<int2>(ne / 2 + 1);
+    w.ccount = cv.take<int>(1);
+    w.cstate = cv.take<int>(ne / 2 + 1);
     return w;
 }
 
@@ -425,14 +724,27 @@ int tridiag_eig(cudaStream_t st, int n, const double* alpha, int nev, double* la
         count_launch();
         {
             KtScope kt(st, KT_INVIT);
+            // singletons one thread each; clusters in lockstep, one CTA each
             if (fp64)
                 invit_kernel<<<(nev + 63) / 64, 64, 0, st>>>(n, nev, alpha, lambda, w.sc, ctol, maxit, w.bf, Qi,
                                                              w.fail);
             else
                 invit_df_kernel<<<(nev + 63) / 64, 64, 0, st>>>(n, nev, w.alh, w.all_, lambda, w.sc, ctol, maxit,
                                                                 w.bf, Qi, w.fail);
+            count_launch();
+            clu_list_kernel<<<1, 32, 0, st>>>(nev, lambda, w.sc, ctol, w.clist, w.ccount, w.cstate);
+            count_launch();
+            const int cgrid = std::max(1, std::min(nev / 2, 2 * device_sms()));
+            for (int it = 0; it < maxit; it++) {
+                if (fp64)
+                    invit_clu_kernel<<<cgrid, CLU_T, 0, st>>>(n, nev, alpha, lambda, w.sc, maxit, it, w.bf, Qi,
+                                                              w.clist, w.ccount, w.cstate, w.fail);
+                else
+                    invit_clu_df_kernel<<<cgrid, CLU_T, 0, st>>>(n, nev, w.alh, w.all_, lambda, w.sc, maxit, it,
+                                                                 w.bf, Qi, w.clist, w.ccount, w.cstate, w.fail);
+                count_launch();
+            }
         }
-        count_launch();
         invit_status_kernel<<<1, 32, 0, st>>>(w.fail, nev, d_status);
         count_launch();
     }
