@@ -179,7 +179,7 @@ def parse():
     p.add_argument("--sample-cols", type=int, default=128)
     p.add_argument("--form", default="mixed", choices=["mixed", "fp64"],
                    help="mixed: digit-slice tensor-core contractions + FP64 refinement; fp64: every step FP64")
-    p.add_argument("--qtrd", default="auto", choices=["auto", "fp32", "fp64", "tc"],
+    p.add_argument("--qtrd", default="auto", choices=["auto", "fp32", "fp64", "tc", "df"],
                    help="arithmetic of the Q_trd back-transform (skew_opts.qtrd)")
     p.add_argument("--fp64-compare", type=int, default=1,
                    help="also time this many solves of the FP64 form (reported beside the mixed form)")
@@ -415,7 +415,7 @@ def run_ours(args, ws, rank, local):
 
     mixed = args.form == "mixed"
     qtrd = {"auto": sk.SKEW_QTRD_AUTO, "fp32": sk.SKEW_QTRD_FP32, "fp64": sk.SKEW_QTRD_FP64,
-            "tc": sk.SKEW_QTRD_TC}[args.qtrd]
+            "tc": sk.SKEW_QTRD_TC, "df": sk.SKEW_QTRD_DF}[args.qtrd]
     opts = sk.Options(mode=sk.SKEW_MODE_MIXED_REFINED if mixed else sk.SKEW_MODE_FP64, qtrd=qtrd)
     wsz = sk.workspace_size(n, nev, opts)
     work = torch.empty(wsz, dtype=torch.uint8, device=dev)
