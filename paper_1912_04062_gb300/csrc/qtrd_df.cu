@@ -12,19 +12,22 @@
 //
 // Structure (the FP32 sliding-window kernel's): reflectors grouped into
 // blocks of 64 sweeps x one step (a parallelogram of rows top .. top+126);
-// each CTA owns a slab of columns, four threads per column (row phase q), and
+// each CTA owns a slab of columns, eight threads per column (row phase q), and
 // keeps the block's window in registers; consecutive blocks of a group share
 // 63 rows, so the window slides by 64 rows, the 64 new rows arriving by
 // cp.async while the block computes.  The FP64 reflectors of the next block
 // arrive by one bulk copy and are split into hi / lo pairs in place.
 //
-// Register window.  Thread q holds window rows 4u + q.  The reflector at
-// offset off = 4m + r (r = off mod 4) touches rows off .. off+63, that is for
-// this thread the rows 4(m + w) + q with w = 1..15 always, plus w = 0 when
-// q >= r or w = 16 when q < r: exactly 16 elements.  The registers are kept
-// rotated so that register w holds row 4(m + w) + q: then every index is a
-// compile-time constant inside the four reflectors of one m, and one rotation
-// by a register between consecutive m keeps the invariant.
+// Register window.  Thread q holds window rows 8u + q (u < 16).  The
+// reflector at offset off = 8m + r (r = off mod 8) touches rows off .. off+63,
+// that is for this thread the rows 8(m + w) + q with w = 1..7 always, plus
+// w = 0 when q >= r or w = 8 when q < r: exactly 8 elements.  The registers
+// are kept rotated so that register w holds row 8(m + w) + q: then every
+// register index is a compile-time constant for all eight reflectors of one
+// m (r only moves shared-memory offsets, so they run as a loop, keeping the
+// code small), and one rotation by a register between consecutive m keeps
+// the invariant.  Eight threads per column give twice the warps of four, so
+// the four schedulers of an SM get near-equal shares of a slab.
 #include "common.cuh"
 #include "internal.h"
 #include "sm100.cuh"
@@ -35,7 +38,11 @@ namespace {
 constexpr int DB = 64;              // band width = reflector length
 constexpr int DELL = 64;            // sweeps per block
 constexpr int DH = DELL + DB - 1;   // window height
-constexpr int DLD = 68;             // staging leading dimension in doubles (conflict-free halves)
+constexpr int P = 8;                // threads per column (row phases)
+constexpr int NR = 128 / P;         // window rows per thread
+constexpr int MS = DELL / P;        // rotation steps per block
+constexpr int DLD = 72;             // staging leading dimension in doubles (conflict-free halves)
+constexpr int QD_MAXT = 512;        // threads per CTA at most (64 columns)
 
 __host__ __device__ inline int df_qsteps(int n, int s) { return (s <= n - 3) ? 1 + (n - 3 - s) / DB : 0; }
 
@@ -118,26 +125,29 @@ struct DfSmem {
     uint64_t bar[2];
 };
 
-// One reflector at offset off = 4m + R of the block: vb points at its element 0
-// (hi, lo pairs), H / L registers in the rotated layout of m.
-template <int R>
-SK_DEV void df_reflector(float (&H)[32], float (&L)[32], const float2* __restrict__ vb, float2 tau, int q) {
+// One reflector at offset off = P m + r of the block: vb points at its element
+// 0 (hi, lo pairs), H / L registers in the rotated layout of m.  Thread q's
+// elements are i = P w + q - r for w = 1..7 and the edge w = 0 (q >= r) or
+// w = 8 (q < r); every register index is a compile-time constant, r and q
+// only move the shared-memory offsets and pick the edge register.
+SK_DEV void df_reflector(float (&H)[NR], float (&L)[NR], const float2* __restrict__ vb, float2 tau, int q, int r) {
     if (tau.x == 0.f) return;  // absent step or zero tail: H = I
-    const bool low = q >= R;   // the 16th element is register 0 (else 16)
-    const float2 ve = vb[low ? q - R : DB + q - R];
-    const float2* vw = vb + 4 + q - R;  // vw[4 (w - 1)] = element 4w + q - R, w = 1..15
-    float eh = low ? H[0] : H[16], el = low ? L[0] : L[16];
+    const bool low = q >= r;
+    const float2 ve = vb[low ? q - r : DB + q - r];
+    const float2* vw = vb + P + q - r;  // vw[P (w - 1)] = element P w + q - r, w = 1..7
+    const float eh0 = low ? H[0] : H[P], el0 = low ? L[0] : L[P];
     float S0 = 0.f, C0 = 0.f, S1 = 0.f, C1 = 0.f;
-    dot_term(ve.x, ve.y, eh, el, S0, C0);
+    dot_term(ve.x, ve.y, eh0, el0, S0, C0);
 #pragma unroll
-    for (int w = 1; w < 16; w++) {
-        const float2 v = vw[4 * (w - 1)];
+    for (int w = 1; w < P; w++) {
+        const float2 v = vw[P * (w - 1)];
         if (w & 1) dot_term(v.x, v.y, H[w], L[w], S1, C1);
         else dot_term(v.x, v.y, H[w], L[w], S0, C0);
     }
     df_add(S0, C0, S1, C1);
-    df_add(S0, C0, __shfl_xor_sync(0xffffffffu, S0, 1), __shfl_xor_sync(0xffffffffu, C0, 1));
-    df_add(S0, C0, __shfl_xor_sync(0xffffffffu, S0, 2), __shfl_xor_sync(0xffffffffu, C0, 2));
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1)
+        df_add(S0, C0, __shfl_xor_sync(0xffffffffu, S0, o), __shfl_xor_sync(0xffffffffu, C0, o));
     // a = tau (v^T z)
     float ah, al;
     {
@@ -147,22 +157,23 @@ SK_DEV void df_reflector(float (&H)[32], float (&L)[32], const float2* __restric
         e = __fmaf_rn(tau.y, S0, e);
         fast_two_sum(p, e, ah, al);
     }
+    float eh = eh0, el = el0;
     axpy_term(ah, al, ve.x, ve.y, eh, el);
     if (low) {
         H[0] = eh;
         L[0] = el;
     } else {
-        H[16] = eh;
-        L[16] = el;
+        H[P] = eh;
+        L[P] = el;
     }
 #pragma unroll
-    for (int w = 1; w < 16; w++) {
-        const float2 v = vw[4 * (w - 1)];
+    for (int w = 1; w < P; w++) {
+        const float2 v = vw[P * (w - 1)];
         axpy_term(ah, al, v.x, v.y, H[w], L[w]);
     }
 }
 
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(QD_MAXT, 1)
 qtrd_df_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict__ tautrd, double* __restrict__ Z,
                int ldz, int ncols, int slab, int* status) {
     extern __shared__ __align__(128) unsigned char qd_raw[];
@@ -173,7 +184,7 @@ qtrd_df_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict_
     if (nc <= 0) return;
     const int t = threadIdx.x, T = blockDim.x;
     // every lane takes part in the shuffles; lanes past the slab work on zeros
-    const int c = t >> 2, q = t & 3;
+    const int c = t / P, q = t % P;
     const bool own = c < nc;
     double* zc = Z + (size_t)(c0 + (own ? c : 0)) * ldz;
     if (t == 0) {
@@ -203,13 +214,14 @@ qtrd_df_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict_
     for (int g = ngroups - 1; g >= 0; g--) {
         const int s0 = g * DELL;
         const int kmax = df_qsteps(n, s0);
-        float H[32], L[32];
+        float H[NR], L[NR];
         {
-            // window of block (g, 0), rotated for m = 15: register w <- row 4((w + 15) mod 32) + q
+            // window of block (g, 0), rotated for m = MS - 1: register w <- row
+            // P ((w + MS - 1) mod NR) + q
             const int top = s0 + 1, Hh = min(DH, n - top);
 #pragma unroll
-            for (int w = 0; w < 32; w++) {
-                const int r = 4 * ((w + 15) & 31) + q;
+            for (int w = 0; w < NR; w++) {
+                const int r = P * ((w + MS - 1) % NR) + q;
                 const float2 f = (own && r < Hh) ? df_split(zc[top + r]) : make_float2(0.f, 0.f);
                 H[w] = f.x;
                 L[w] = f.y;
@@ -254,25 +266,25 @@ qtrd_df_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict_
             __syncthreads();
             const float2* vblk = reinterpret_cast<const float2*>(sm.v[buf]);
 #pragma unroll 1
-            for (int m = DELL / 4 - 1; m >= 0; m--) {
-                const float2* vm = vblk + (size_t)(4 * m) * DB;
-                df_reflector<3>(H, L, vm + 3 * DB, sm.tau[buf][4 * m + 3], q);
-                df_reflector<2>(H, L, vm + 2 * DB, sm.tau[buf][4 * m + 2], q);
-                df_reflector<1>(H, L, vm + 1 * DB, sm.tau[buf][4 * m + 1], q);
-                df_reflector<0>(H, L, vm, sm.tau[buf][4 * m], q);
-                // renormalise the pairs these four reflectors touched (w = 0..16)
+            for (int m = MS - 1; m >= 0; m--) {
+#pragma unroll 1
+                for (int r = P - 1; r >= 0; r--) {
+                    const int off = P * m + r;
+                    df_reflector(H, L, vblk + (size_t)off * DB, sm.tau[buf][off], q, r);
+                }
+                // renormalise the pairs these P reflectors touched (w = 0..P)
 #pragma unroll
-                for (int w = 0; w <= 16; w++) {
+                for (int w = 0; w <= P; w++) {
                     float s, e;
                     two_sum(H[w], L[w], s, e);
                     H[w] = s;
                     L[w] = e;
                 }
                 if (m > 0) {
-                    // register w now holds row 4(m - 1 + w) + q
-                    const float th = H[31], tl = L[31];
+                    // register w now holds row P (m - 1 + w) + q
+                    const float th = H[NR - 1], tl = L[NR - 1];
 #pragma unroll
-                    for (int w = 31; w > 0; w--) {
+                    for (int w = NR - 1; w > 0; w--) {
                         H[w] = H[w - 1];
                         L[w] = L[w - 1];
                     }
@@ -280,32 +292,32 @@ qtrd_df_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict_
                     L[0] = tl;
                 }
             }
-            // register u holds row 4u + q now
+            // register u holds row P u + q now
             if (more) {
                 // rows 0..63 are final for this group: out through shared memory
 #pragma unroll
-                for (int u = 0; u < 16; u++) sm.zout[c * DLD + 4 * u + q] = df_join(H[u], L[u]);
+                for (int u = 0; u < NR / 2; u++) sm.zout[c * DLD + P * u + q] = df_join(H[u], L[u]);
                 asm volatile("cp.async.wait_all;" ::: "memory");
                 __syncthreads();
                 for (int e = t; e < 64 * nc; e += T) {
                     const int cc = e >> 6, j = e & 63;
                     Z[(size_t)(c0 + cc) * ldz + top + j] = sm.zout[cc * DLD + j];  // top + 63 < n here
                 }
-                // slide by 64 rows and rotate for m = 15: new row u' goes to
-                // register (u' + 17) mod 32; rows 0..62 are old rows 64..126,
-                // rows 63..126 come from zin, row 127 is padding
-                float NH[32], NL[32];
+                // slide by 64 rows and rotate for m = MS - 1: new row u' goes to
+                // register (u' - MS + 1) mod NR; rows 0..62 are old rows
+                // 64..126, rows 63..126 come from zin, row 127 is padding
+                float NH[NR], NL[NR];
 #pragma unroll
-                for (int up = 0; up < 32; up++) {
-                    const int dst = (up + 17) & 31;
-                    if (up <= 14) {
-                        NH[dst] = H[up + 16];
-                        NL[dst] = L[up + 16];
+                for (int up = 0; up < NR; up++) {
+                    const int dst = (up + NR - MS + 1) % NR;
+                    if (up < NR / 2 - 1) {
+                        NH[dst] = H[up + NR / 2];
+                        NL[dst] = L[up + NR / 2];
                     } else {
-                        const int j = 4 * up + q - (DH - DB);  // zin row of window row 4 up + q
+                        const int j = P * up + q - (DH - DB);  // zin row of window row P up + q
                         float2 f = make_float2(0.f, 0.f);
-                        if (up == 15 && q <= 2) {
-                            f = make_float2(H[31], L[31]);
+                        if (up == NR / 2 - 1 && P * up + q <= DH - DB - 1) {
+                            f = make_float2(H[NR - 1], L[NR - 1]);
                         } else if (j < 64) {
                             f = df_split(sm.zin[c * DLD + j]);
                         }
@@ -314,7 +326,7 @@ qtrd_df_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict_
                     }
                 }
 #pragma unroll
-                for (int w = 0; w < 32; w++) {
+                for (int w = 0; w < NR; w++) {
                     H[w] = NH[w];
                     L[w] = NL[w];
                 }
@@ -324,8 +336,8 @@ qtrd_df_kernel(int n, const double* __restrict__ Vtrd, const double* __restrict_
                 const int Hh = min(DH, n - top);
                 if (own) {
 #pragma unroll
-                    for (int u = 0; u < 32; u++) {
-                        const int r = 4 * u + q;
+                    for (int u = 0; u < NR; u++) {
+                        const int r = P * u + q;
                         if (r < Hh) zc[top + r] = df_join(H[u], L[u]);
                     }
                 }
@@ -343,19 +355,20 @@ cudaError_t apply_qtrd_df(cudaStream_t st, int n, int b, const double* Vtrd, con
                           int ldz, int k, int* status) {
     if (b != DB) return cudaErrorInvalidValue;
     if (n < 3 || k <= 0) return cudaSuccess;
-    // one CTA per SM (the staging takes 131 KB); slabs of at most 64 columns
+    // one CTA per SM (the staging takes 140 KB); slabs of at most 64 columns
     // sized so that the CTAs fill whole waves
     const int sms = device_sms();
-    int waves = 1, slab = 64;
+    const int maxslab = QD_MAXT / P;
+    int waves = 1, slab = maxslab;
     while (true) {
         slab = (k + sms * waves - 1) / (sms * waves);
-        if (slab <= 64) break;
+        if (slab <= maxslab) break;
         waves++;
     }
     if (slab < 8) slab = (k < 8) ? k : 8;
     const int grid = (k + slab - 1) / slab;
     // at least 64 threads: thread t < 64 brings the tau of sweep t
-    const int threads = max(64, (4 * slab + 31) / 32 * 32);
+    const int threads = max(64, (P * slab + 31) / 32 * 32);
     const size_t smem = sizeof(DfSmem);
     cudaFuncSetAttribute(qtrd_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     KtScope kt(st, KT_QTRD);
