@@ -115,13 +115,20 @@ __device__ void bt_reduce_body(const BItem& it, double* S, int ld, double* v, do
                 p[i] = tau * s2;
             }
             __syncthreads();
-            // S22 += v p^T - p v^T on the whole square: each product is rounded
-            // on its own, so element (j, i) receives exactly minus what (i, j)
-            // receives and S stays exactly skew
+            // S22 += v p^T - p v^T: each product is rounded on its own, so the
+            // update of (j, i) is exactly minus that of (i, j); the strict lower
+            // triangle is computed and its negation stored above (the diagonal
+            // stays 0), which keeps S exactly skew with half the FP64 work of
+            // updating the whole square, and the same values
             const int m = n - c - 1;
             for (int e = t; e < m * m; e += BT) {
                 const int i = c + 1 + e % m, j = c + 1 + e / m;
-                S[i + (size_t)j * ld] += __dsub_rn(__dmul_rn(v[i], p[j]), __dmul_rn(p[i], v[j]));
+                if (i > j) {
+                    const double x =
+                        S[i + (size_t)j * ld] + __dsub_rn(__dmul_rn(v[i], p[j]), __dmul_rn(p[i], v[j]));
+                    S[i + (size_t)j * ld] = x;
+                    S[j + (size_t)i * ld] = -x;
+                }
             }
         }
         __syncthreads();
