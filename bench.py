@@ -452,6 +452,47 @@ def run_ours(args, ws, rank, local):
     del work
     torch.cuda.empty_cache()
 
+    # ---- end to end through the host-buffer entry point (pinned host
+    # memory; the copies in and out are inside each call)
+    e2e = None
+    if args.e2e_steps > 0:
+        hA = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        hA.copy_(A)
+        hl = torch.empty(nev, dtype=torch.float64, pin_memory=True)
+        hZr = torch.empty((nev, n), dtype=torch.float64, pin_memory=True).t()
+        hZi = torch.empty((nev, n), dtype=torch.float64, pin_memory=True).t()
+        torch.cuda.empty_cache()
+        L = sk.lib()
+        oc = opts.c()
+
+        def host_solve():
+            code = L.skew_eig_host(n, sk._ptr(hA), n, nev, sk._ptr(hl), sk._ptr(hZr), sk._ptr(hZi),
+                                   sk.ctypes.byref(oc), sk._stream(stream))
+            if code != 0:
+                raise RuntimeError(f"host solve failed: {code}")
+
+        host_solve()  # warm-up: the library pool reserves the workspace once
+        torch.cuda.synchronize()
+        barrier(ws)
+        eclk = ClockSampler(local)
+        eclk.start()
+        t0 = time.perf_counter()
+        per_call = []
+        for _ in range(args.e2e_steps):
+            t1 = time.perf_counter()
+            host_solve()  # synchronous: returns after the copies out
+            per_call.append(round(time.perf_counter() - t1, 4))
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        e2e_clocks = eclk.stop()
+        e2e_s = max_over_ranks(ws, e2e_s)
+        sk.lib().skew_release_memory()
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n * n,
+               "d2h_bytes_per_step": 8 * (nev + 2 * n * nev), "entry": "skew_eig_host",
+               "calls": args.e2e_steps, "warmup_calls": 1, "per_call_s": per_call,
+               "clocks": e2e_clocks}
+        del hA, hZr, hZi
+
     # ---- the FP64 form on the same matrix (the comparison the metric names)
     fp64 = None
     if mixed and args.fp64_compare > 0:
@@ -475,43 +516,6 @@ def run_ours(args, ws, rank, local):
         del w64, X64, Y64
         torch.cuda.empty_cache()
     total_F = 4.0 / 3.0 * n ** 3 + 8.0 * nev * n * n
-
-    # ---- end to end through the host-buffer entry point (pinned host
-    # memory; the copies in and out are inside each call)
-    e2e = None
-    if args.e2e_steps > 0:
-        hA = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
-        hA.copy_(A)
-        hl = torch.empty(nev, dtype=torch.float64, pin_memory=True)
-        hZr = torch.empty((nev, n), dtype=torch.float64, pin_memory=True).t()
-        hZi = torch.empty((nev, n), dtype=torch.float64, pin_memory=True).t()
-        del A, Zr, Zi
-        torch.cuda.empty_cache()
-        L = sk.lib()
-        oc = opts.c()
-
-        def host_solve():
-            code = L.skew_eig_host(n, sk._ptr(hA), n, nev, sk._ptr(hl), sk._ptr(hZr), sk._ptr(hZi),
-                                   sk.ctypes.byref(oc), sk._stream(stream))
-            if code != 0:
-                raise RuntimeError(f"host solve failed: {code}")
-
-        host_solve()  # warm-up: the library pool reserves the workspace once
-        torch.cuda.synchronize()
-        barrier(ws)
-        t0 = time.perf_counter()
-        per_call = []
-        for _ in range(args.e2e_steps):
-            t1 = time.perf_counter()
-            host_solve()  # synchronous: returns after the copies out
-            per_call.append(round(time.perf_counter() - t1, 4))
-        torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        e2e_s = max_over_ranks(ws, e2e_s)
-        sk.lib().skew_release_memory()
-        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n * n,
-               "d2h_bytes_per_step": 8 * (nev + 2 * n * nev), "entry": "skew_eig_host",
-               "calls": args.e2e_steps, "warmup_calls": 1, "per_call_s": per_call}
 
     cpu = None
     if rank == 0 and not args.no_cpu and ws == 1:
