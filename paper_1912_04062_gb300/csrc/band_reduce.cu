@@ -73,6 +73,9 @@ panel_qr_kernel(int m, int nb, double* __restrict__ P, int ldp, double* __restri
                 rowbuf[buf * nb + c] = S[(size_t)c * rpc + (i - r0)];
         }
         if (!sk_grid_barrier(bar, epoch, status, spin_cap)) return;
+        // row i's entries: loaded now, in flight with the partials below
+        const double x0_pre = (t == 0) ? __ldcg(rowbuf + buf * nb + i) : 0.0;
+        const double rb_pre = (i + 1 + t < nb) ? __ldcg(rowbuf + buf * nb + i + 1 + t) : 0.0;
         // ---- phase B: reduce partials, four threads per column over CTAs
         // q, q+4, .. (a fixed order: identical in all CTAs)
         for (int cb = i; cb < nb; cb += QR_THREADS / 4) {
@@ -91,7 +94,7 @@ panel_qr_kernel(int m, int nb, double* __restrict__ P, int ldp, double* __restri
         }
         __syncthreads();
         if (t == 0) {
-            double x0 = __ldcg(rowbuf + buf * nb + i);
+            double x0 = x0_pre;
             double tail2 = ws[i];
             double tu, sc, be;
             if (tail2 == 0.0) {
@@ -109,7 +112,7 @@ panel_qr_kernel(int m, int nb, double* __restrict__ P, int ldp, double* __restri
         const double tu = s_tau, sc = s_scale;
         // w_c = v^T P[:, c] = P[i, c] + scale * (x_tail . P_tail[:, c]), c > i
         for (int c = i + 1 + t; c < nb; c += QR_THREADS)
-            ws[c] = __ldcg(rowbuf + buf * nb + c) + sc * ws[c];
+            ws[c] = ((c == i + 1 + t) ? rb_pre : __ldcg(rowbuf + buf * nb + c)) + sc * ws[c];
         for (int r = t; r < rows; r += QR_THREADS) {
             int gr = r0 + r;
             double v = 0.0;

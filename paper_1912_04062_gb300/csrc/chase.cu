@@ -147,12 +147,14 @@ __device__ bool chase_task(int n, int s, int k, int nsw, const int* __restrict__
         int ok = 1;
         if (want > 0) {
             unsigned polls = 0;
+            // error word every 256 polls, sleeps only after 256 tries
             while (sk_ld_acquire_s32(prog_prev) < want) {
-                if (++polls > spin_cap || *(volatile int*)status != 0) {
+                ++polls;
+                if (polls > spin_cap || ((polls & 255u) == 0 && *(volatile int*)status != 0)) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
+                if (polls > 256) __nanosleep(32);
             }
             if (!ok) sk_set_error(status, SKEW_ERR_DEVICE_TIMEOUT);
         }

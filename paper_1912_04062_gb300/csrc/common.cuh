@@ -59,12 +59,16 @@ SK_DEV bool sk_grid_barrier(unsigned* counter, unsigned& epoch, int* status, uns
         sk_atom_add_release(counter, 1u);
         int ok = 1;
         unsigned polls = 0;
+        // the error word is read every 256 polls and the poll sleeps only
+        // after 256 tries: a barrier completes within one L2 round trip of
+        // its last arrival
         while (sk_ld_acquire(counter) < target) {
-            if (++polls > cap || *(volatile int*)status != 0) {
+            ++polls;
+            if (polls > cap || ((polls & 255u) == 0 && *(volatile int*)status != 0)) {
                 ok = 0;
                 break;
             }
-            __nanosleep(64);
+            if (polls > 256) __nanosleep(64);
         }
         if (!ok) sk_set_error(status, SKEW_ERR_DEVICE_TIMEOUT);
         s_ok = ok;
