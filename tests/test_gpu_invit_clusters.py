@@ -14,7 +14,8 @@ off-diagonals, so that each block eigenvalue becomes a cluster of r
 eigenvalues inside a window of about the coupling: 20 clusters of 20, and
 two clusters of 300 (more members than the CTA has threads).  The double-
 float form runs inside the refined solve; a prescribed spectrum with planted
-8-fold clusters checks it at the FP64 bounds.
+8-fold clusters checks it at the FP64 bounds.  The clustered workload's own
+recipe (n = 4096, 0.1 n vectors) checks both forms with partial vectors.
 """
 import numpy as np
 import pytest
@@ -112,3 +113,41 @@ def test_refined_solve_with_planted_clusters():
     m = oracle.scaled_metrics(A, lam.cpu().numpy(), Zr.cpu().numpy(), Zi.cpu().numpy(), lam_ref=lam_ref,
                               norm2=float(lam_ref[0]))
     assert m["eig_err"] <= 1e-12 and m["resid"] <= 50 and m["orth"] <= 50, m
+
+
+@pytest.mark.parametrize("mode", ["fp64", "refined"])
+def test_clustered_spectrum_partial_vectors_match_oracle(mode):
+    # the clustered workload's recipe at n = 4096 (log-uniform spectrum in
+    # [1e-6, 1], 5 % of the values in 16-fold groups inside 1e-10 windows; two
+    # groups fall among the 0.1 n wanted values at this seed): partial vectors,
+    # so the refined mode runs the double-float Q_trd and both forms run the
+    # lockstep clusters.  Eigenvalues against the prescribed spectrum, the FP64
+    # bounds, and each planted group's subspace against the oracle's
+    import torch
+    import inputs
+    import oracle
+    import paper_1912_04062_gb300 as sk
+    n = 4096
+    nev = n // 10
+    A, l = inputs.clustered(n, seed=4)
+    lam_ref = np.sort(l)[::-1][:nev]
+    groups = [(k0, k1) for k0, k1 in _clusters(lam_ref, 1e-8) if k1 - k0 >= 16]
+    assert len(groups) >= 2
+    dA = sk.fortran(torch.from_numpy(np.asfortranarray(A)).cuda())
+    opts = sk.Options(mode=sk.SKEW_MODE_FP64 if mode == "fp64" else sk.SKEW_MODE_MIXED_REFINED)
+    ws = torch.empty(sk.workspace_size(n, nev, opts), dtype=torch.uint8, device="cuda")
+    lam = torch.empty(nev, dtype=torch.float64, device="cuda")
+    Zr, Zi = sk.fortran_empty(n, nev), sk.fortran_empty(n, nev)
+    info = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    assert sk.skew_eig_ex(dA, nev, lam, Zr, Zi, ws, info, opts) == 0
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    L, X, Y = lam.cpu().numpy(), Zr.cpu().numpy(), Zi.cpu().numpy()
+    m = oracle.scaled_metrics(A, L, X, Y, lam_ref=lam_ref, norm2=float(np.max(l)))
+    assert m["eig_err"] <= 1e-12 and m["resid"] <= 50 and m["orth"] <= 50, m
+    lo, Xo, Yo, info_o = oracle.skew_eig(A, nev)
+    assert info_o == 0
+    Z, Zo = X + 1j * Y, Xo + 1j * Yo
+    for k0, k1 in groups:
+        sv = np.linalg.svd(Z[:, k0:k1].conj().T @ Zo[:, k0:k1], compute_uv=False)
+        assert np.min(sv) >= 1 - 1e-8, (k0, k1, float(np.min(sv)))
