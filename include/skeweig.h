@@ -175,6 +175,12 @@ size_t skew_eig_workspace_size_ex(int n, int nev, const skew_opts* opts, int vec
  * bytes, 256-byte aligned).  ldz >= max(1, n) is the leading dimension of
  * Z_re / Z_im.  The numerical status is written to *d_info (device int) in
  * stream order; the return value only reports argument and launch errors.
+ * Without refinement (the FP64 form, and the mixed modes when nev < n/2, n is
+ * odd or no vectors are wanted) the call neither allocates nor synchronises,
+ * and its launches can be captured in a CUDA graph and replayed.  With
+ * refinement (mixed modes, n even, nev = n/2) it synchronises `stream` once
+ * per refinement iteration to read the convergence test on the host, so it
+ * returns after the solve and cannot be captured.
  * Arguments are numbered as in skew_eig with 8 ldz, 9 opts (NULL = default),
  * 10 workspace, 11 ws_bytes, 12 d_info, 13 stream.
  */

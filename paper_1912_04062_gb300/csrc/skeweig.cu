@@ -847,9 +847,12 @@ int skew_eig_host(int n, const double* A, int lda, int nev, double* lambda, doub
     int* d_info = reinterpret_cast<int*>(base + bytes - 256);
     int info = 0;
     rc = 0;
-    if (cudaMemcpy2DAsync(dA, sizeof(double) * nn, A, sizeof(double) * (size_t)lda, sizeof(double) * nn, nn,
-                          cudaMemcpyHostToDevice, st) != cudaSuccess)
-        rc = SKEW_ERR_CUDA;
+    // one linear copy when the columns are contiguous, a pitched one otherwise
+    const cudaError_t ce =
+        (lda == n) ? cudaMemcpyAsync(dA, A, sizeof(double) * nn * nn, cudaMemcpyHostToDevice, st)
+                   : cudaMemcpy2DAsync(dA, sizeof(double) * nn, A, sizeof(double) * (size_t)lda, sizeof(double) * nn,
+                                       nn, cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) rc = SKEW_ERR_CUDA;
     if (!rc) rc = run_solve(st, n, dA, n, nev, dl, dzr, dzi, n, opts, base, bytes - 256, d_info);
     if (!rc) {
         if (cudaMemcpyAsync(lambda, dl, sizeof(double) * nev, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SKEW_ERR_CUDA;
