@@ -477,11 +477,16 @@ def run_ours(args, ws, rank, local):
         eclk = ClockSampler(local)
         eclk.start()
         t0 = time.perf_counter()
-        per_call = []
+        per_call, per_call_dev = [], []
         for _ in range(args.e2e_steps):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
             t1 = time.perf_counter()
             host_solve()  # synchronous: returns after the copies out
             per_call.append(round(time.perf_counter() - t1, 4))
+            ev1.record(stream)
+            ev1.synchronize()
+            per_call_dev.append(round(ev0.elapsed_time(ev1) / 1e3, 4))
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         e2e_clocks = eclk.stop()
@@ -490,6 +495,7 @@ def run_ours(args, ws, rank, local):
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n * n,
                "d2h_bytes_per_step": 8 * (nev + 2 * n * nev), "entry": "skew_eig_host",
                "calls": args.e2e_steps, "warmup_calls": 1, "per_call_s": per_call,
+               "per_call_device_s": per_call_dev,
                "clocks": e2e_clocks}
         del hA, hZr, hZi
 

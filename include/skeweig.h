@@ -175,12 +175,12 @@ size_t skew_eig_workspace_size_ex(int n, int nev, const skew_opts* opts, int vec
  * bytes, 256-byte aligned).  ldz >= max(1, n) is the leading dimension of
  * Z_re / Z_im.  The numerical status is written to *d_info (device int) in
  * stream order; the return value only reports argument and launch errors.
- * Without refinement (the FP64 form, and the mixed modes when nev < n/2, n is
- * odd or no vectors are wanted) the call neither allocates nor synchronises,
- * and its launches can be captured in a CUDA graph and replayed.  With
- * refinement (mixed modes, n even, nev = n/2) it synchronises `stream` once
- * per refinement iteration to read the convergence test on the host, so it
- * returns after the solve and cannot be captured.
+ * The call neither allocates nor synchronises, and its launches can be
+ * captured in a CUDA graph and replayed: the refinement of the mixed modes
+ * takes its decisions (stop, digit slices of the update) on the device and
+ * launches its full iteration budget, whose launches after the stop return at
+ * once.  With kernel timing on (skew_kernel_timing) the refinement reads its
+ * decisions on the host instead, synchronising `stream` once per iteration.
  * Arguments are numbered as in skew_eig with 8 ldz, 9 opts (NULL = default),
  * 10 workspace, 11 ws_bytes, 12 d_info, 13 stream.
  */
@@ -387,8 +387,8 @@ int skew_gemm_f64acc_ex(int M, int N, int K, double alpha, const double* A,
  * given approximate lambda (n/2) and Z_re / Z_im (n x n/2, ld ldz, device)
  * of skew A (n even), run at most `iters` Ogita-Aishima iterations through
  * H = -iA with FP64-accurate tensor-core products and overwrite them.
- * Synchronises `stream` once per iteration (convergence test).  Workspace
- * >= skew_refine_ws(n) bytes.  Not in the paper.
+ * Asynchronous (the convergence test runs on the device; see skew_eig_ex).
+ * Workspace >= skew_refine_ws(n) bytes.  Not in the paper.
  * Arguments: 1 n (even, >= 2), 2 A, 3 lda, 4 lambda, 5/6 Z_re/Z_im, 7 ldz,
  * 8 iters >= 1.
  */
@@ -397,8 +397,10 @@ int skew_refine(int n, const double* A, int lda, double* lambda, double* Z_re,
                 double* Z_im, int ldz, int iters, void* ws, size_t ws_bytes,
                 int* d_status, void* stream);
 
-/* Statistics of the most recent refinement in this process (diagnostics):
- * returns the number of iterations; emax[i] = largest first-order correction
+/* Statistics of the most recent refinement in this process (diagnostics;
+ * read them after synchronising the stream of that solve, whose record
+ * arrives in stream order): returns the number of iterations; emax[i] =
+ * largest first-order correction
  * |E_jk| of iteration i, nclose[i] = pairs not separated enough for it
  * (up to cap entries each, either pointer may be NULL). */
 int skew_refine_stats(double* emax, int* nclose, int cap);

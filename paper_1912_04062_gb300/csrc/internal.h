@@ -145,15 +145,20 @@ struct OzOperand {
 // copying (k0 a multiple of 64; rows and K within the operand).
 OzOperand oz_view(const OzOperand& o, int r0, int k0, int rows, int K);
 size_t ozaki_operand_ws(int rows, int K);
+// skip (device flag, may be null): nonzero at run time -> the launches do nothing.
 int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long rs, long long ks, double sgn, int skew,
-                void* ws, size_t ws_bytes, OzOperand* op);
+                void* ws, size_t ws_bytes, OzOperand* op, const int* skip = nullptr);
 // ksplit > 1: K is cut into up to that many ranges (one CTA per tile and
 // range) and the partial tiles, ranges x N x M doubles in part (capacity
 // part_elems doubles: fewer ranges are taken when they would not fit), are
 // summed in order.
 int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, double alpha, double beta, double* C,
                    long long ldc, int* status, int slices = 8, int lower = 0, int ksplit = 1,
-                   double* part = nullptr, size_t part_elems = 0);
+                   double* part = nullptr, size_t part_elems = 0, const int* skip = nullptr,
+                   const int* s_dyn = nullptr);
+// skip: device flag, nonzero at run time -> the launch does nothing; s_dyn:
+// device slice count (1 .. slices) read by the kernel in place of slices
+// (the launch shape and the work recorded for kernel timing use slices).
 // a_skew: A is the skew matrix of the strict lower triangle stored column-major
 // with leading dimension a_ks (a_rs unused).  slices (1..8): digit slices kept,
 // accuracy about 2^-7 slices relative to |a_r|max |b_c|max per term.  lower:
@@ -180,6 +185,12 @@ size_t refine_ws(int n);
 int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, double* M, int maxit, void* ws,
            size_t ws_bytes, int* status, RefineInfo* info, double rho = 1024.0);
 RefineInfo& last_refine_info();
+// Statistics of a refinement that ran without host round trips reach
+// last_refine_info() through a pinned buffer: refine_stats_flush() copies
+// them in (the caller has synchronised the solve's stream first);
+// refine_stats_discard() drops a copy still pending (a new solve started).
+void refine_stats_flush();
+void refine_stats_discard();
 
 // ---- batched.cu (many small independent solves) ------------------------------
 // Largest order of the one-CTA shared-memory path, and of the batched path
@@ -260,6 +271,7 @@ enum {
 extern int g_kt_ozaki_kind;
 int kt_begin(cudaStream_t st);
 void kt_end(cudaStream_t st, int slot, int kind, double flops);
+bool kt_enabled();
 // Brackets the launches issued in its lifetime as one timed record of `kind`.
 struct KtScope {
     cudaStream_t st;

@@ -79,6 +79,8 @@ struct OzParams {
     int kz;                  // split K: chunks per split (blockIdx.y), 0 = whole K
     double* part;            // split K: partial tiles, [split][N][M]
     int akoff, bkoff;        // K offsets of views into larger splits (elements)
+    const int* skip;         // device flag: nonzero -> the launch does nothing (may be null)
+    const int* s_dyn;        // device slice count overriding s (may be null)
 };
 
 struct OzSmem {
@@ -178,6 +180,8 @@ template <bool ONE>
 __global__ void __maxnreg__(168)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams p) {
     extern __shared__ unsigned char oz_raw[];
+    // a skipped launch returns before any barrier, copy or tensor-memory use
+    if (p.skip && *p.skip) return;
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) &
                                                          ~uintptr_t(1023));
     unsigned char* sB = sm;                        // [set][slice] 64 x 128 B
@@ -194,7 +198,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     __shared__ int s_bi, s_bc, s_ai, s_ac;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = p.s;
+    const int S = p.s_dyn ? *p.s_dyn : p.s;
     const int nz = p.kz ? (p.nchunks + p.kz - 1) / p.kz : 1;
     const int nitems = p.mt * p.nt * nz;  // below 2^31 for every supported size
     // Work item it = (tile, K range z), tile = it / nz.  Tile order: groups of
@@ -447,7 +451,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 // per block, read along rows (coalesced); per-row maxima go to rowmax (ordered
 // bit patterns of non-negative doubles) with atomicMax.
 __global__ void oz_rowmax_cols_kernel(int rows, int K, const double* __restrict__ src, long long sk,
-                                      unsigned long long* __restrict__ rowmax) {
+                                      unsigned long long* __restrict__ rowmax, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ unsigned long long red[8][33];
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     const int r = blockIdx.x * 32 + tx, k0 = blockIdx.y * 256;
@@ -468,7 +473,9 @@ __global__ void oz_rowmax_cols_kernel(int rows, int K, const double* __restrict_
 // Digit slices when rows are contiguous (sr == 1): a 32 x 32 tile is read
 // along rows and written along k through shared memory.
 __global__ void oz_split_cols_kernel(int rows, int K, int Rp, int Kp, const double* __restrict__ src, long long sk,
-                                     double sgn, const int* __restrict__ e, __nv_bfloat16* __restrict__ dst) {
+                                     double sgn, const int* __restrict__ e, __nv_bfloat16* __restrict__ dst,
+                                     const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ double tile[32][33];
     const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -500,7 +507,8 @@ SK_DEV double oz_elem(const double* __restrict__ src, long long sr, long long sk
 }
 
 __global__ void oz_exp_kernel(int rows, int K, const double* __restrict__ src, long long sr, long long sk,
-                              int* __restrict__ e, int skew) {
+                              int* __restrict__ e, int skew, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ unsigned long long red[32];
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
         unsigned long long m = 0;
@@ -526,7 +534,9 @@ __global__ void oz_exp_kernel(int rows, int K, const double* __restrict__ src, l
 // comes from L2).  Padding rows and columns are zero.
 __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, int Rp, int Kp, const double* __restrict__ src,
                                                             long long sr, double sgn, int* __restrict__ e,
-                                                            __nv_bfloat16* __restrict__ dst) {
+                                                            __nv_bfloat16* __restrict__ dst,
+                                                            const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ unsigned long long red[8];
     const bool neg = sgn < 0.0;
     for (int r = blockIdx.x; r < Rp; r += gridDim.x) {
@@ -560,7 +570,9 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, int
 // Digit slices: plane i holds rows [i Rp, i Rp + rows) of a (SL Rp) x Kp
 // row-major BF16 array; padding rows / columns are zero.
 __global__ void oz_split_kernel(int rows, int K, int Rp, int Kp, const double* __restrict__ src, long long sr,
-                                long long sk, double sgn, const int* __restrict__ e, __nv_bfloat16* __restrict__ dst) {
+                                long long sk, double sgn, const int* __restrict__ e, __nv_bfloat16* __restrict__ dst,
+                                const int* __restrict__ skip) {
+    if (skip && *skip) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Kp) return;
     for (int r = blockIdx.y; r < Rp; r += gridDim.y) {
@@ -577,7 +589,8 @@ __global__ void oz_split_kernel(int rows, int K, int Rp, int Kp, const double* _
 // tiles of the lower triangle, read along i; per-tile row and column maxima go
 // to rowmax (as ordered bit patterns of non-negative doubles) with atomicMax.
 __global__ void oz_skew_rowmax_kernel(int n, const double* __restrict__ W, long long ld,
-                                      unsigned long long* __restrict__ rowmax) {
+                                      unsigned long long* __restrict__ rowmax, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ unsigned long long tile[32][33];
     const int bi = blockIdx.x, bj = blockIdx.y;
     if (bi < bj) return;
@@ -596,7 +609,9 @@ __global__ void oz_skew_rowmax_kernel(int n, const double* __restrict__ W, long 
     }
 }
 
-__global__ void oz_exp_from_max_kernel(int rows, const unsigned long long* __restrict__ rowmax, int* __restrict__ e) {
+__global__ void oz_exp_from_max_kernel(int rows, const unsigned long long* __restrict__ rowmax, int* __restrict__ e,
+                                       const int* __restrict__ skip) {
+    if (skip && *skip) return;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
         const double m = __longlong_as_double((long long)rowmax[r]);
         int ex = 0;
@@ -608,7 +623,9 @@ __global__ void oz_exp_from_max_kernel(int rows, const unsigned long long* __res
 // Digit slices of the skew S: tiles below the diagonal are read along rows of
 // W and transposed through shared memory, tiles above read -W(k, r) along k.
 __global__ void oz_split_skew_kernel(int rows, int Rp, int Kp, const double* __restrict__ W, long long ld,
-                                     const int* __restrict__ e, __nv_bfloat16* __restrict__ dst) {
+                                     const int* __restrict__ e, __nv_bfloat16* __restrict__ dst,
+                                     const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ double tile[32][33];
     const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -677,7 +694,7 @@ size_t ozaki_gemm_ws(int M, int N, int K) { return ozaki_operand_ws(M, K) + ozak
 // or, with skew, of the skew matrix whose strict lower triangle src holds
 // (leading dimension ks).  Rows are padded to a multiple of 128, K to 64.
 int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long rs, long long ks, double sgn, int skew,
-                void* ws, size_t ws_bytes, OzOperand* op) {
+                void* ws, size_t ws_bytes, OzOperand* op, const int* skip) {
     if (rows <= 0 || K <= 0) return SKEW_ERR_UNSUPPORTED;
     const long long Kp = rup(K, OKA), Rp = rup(rows, OM);
     Carve cv(ws, ws_bytes);
@@ -691,27 +708,27 @@ int ozaki_split(cudaStream_t st, int rows, int K, const double* src, long long r
             return cuda_fail(err);
         if (skew) {
             const unsigned T = (unsigned)((rows + 31) / 32);
-            oz_skew_rowmax_kernel<<<dim3(T, T), dim3(32, 8), 0, st>>>(rows, src, ks, rowmax);
+            oz_skew_rowmax_kernel<<<dim3(T, T), dim3(32, 8), 0, st>>>(rows, src, ks, rowmax, skip);
         } else {
             oz_rowmax_cols_kernel<<<dim3((unsigned)((rows + 31) / 32), (unsigned)((K + 255) / 256)), dim3(32, 8), 0,
-                                    st>>>(rows, K, src, ks, rowmax);
+                                    st>>>(rows, K, src, ks, rowmax, skip);
         }
-        oz_exp_from_max_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, rowmax, e);
+        oz_exp_from_max_kernel<<<(rows + 255) / 256, 256, 0, st>>>(rows, rowmax, e, skip);
         if (skew)
             oz_split_skew_kernel<<<dim3((unsigned)((Rp + 31) / 32), (unsigned)((Kp + 31) / 32)), dim3(32, 8), 0, st>>>(
-                rows, (int)Rp, (int)Kp, src, ks, e, d);
+                rows, (int)Rp, (int)Kp, src, ks, e, d, skip);
         else
             oz_split_cols_kernel<<<dim3((unsigned)((Rp + 31) / 32), (unsigned)((Kp + 31) / 32)), dim3(32, 8), 0, st>>>(
-                rows, K, (int)Rp, (int)Kp, src, ks, sgn, e, d);
+                rows, K, (int)Rp, (int)Kp, src, ks, sgn, e, d, skip);
         count_launch(3);
     } else if (ks == 1) {
         oz_split_rows_kernel<<<(int)(Rp < 32768 ? Rp : 32768), 256, 0, st>>>(rows, K, (int)Rp, (int)Kp, src, rs, sgn, e,
-                                                                            d);
+                                                                            d, skip);
         count_launch(1);
     } else {
-        oz_exp_kernel<<<(int)(rows < 16384 ? rows : 16384), 256, 0, st>>>(rows, K, src, rs, ks, e, 0);
+        oz_exp_kernel<<<(int)(rows < 16384 ? rows : 16384), 256, 0, st>>>(rows, K, src, rs, ks, e, 0, skip);
         oz_split_kernel<<<dim3((unsigned)((Kp + 255) / 256), (unsigned)(Rp < 65535 ? Rp : 65535)), 256, 0, st>>>(
-            rows, K, (int)Rp, (int)Kp, src, rs, ks, sgn, e, d);
+            rows, K, (int)Rp, (int)Kp, src, rs, ks, sgn, e, d, skip);
         count_launch(2);
     }
     op->d = d;
@@ -738,7 +755,8 @@ OzOperand oz_view(const OzOperand& o, int r0, int k0, int rows, int K) {
 
 // C = alpha * A B^T + beta C from split operands (A: M x K, B: N x K).
 int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, double alpha, double beta, double* C,
-                   long long ldc, int* status, int slices, int lower, int ksplit, double* part, size_t part_elems) {
+                   long long ldc, int* status, int slices, int lower, int ksplit, double* part, size_t part_elems,
+                   const int* skip, const int* s_dyn) {
     const int M = A.rows, N = B.rows, K = A.K;
     if (M <= 0 || N <= 0) return 0;
     if (B.K != K || slices < 1 || slices > SL) return SKEW_ERR_UNSUPPORTED;
@@ -768,6 +786,8 @@ int ozaki_gemm_pre(cudaStream_t st, const OzOperand& A, const OzOperand& B, doub
     p.ldc = ldc;
     p.status = status;
     p.s = slices;
+    p.skip = skip;
+    p.s_dyn = s_dyn;
     p.lower = lower;
     p.mt = (M + OM - 1) / OM;
     p.nt = (N + ON - 1) / ON;

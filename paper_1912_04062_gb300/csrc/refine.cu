@@ -72,7 +72,14 @@ struct RefineScalars {
     double rnorm2;                 // sum |R~_ij|^2 over the E11 block (orthogonality before the update)
     unsigned long long where;      // packed location of the max: i | j << 20 | blk << 40
     unsigned long long umax_bits;  // max |U_ij| of the update (as double bits)
+    // the iteration's control on the device (no host round trip): once done is
+    // set the remaining launches of the loop return at once
+    int done;
+    int su;            // digit slices of this iteration's update product
+    RefineInfo hist;   // per-iteration record, copied to the host at the end
 };
+
+SK_DEV double refine_tau(int n, const RefineScalars* sc) { return 64.0 * n * DBL_EPSILON * sc->lmax; }
 
 constexpr int KC = 16;  // largest cluster handled by Rayleigh-Ritz
 
@@ -100,7 +107,8 @@ SK_DEV double tskew(const double* __restrict__ T, long long ld, int a, int b) {
 }
 // lambda~_i = Sg_ii / G_ii = (T_XY - T_YX)_ii / (XX + YY)_ii
 __global__ void refine_lambda_kernel(int m, int n, const double* __restrict__ Wg, const double* __restrict__ T,
-                                     double* __restrict__ lt) {
+                                     double* __restrict__ lt, const int* __restrict__ skip) {
+    if (*skip) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const long long ld = n;
@@ -136,7 +144,10 @@ SK_DEV bool separated(double li, double lj, cplx Sg, cplx R, double tau, double 
 // close[i] = 1 when the neighbours i and i+1 (eigenvalues sorted descending)
 // are not separated
 __global__ void refine_close_kernel(int m, int n, const double* __restrict__ Wg, const double* __restrict__ T,
-                                    const double* __restrict__ lt, double tau, double rho, int* __restrict__ close) {
+                                    const double* __restrict__ lt, const RefineScalars* sc, double rho,
+                                    int* __restrict__ close) {
+    if (sc->done) return;
+    const double tau = refine_tau(n, sc);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     int c = 0;
@@ -157,8 +168,9 @@ __global__ void refine_close_kernel(int m, int n, const double* __restrict__ Wg,
 // Ritz values (descending) replace lt, and cid marks the members.
 __global__ void refine_rr_kernel(int m, int n, const double* __restrict__ Wg, const double* __restrict__ T,
                                  const int* __restrict__ close, double* __restrict__ lt, int* __restrict__ cid,
-                                 double* __restrict__ Vc, int* __restrict__ nbig) {
+                                 double* __restrict__ Vc, int* __restrict__ nbig, const int* __restrict__ skip) {
     __shared__ cplx L[KC][KC], K[KC][KC], W[KC][KC];
+    if (*skip) return;
     const int c0 = blockIdx.x;
     if (c0 >= m || threadIdx.x != 0) return;
     const bool start = close[c0] && (c0 == 0 || !close[c0 - 1]);
@@ -305,8 +317,10 @@ SK_DEV int basis_of(int i, int m, const int* __restrict__ cid, const double* __r
 // m x m planes of Et (E~11 real, imag, E~21 real, imag).
 __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg, const double* __restrict__ T,
                                      const double* __restrict__ lt, const int* __restrict__ cid,
-                                     const double* __restrict__ Vc, double tau, double* __restrict__ Et,
+                                     const double* __restrict__ Vc, double* __restrict__ Et,
                                      RefineScalars* sc) {
+    if (sc->done) return;
+    const double tau = refine_tau(n, sc);
     const long long ld = n, mm = (long long)m * m;
     double emax = 0.0, rn2 = 0.0;
     unsigned int close = 0;
@@ -383,6 +397,7 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
 // by conj(B)); then U = [[Er + Fr, Ei + Fi], [Fi - Ei, Er - Fr]].
 __global__ void refine_u_kernel(int m, const int* __restrict__ cid, const double* __restrict__ Vc,
                                 const double* __restrict__ Et, double* __restrict__ U, RefineScalars* sc) {
+    if (sc->done) return;
     const long long mm = (long long)m * m, ldu = 2LL * m;
     double umax = 0.0;
     for (int j = blockIdx.y; j < m; j += gridDim.y)
@@ -423,7 +438,7 @@ __global__ void refine_u_kernel(int m, const int* __restrict__ cid, const double
 }
 
 __global__ void refine_reset_kernel(RefineScalars* sc) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !sc->done) {
         sc->emax_bits = 0ULL;
         sc->nclose = 0u;
         sc->rnorm2 = 0.0;
@@ -432,8 +447,10 @@ __global__ void refine_reset_kernel(RefineScalars* sc) {
     }
 }
 
-__global__ void lmax_kernel(int m, const double* __restrict__ lt, double* __restrict__ out) {
+__global__ void lmax_kernel(int m, const double* __restrict__ lt, double* __restrict__ out,
+                            const int* __restrict__ skip) {
     __shared__ double red[32];
+    if (*skip) return;
     double v = 0.0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) v = fmax(v, fabs(lt[i]));
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -444,6 +461,46 @@ __global__ void lmax_kernel(int m, const double* __restrict__ lt, double* __rest
         for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) r = fmax(r, red[w]);
         *out = r;
     }
+}
+
+// The loop's state at the start of a refinement.
+__global__ void refine_init_kernel(RefineScalars* sc) {
+    if (threadIdx.x == 0) {
+        sc->done = 0;
+        sc->su = 8;
+        sc->hist = RefineInfo{};
+    }
+}
+
+// After the corrections of iteration it: the update's digit slices (M + M U
+// with |U| <= umax needs a relative error of about 2^-62 / umax: entries of M
+// ~ n^-1/2, rows of length n, so fewer slices serve once the corrections are
+// small) and the iteration's record.
+__global__ void refine_su_kernel(RefineScalars* sc, int it, int sl) {
+    if (threadIdx.x != 0 || sc->done) return;
+    const double umax = __longlong_as_double((long long)sc->umax_bits);
+    int su = 8;
+    if (umax > 0.0) {
+        su = (int)ceil((62.0 + log2(umax)) / 7.0);
+        su = su < 3 ? 3 : (su > 8 ? 8 : su);
+    }
+    sc->su = su;
+    if (it < 8) {
+        sc->hist.emax[it] = __longlong_as_double((long long)sc->emax_bits);
+        sc->hist.nclose[it] = (int)sc->nclose;
+        sc->hist.rnorm[it] = sqrt(sc->rnorm2);
+        sc->hist.where[it] = (long long)sc->where;
+        sc->hist.slices[it] = sl;
+        sc->hist.uslices[it] = su;
+    }
+}
+
+// End of iteration it: the next iteration would move the vectors by about
+// emax^2, so the loop stops once emax is below 1e-8 (the FP64 level).
+__global__ void refine_decide_kernel(RefineScalars* sc, int it) {
+    if (threadIdx.x != 0 || sc->done) return;
+    sc->hist.iterations = it + 1;
+    if (__longlong_as_double((long long)sc->emax_bits) < 1e-8) sc->done = 1;
 }
 
 // 2-D grid for the m x m element kernels: x over i (256 threads a block), y
@@ -499,6 +556,50 @@ size_t refine_ws(int n) {
     return cv.off + 256;
 }
 
+namespace {
+// The iteration record of a refinement the device drives reaches the host in
+// stream order through one pinned buffer (allocated at the first refinement
+// that is not being captured into a graph; a captured one before it keeps no
+// record).
+struct StatsCopy {
+    RefineInfo* pinned = nullptr;
+    RefineInfo* target = nullptr;
+    bool pending = false;
+};
+StatsCopy& stats_copy() {
+    static StatsCopy c;
+    return c;
+}
+
+int refine_stats_enqueue(cudaStream_t st, const RefineInfo* d_hist, RefineInfo* target) {
+    StatsCopy& c = stats_copy();
+    if (!c.pinned) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (const cudaError_t e = cudaStreamIsCapturing(st, &cs)) return cuda_fail(e);
+        if (cs != cudaStreamCaptureStatusNone) return 0;
+        void* p = nullptr;
+        if (cudaMallocHost(&p, sizeof(RefineInfo)) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        c.pinned = static_cast<RefineInfo*>(p);
+    }
+    if (const cudaError_t e = cudaMemcpyAsync(c.pinned, d_hist, sizeof(RefineInfo), cudaMemcpyDeviceToHost, st))
+        return cuda_fail(e);
+    c.target = target;
+    c.pending = true;
+    return 0;
+}
+}  // namespace
+
+void refine_stats_flush() {
+    StatsCopy& c = stats_copy();
+    if (c.pending && c.target && c.pinned) *c.target = *c.pinned;
+    c.pending = false;
+}
+
+void refine_stats_discard() { stats_copy().pending = false; }
+
 int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, double* M, int maxit, void* ws,
            size_t ws_bytes, int* status, RefineInfo* info, double rho) {
     if (n % 2 || n < 2) return SKEW_ERR_UNSUPPORTED;
@@ -512,16 +613,24 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
     }
     count_launch();
     if (info) {
-        info->iterations = 0;
-        for (int k = 0; k < 8; k++) {
-            info->emax[k] = 0.0;
-            info->nclose[k] = info->slices[k] = info->uslices[k] = 0;
-        }
+        refine_stats_discard();
+        *info = RefineInfo{};
     }
     struct KindScope {  // products of this loop are timed as their own kind
         KindScope() { g_kt_ozaki_kind = KT_OZAKI_REFINE; }
         ~KindScope() { g_kt_ozaki_kind = KT_OZAKI; }
     } kind_scope;
+    // The loop's decisions (tau from the largest Rayleigh quotient, the
+    // update's digit slices, the stop) are taken on the device, and once the
+    // loop has stopped the remaining launches return at once: no host round
+    // trip, so the solve stays asynchronous and graph-capturable.  With
+    // kernel timing on, the host reads the update's slice count before
+    // launching the update (each timed launch records its work) and stops
+    // launching when the device does; both paths take the same decisions.
+    const bool host_driven = kt_enabled();
+    const int* skip = &w.sc->done;
+    refine_init_kernel<<<1, 32, 0, st>>>(w.sc);
+    count_launch();
     const long long ldn = n;
     // row r of S is minus column r of S (skew), read contiguously
     OzOperand os{}, omc{}, oam{}, ou{}, omr{};
@@ -536,79 +645,73 @@ int refine(cudaStream_t st, int n, const double* A, int lda, double* lambda, dou
         // Wg = M^T M (symmetric), AM = S M, T = M^T (S M) (skew): FP64-accurate
         // tensor-core products, Wg and T on their lower triangle; the column
         // slices of M serve all three
-        rc = ozaki_split(st, n, n, M, ldn, 1, 1.0, 0, w.oz_mc, w.oz_bytes, &omc);
+        rc = ozaki_split(st, n, n, M, ldn, 1, 1.0, 0, w.oz_mc, w.oz_bytes, &omc, skip);
         if (rc) return rc;
-        rc = ozaki_gemm_pre(st, omc, omc, 1.0, 0.0, w.Wg, ldn, status, sl, 1);
+        rc = ozaki_gemm_pre(st, omc, omc, 1.0, 0.0, w.Wg, ldn, status, sl, 1, 1, nullptr, 0, skip);
         if (rc) return rc;
-        rc = ozaki_gemm_pre(st, os, omc, 1.0, 0.0, w.AM, ldn, status, sl, 0);
+        rc = ozaki_gemm_pre(st, os, omc, 1.0, 0.0, w.AM, ldn, status, sl, 0, 1, nullptr, 0, skip);
         if (rc) return rc;
-        rc = ozaki_split(st, n, n, w.AM, ldn, 1, 1.0, 0, w.oz_amu, w.oz_bytes, &oam);
+        rc = ozaki_split(st, n, n, w.AM, ldn, 1, 1.0, 0, w.oz_amu, w.oz_bytes, &oam, skip);
         if (rc) return rc;
-        rc = ozaki_gemm_pre(st, omc, oam, 1.0, 0.0, w.T, ldn, status, sl, 1);
+        rc = ozaki_gemm_pre(st, omc, oam, 1.0, 0.0, w.T, ldn, status, sl, 1, 1, nullptr, 0, skip);
         if (rc) return rc;
         {
             KtScope kt(st, KT_REFINE_AUX);
-            refine_lambda_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt);
+            refine_lambda_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt, skip);
             refine_reset_kernel<<<1, 32, 0, st>>>(w.sc);
-            lmax_kernel<<<1, 1024, 0, st>>>(m, w.lt, &w.sc->lmax);
-        }
-        count_launch(3);
-        double lmax = 0.0;
-        if (const cudaError_t e = cudaMemcpyAsync(&lmax, &w.sc->lmax, sizeof(double), cudaMemcpyDeviceToHost, st))
-            return cuda_fail(e);
-        if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
-        const double tau = 64.0 * n * DBL_EPSILON * lmax;
-        {
-            KtScope kt(st, KT_REFINE_AUX);
-            refine_close_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt, tau, rho, w.close);
-            refine_rr_kernel<<<m, 32, 0, st>>>(m, n, w.Wg, w.T, w.close, w.lt, w.cid, w.Vc, w.nbig);
+            lmax_kernel<<<1, 1024, 0, st>>>(m, w.lt, &w.sc->lmax, skip);
+            refine_close_kernel<<<(m + 127) / 128, 128, 0, st>>>(m, n, w.Wg, w.T, w.lt, w.sc, rho, w.close);
+            refine_rr_kernel<<<m, 32, 0, st>>>(m, n, w.Wg, w.T, w.close, w.lt, w.cid, w.Vc, w.nbig, skip);
             // E~ lives in the AM buffer (free once T is formed)
-            refine_etilde_kernel<<<grid2(m), 256, 0, st>>>(m, n, w.Wg, w.T, w.lt, w.cid, w.Vc, tau,
-                                                                          w.AM, w.sc);
+            refine_etilde_kernel<<<grid2(m), 256, 0, st>>>(m, n, w.Wg, w.T, w.lt, w.cid, w.Vc, w.AM, w.sc);
             refine_u_kernel<<<grid2(m), 256, 0, st>>>(m, w.cid, w.Vc, w.AM, w.U, w.sc);
+            refine_su_kernel<<<1, 32, 0, st>>>(w.sc, it, sl);
         }
-        count_launch(4);
-        RefineScalars h{};
-        if (const cudaError_t e = cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, st))
-            return cuda_fail(e);
-        if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
-        double emax, umax;
-        std::memcpy(&emax, &h.emax_bits, sizeof(double));
-        std::memcpy(&umax, &h.umax_bits, sizeof(double));
-        // M <- M + M U: with |U| <= umax the product needs a relative error of
-        // about 2^-62 / umax (entries of M ~ n^-1/2, rows of length n), so
-        // fewer slices serve once the corrections are small
+        count_launch(8);
+        // M <- M + M U with the device's slice count (read by the kernel), or
+        // with the host's copy of it when the launch is timed
         int su = 8;
-        if (umax > 0.0) {
-            su = (int)std::ceil((62.0 + std::log2(umax)) / 7.0);
-            su = su < 3 ? 3 : (su > 8 ? 8 : su);
+        const int* su_dev = &w.sc->su;
+        bool last = false;
+        if (host_driven) {
+            RefineScalars h{};
+            if (const cudaError_t e = cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, st))
+                return cuda_fail(e);
+            if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
+            if (h.done) break;
+            su = h.su;
+            su_dev = nullptr;
+            double emax;
+            std::memcpy(&emax, &h.emax_bits, sizeof(double));
+            last = emax < 1e-8;  // the device's stop rule (refine_decide_kernel)
         }
         // the product reads M's digit slices, taken before C is written
-        rc = ozaki_split(st, n, n, M, 1, ldn, 1.0, 0, w.oz_mr, w.oz_bytes, &omr);
+        rc = ozaki_split(st, n, n, M, 1, ldn, 1.0, 0, w.oz_mr, w.oz_bytes, &omr, skip);
         if (rc) return rc;
-        rc = ozaki_split(st, n, n, w.U, 2LL * m, 1, 1.0, 0, w.oz_amu, w.oz_bytes, &ou);
+        rc = ozaki_split(st, n, n, w.U, 2LL * m, 1, 1.0, 0, w.oz_amu, w.oz_bytes, &ou, skip);
         if (rc) return rc;
-        rc = ozaki_gemm_pre(st, omr, ou, 1.0, 1.0, M, ldn, status, su, 0);
+        rc = ozaki_gemm_pre(st, omr, ou, 1.0, 1.0, M, ldn, status, su, 0, 1, nullptr, 0, skip, su_dev);
         if (rc) return rc;
+        // lt is left unchanged once the loop has stopped, so the copy may run
         if (const cudaError_t e = cudaMemcpyAsync(lambda, w.lt, sizeof(double) * m, cudaMemcpyDeviceToDevice, st))
             return cuda_fail(e);
-        if (info) {
-            info->iterations = it + 1;
-            if (it < 8) {
-                info->emax[it] = emax;
-                info->nclose[it] = (int)h.nclose;
-                info->rnorm[it] = std::sqrt(h.rnorm2);
-                info->where[it] = (long long)h.where;
-                info->slices[it] = sl;
-                info->uslices[it] = su;
-            }
-        }
-        // the next iteration would move the vectors by ~emax^2: stop once that
-        // is below the FP64 level
-        if (emax < 1e-8) break;
+        refine_decide_kernel<<<1, 32, 0, st>>>(w.sc, it);
+        count_launch();
+        if (last) break;
     }
-    if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
-    return 0;
+    if (info) {
+        // the iteration record: read now when the host drives the loop,
+        // otherwise copied in stream order for refine_stats_flush()
+        if (host_driven) {
+            if (const cudaError_t e = cudaMemcpyAsync(info, &w.sc->hist, sizeof(RefineInfo), cudaMemcpyDeviceToHost, st))
+                return cuda_fail(e);
+            if (const cudaError_t e = cudaStreamSynchronize(st)) return cuda_fail(e);
+        } else {
+            rc = refine_stats_enqueue(st, &w.sc->hist, info);
+            if (rc) return rc;
+        }
+    }
+    return cuda_ok(cudaGetLastError());
 }
 
 }  // namespace sk

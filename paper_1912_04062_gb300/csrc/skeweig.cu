@@ -212,6 +212,7 @@ int run_solve(cudaStream_t st, int n, const double* A, int lda, int nev, double*
     }
     const int maxit = (o && (o->fault & SKEW_FAULT_INVIT_NOCONV)) ? 0 : 5;
     const unsigned spin_cap = (o && (o->fault & SKEW_FAULT_TINY_WAIT)) ? SK_TINY_SPIN_CAP : 0;
+    refine_stats_discard();
     last_refine_info() = RefineInfo{};  // iterations = 0 unless this solve refines
 
     mark(0);
@@ -393,6 +394,8 @@ int cuda_fail(cudaError_t e) {
     if (e != cudaSuccess) g_last_cuda_error.store(cudaGetErrorName(e), std::memory_order_relaxed);
     return SKEW_ERR_CUDA;
 }
+
+bool kt_enabled() { return ktimer().on; }
 
 int kt_begin(cudaStream_t st) {
     KTimer& t = ktimer();
@@ -1057,6 +1060,7 @@ int skew_kernel_timeline(int cap, int* kinds, double* start_ms, double* end_ms) 
 }
 
 int skew_refine_stats(double* emax, int* nclose, int cap) {
+    refine_stats_flush();
     const RefineInfo& r = last_refine_info();
     for (int i = 0; i < cap && i < 8; i++) {
         if (emax) emax[i] = r.emax[i];
@@ -1066,6 +1070,7 @@ int skew_refine_stats(double* emax, int* nclose, int cap) {
 }
 
 int skew_refine_trace(double* rnorm, long long* where, int cap) {
+    refine_stats_flush();
     const RefineInfo& r = last_refine_info();
     for (int i = 0; i < cap && i < 8; i++) {
         if (rnorm) rnorm[i] = r.rnorm[i];
@@ -1075,6 +1080,7 @@ int skew_refine_trace(double* rnorm, long long* where, int cap) {
 }
 
 int skew_refine_slices(int* slices, int* uslices, int cap) {
+    refine_stats_flush();
     const RefineInfo& r = last_refine_info();
     for (int i = 0; i < cap && i < 8; i++) {
         if (slices) slices[i] = r.slices[i];

@@ -2,12 +2,13 @@
 with a caller workspace and a device status word allocates nothing and does
 not synchronise, so its launches can be captured once and replayed).
 
-The FP64 form and the partial-vector refined mode (no refinement loop) are
-captured with torch's graph capture on the current stream and replayed on a
-new matrix written into the captured input buffer; the replay must equal a
-direct solve of that matrix bit for bit (the solve is deterministic).  The
-refined mode with a complete basis reads its convergence test on the host
-once per iteration and is documented as not capturable.
+The FP64 form, the partial-vector refined mode and the refined mode with a
+complete basis (whose refinement decides on the device and launches its
+whole iteration budget) are captured with torch's graph capture on the
+current stream and replayed on a new matrix written into the captured input
+buffer; the replay must equal a direct solve of that matrix bit for bit (the
+solve is deterministic).  With kernel timing on, the refinement takes the
+same decisions on the host: results and statistics must not change.
 """
 import numpy as np
 import pytest
@@ -22,7 +23,8 @@ def _dev():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("n,nev,mode", [(300, 150, "fp64"), (513, 40, "fp64"), (400, 37, "refined")])
+@pytest.mark.parametrize("n,nev,mode", [(300, 150, "fp64"), (513, 40, "fp64"), (400, 37, "refined"),
+                                        (300, 150, "refined"), (642, 321, "refined")])
 def test_solve_replays_from_a_cuda_graph(n, nev, mode):
     import torch
     import inputs
@@ -61,3 +63,37 @@ def test_solve_replays_from_a_cuda_graph(n, nev, mode):
     import oracle
     lam_o, *_ = oracle.skew_eig(A2, nev, vectors=False)
     assert np.max(np.abs(got[0].cpu().numpy() - lam_o)) <= 1e-12 * lam_o[0]
+
+
+def test_refinement_decides_alike_on_device_and_host():
+    # the same refined solve with kernel timing off (device-driven loop) and on
+    # (host-driven loop): identical values and iteration records
+    import torch
+    import inputs
+    import paper_1912_04062_gb300 as sk
+    n = 770
+    nev = n // 2
+    A, _ = inputs.prescribed(n, seed=23)
+    dA = sk.fortran(torch.from_numpy(np.asfortranarray(A)).cuda())
+    opts = sk.Options(mode=sk.SKEW_MODE_MIXED_REFINED)
+    ws = torch.empty(sk.workspace_size(n, nev, opts), dtype=torch.uint8, device="cuda")
+    out = []
+    for timing in (False, True):
+        sk.kernel_timing(timing)
+        try:
+            lam = torch.empty(nev, dtype=torch.float64, device="cuda")
+            Zr, Zi = sk.fortran_empty(n, nev), sk.fortran_empty(n, nev)
+            info = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+            assert sk.skew_eig_ex(dA, nev, lam, Zr, Zi, ws, info, opts) == 0
+            torch.cuda.synchronize()
+        finally:
+            sk.kernel_timing(False)
+        assert int(info.item()) == 0
+        it, emax, nclose = sk.refine_stats()
+        sl, su = sk.refine_slices()
+        assert 1 <= it <= 8 and emax[-1] < 1e-8, (it, emax)
+        out.append((lam.cpu(), Zr.cpu(), Zi.cpu(), it, list(emax), list(sl), list(su)))
+    a, b = out
+    for x, y in zip(a[:3], b[:3]):
+        assert torch.equal(x, y)
+    assert a[3:] == b[3:]
