@@ -12,6 +12,9 @@ dominant kernel kind against the peak of its own arithmetic.  Accuracy (all
 columns, FP64 products) and the FP64 form's solve are measured after the timed
 region.  ``e2e`` repeats the solve through ``skew_eig_host`` (pinned host
 buffers, host<->device copies inside each call; one warm-up call first).
+``batched`` (after the main line's own measurements) times the batched
+workload -- 2000 matrices of log-uniform order in [32, 1024], one
+graph-captured persistent launch -- against a loop of single solves.
 
 ``cpu_baseline`` times the FP64 CPU oracle on all host cores on a bounded
 sample (the same construction at order --cpu-n, scaled to n by n^3), with
@@ -77,13 +80,13 @@ KIND_KERNELS = {
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel from an ncu capture, valid while the kernel's source file is the one
 # captured (sha256 prefix); otherwise the traffic is reported as null.
-# ozaki_refine: one 4096^3 product (8 slices) read + wrote 2.34e9 B; an
+# ozaki_refine: one 4096^3 product (8 slices) read + wrote 2.336e9 B; an
 # n = 16384 refinement launch covers 64x the tiles x K of a full product (32x
 # for a lower-triangle one; two of each per iteration: x48 on average).
 TRAFFIC = {
-    "ozaki_refine": {"bytes": 2.34e9 * 48, "n": 16384, "file": "paper_1912_04062_gb300/csrc/ozaki_gemm.cu",
-                     "sha256_16": "4a236564973d3593",
-                     "how": "ncu capture of a 4096^3 product (2.34e9 B, profiles/ozaki_gemm_kernel_4096cube.md) "
+    "ozaki_refine": {"bytes": 2.336e9 * 48, "n": 16384, "file": "paper_1912_04062_gb300/csrc/ozaki_gemm.cu",
+                     "sha256_16": "c48ce4e367c48c3a",
+                     "how": "ncu capture of a 4096^3 product (2.336e9 B, profiles/ozaki_gemm_kernel_4096cube.md) "
                             "scaled by tiles x K (x48)"},
 }
 
@@ -191,6 +194,9 @@ def parse():
     p.add_argument("--gemm", default="4096,4096,4096,8,0",
                    help="M,N,K,slices,lower of the gemm workload")
     p.add_argument("--batch-count", type=int, default=2000)
+    p.add_argument("--batched-leg", type=int, default=2,
+                   help="single workload: timed replays of the batched workload reported beside the main line "
+                        "(0 = leave it out)")
     p.add_argument("--clustered-n", type=int, default=32768, help="clustered: order of the workload")
     p.add_argument("--clustered-reps", type=int, default=1, help="clustered: solves per case (fastest kept)")
     p.add_argument("--retune", action="store_true", help="batched: tune the launch on this batch")
@@ -523,6 +529,24 @@ def run_ours(args, ws, rank, local):
         torch.cuda.empty_cache()
     total_F = 4.0 / 3.0 * n ** 3 + 8.0 * nev * n * n
 
+    # ---- the batched workload (one graph-captured persistent launch against
+    # a loop of single solves), reported beside the main line
+    batched = None
+    if args.batched_leg > 0:
+        r = batched_leg(args, ws, rank, local, steps=args.batched_leg, warmup=1, loop_warmup=False)
+        batched = {"workload": (f"{args.batch_count} skew-symmetric matrices, n log-uniform in [32, 1024] (odd and "
+                                "even), prescribed spectra l ~ U(0.1, 10), Haar Q, nev = n/2, FP64"),
+                   "s": r["t_batched"], "replays": args.batched_leg, "loop_of_single_solves_s": r["t_loop"],
+                   "speedup_vs_loop": r["t_loop"] / r["t_batched"],
+                   "fp64_equiv_tflops": r["flops"] / r["t_batched"] / 1e12,
+                   "launch": {"kernels_per_batch": r["launches"], "cuda_graph": True, "ctas_per_sm": r["cfg"][0],
+                              "smem_max_n": r["cfg"][1], "source": r["source"]},
+                   "accuracy_sample": {"matrices": r["sampled"], "worst_resid_scaled": r["worst"]["resid"],
+                                       "worst_orth_scaled": r["worst"]["orth"], "all_info_zero": r["info_ok"]},
+                   "count_this_rank": r["count"], "input_build_s": round(r["input_build_s"], 1),
+                   "clocks": r["clocks"]}
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu and ws == 1:
         r = cpu_sample(args.cpu_n, n)
@@ -556,20 +580,22 @@ def run_ours(args, ws, rank, local):
                "kernels_sum_over_step": sum(kms.values()) / ms,
                "stages_ms": {k: round(v, 3) for k, v in stage_ms.items()},
                "accuracy": acc, "fp64_form": fp64, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "batched": batched,
                "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(out), flush=True)
 
 
-def run_batched(args, ws, rank, local):
-    """Batched workload: count matrices, n log-uniform in [32, 1024] (odd and
-    even), prescribed spectra l ~ U(0.1, 10), Haar Q, all n/2 pairs, FP64; under
-    torchrun each rank takes its longest-processing-time share (no collective
-    on the data path).  The batch is one plan (skew_batched_plan_*): one
-    persistent launch, captured in a CUDA graph and replayed; its launch
-    configuration comes from the tuning table for this GPU, or is tuned on the
-    batch (--retune, or no entry).  Timed against a loop of single solves
-    (skew_eig_ex) on the same device matrices; an accuracy sample is checked on
-    the device."""
+def batched_leg(args, ws, rank, local, steps, warmup, loop_warmup=True):
+    """Batched workload: args.batch_count matrices, n log-uniform in [32,
+    1024] (odd and even), prescribed spectra l ~ U(0.1, 10), Haar Q, all n/2
+    pairs, FP64; under torchrun each rank takes its longest-processing-time
+    share (no collective on the data path).  The batch is one plan
+    (skew_batched_plan_*): one persistent launch, captured in a CUDA graph and
+    replayed; its launch configuration comes from the tuning table for this
+    GPU, or is tuned on the batch (--retune, or no entry).  Timed against a
+    loop of single solves (skew_eig_ex) on the same device matrices; an
+    accuracy sample is checked on the device.  Returns the measurements (every
+    rank; times are the max over ranks)."""
     import torch
 
     import inputs
@@ -579,11 +605,14 @@ def run_batched(args, ws, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
+    t_in = time.perf_counter()
     sizes = [int(x) for x in inputs.batch_sizes(args.batch_count, seed=5)]
     mine = sk.shard_lpt(sizes, ws)[rank]
     items = inputs.batch(sizes=sizes, seed=5)
     mine_set = set(mine)
     mats = [sk.fortran(torch.from_numpy(np_a).to(dev)) for k, (np_a, _) in enumerate(items) if k in mine_set]
+    del items
+    t_in = time.perf_counter() - t_in
     nevs = [int(m.shape[0]) // 2 for m in mats]
     my_sizes = [int(m.shape[0]) for m in mats]
     count = len(mats)
@@ -626,22 +655,22 @@ def run_batched(args, ws, rank, local):
             if code != 0:
                 raise RuntimeError(f"single solve failed: {code}")
 
-    def timed(fn, steps):
+    def timed(fn, nsteps):
         barrier(ws)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(nsteps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return max_over_ranks(ws, e0.elapsed_time(e1) / steps / 1e3)
+        return max_over_ranks(ws, e0.elapsed_time(e1) / nsteps / 1e3)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched()
     clk = ClockSampler(local)
     clk.start()
-    t_batched = timed(batched, args.steps)
+    t_batched = timed(batched, steps)
     clocks = clk.stop()
     info_ok = bool((plan.info[:count] == 0).all().item())
     # accuracy sample: every 50th matrix of this rank's share
@@ -652,24 +681,39 @@ def run_batched(args, ws, rank, local):
         res, orth, fro = sk.metrics(mats[k], lams[k], Zr[k], Zi[k])
         worst["resid"] = max(worst["resid"], res / (n * eps * fro))
         worst["orth"] = max(worst["orth"], orth / (n * eps))
-    loop()  # warm-up of the single-solve path
+    if loop_warmup:
+        loop()  # warm-up of the single-solve path
+    else:  # the single-solve path is warm already: one solve of the largest order
+        k = my_sizes.index(nmax)
+        if sk.skew_eig_ex(mats[k], nevs[k], lams[k], Zr[k], Zi[k], w1, i1, opts) != 0:
+            raise RuntimeError("single solve failed")
     t_loop = timed(loop, 1)
     flops = sum(4.0 / 3.0 * n ** 3 + 8.0 * (n // 2) * n * n for n in my_sizes)
+    return {"t_batched": t_batched, "t_loop": t_loop, "count": count, "my_sizes": my_sizes, "cfg": cfg,
+            "source": source, "launches": int(launches), "flops": flops, "worst": worst,
+            "sampled": len(range(0, count, 50)), "info_ok": info_ok, "tuned": tuned, "clocks": clocks,
+            "input_build_s": t_in}
+
+
+def run_batched(args, ws, rank, local):
+    """The batched workload on its own JSON line (batched_leg)."""
+    r = batched_leg(args, ws, rank, local, args.steps, args.warmup)
     if rank == 0:
+        t_batched, my_sizes, cfg = r["t_batched"], r["my_sizes"], r["cfg"]
         out = {"metric": f"batched skew eigensolve time ({args.batch_count} matrices, n log-uniform in [32, 1024], "
                          "nev = n/2)", "value": t_batched, "unit": "s", "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_batched * 1e3, "higher_is_better": False, "scaling": "strong",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": "batched", "count": args.batch_count, "count_this_rank": count,
+               "config": {"workload": "batched", "count": args.batch_count, "count_this_rank": r["count"],
                           "sum_n3": float(sum(float(n) ** 3 for n in my_sizes)),
-                          "launch": {"ctas_per_sm": cfg[0], "smem_max_n": cfg[1], "source": source,
-                                     "kernels_per_batch": int(launches), "cuda_graph": True},
+                          "launch": {"ctas_per_sm": cfg[0], "smem_max_n": cfg[1], "source": r["source"],
+                                     "kernels_per_batch": r["launches"], "cuda_graph": True},
                           "parallelism": f"lpt-shard x{ws}" if ws > 1 else "single"},
-               "fp64_equiv_tflops": flops / t_batched / 1e12,
-               "loop_of_single_solves_s": t_loop, "speedup_vs_loop": t_loop / t_batched,
-               "accuracy_sample": {"matrices": len(range(0, count, 50)), "worst_resid_scaled": worst["resid"],
-                                   "worst_orth_scaled": worst["orth"], "all_info_zero": info_ok},
-               "tuning": tuned, "gpu_launches": int(launches) * args.steps, "clocks": clocks}
+               "fp64_equiv_tflops": r["flops"] / t_batched / 1e12,
+               "loop_of_single_solves_s": r["t_loop"], "speedup_vs_loop": r["t_loop"] / t_batched,
+               "accuracy_sample": {"matrices": r["sampled"], "worst_resid_scaled": r["worst"]["resid"],
+                                   "worst_orth_scaled": r["worst"]["orth"], "all_info_zero": r["info_ok"]},
+               "tuning": r["tuned"], "gpu_launches": r["launches"] * args.steps, "clocks": r["clocks"]}
         print(json.dumps(out), flush=True)
 
 
