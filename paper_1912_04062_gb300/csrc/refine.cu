@@ -322,7 +322,8 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
     if (sc->done) return;
     const double tau = refine_tau(n, sc);
     const long long ld = n, mm = (long long)m * m;
-    double emax = 0.0, rn2 = 0.0;
+    // largest |E|^2 (the square root is taken once, after the loop)
+    double emax2 = 0.0, rn2 = 0.0;
     unsigned int close = 0;
     unsigned long long wloc = 0;
     // element (i, j), e = j m + i: threads along i, the grid's y along j (no
@@ -331,21 +332,32 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const long long e = (long long)j * m + i;
         const double li = lt[i], lj = lt[j];
-        int ia[KC], ja[KC];
-        cplx ic[KC], jc[KC];
-        const int ki = basis_of(i, m, cid, Vc, ia, ic);
-        const int kj = basis_of(j, m, cid, Vc, ja, jc);
-        cplx Sg = {0, 0}, G = {0, 0}, Sf = {0, 0}, F = {0, 0};
-        for (int a = 0; a < ki; a++)
-            for (int b = 0; b < kj; b++) {
-                const Blocks bl = blocks(ia[a], ja[b], m, ld, Wg, T);
-                const cplx h = cmul(cconj(ic[a]), jc[b]);   // conj(B_ai) B_bj
-                const cplx t = cmul(ic[a], jc[b]);          // B_ai B_bj
-                Sg = cadd(Sg, cmul(h, bl.Sg));
-                G = cadd(G, cmul(h, bl.G));
-                Sf = cadd(Sf, cmul(t, bl.Sf));
-                F = cadd(F, cmul(t, bl.F));
-            }
+        cplx Sg, G, Sf, F;
+        if (cid[i] < 0 && cid[j] < 0) {
+            // neither index belongs to a cluster: B is the identity there, and
+            // the rotated blocks are the blocks themselves
+            const Blocks bl = blocks(i, j, m, ld, Wg, T);
+            Sg = bl.Sg;
+            G = bl.G;
+            Sf = bl.Sf;
+            F = bl.F;
+        } else {
+            int ia[KC], ja[KC];
+            cplx ic[KC], jc[KC];
+            const int ki = basis_of(i, m, cid, Vc, ia, ic);
+            const int kj = basis_of(j, m, cid, Vc, ja, jc);
+            Sg = G = Sf = F = cplx{0, 0};
+            for (int a = 0; a < ki; a++)
+                for (int b = 0; b < kj; b++) {
+                    const Blocks bl = blocks(ia[a], ja[b], m, ld, Wg, T);
+                    const cplx h = cmul(cconj(ic[a]), jc[b]);   // conj(B_ai) B_bj
+                    const cplx t = cmul(ic[a], jc[b]);          // B_ai B_bj
+                    Sg = cadd(Sg, cmul(h, bl.Sg));
+                    G = cadd(G, cmul(h, bl.G));
+                    Sf = cadd(Sf, cmul(t, bl.Sf));
+                    F = cadd(F, cmul(t, bl.F));
+                }
+        }
         const bool same = (cid[i] >= 0 && cid[i] == cid[j]);
         const cplx R = {(i == j ? 1.0 : 0.0) - G.r, -G.i};
         cplx E11, E21;
@@ -353,8 +365,8 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
         if (i != j && !same && separated(li, lj, Sg, R, tau, RHO1)) {
             const double d = lj - li;
             E11 = {(Sg.r + lj * R.r) / d, (Sg.i + lj * R.i) / d};
-            const double a = hypot(E11.r, E11.i);
-            if (a > emax) { emax = a; wloc = (unsigned long long)i | ((unsigned long long)j << 20); }
+            const double a = E11.r * E11.r + E11.i * E11.i;
+            if (a > emax2) { emax2 = a; wloc = (unsigned long long)i | ((unsigned long long)j << 20); }
         } else {
             E11 = cscale(R, 0.5);
             if (i != j && !same) close++;
@@ -363,9 +375,9 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
         const double d2 = lj + li;
         if (fabs(d2) > fmax(tau, RHO1 * (hypot(Sf.r, Sf.i) + fabs(lj) * hypot(F.r, F.i)))) {
             E21 = cscale(num, 1.0 / d2);
-            const double a = hypot(E21.r, E21.i);
-            if (a > emax) {
-                emax = a;
+            const double a = E21.r * E21.r + E21.i * E21.i;
+            if (a > emax2) {
+                emax2 = a;
                 wloc = (unsigned long long)i | ((unsigned long long)j << 20) | (1ULL << 40);
             }
         } else {
@@ -377,6 +389,7 @@ __global__ void refine_etilde_kernel(int m, int n, const double* __restrict__ Wg
         Et[2 * mm + e] = E21.r;
         Et[3 * mm + e] = E21.i;
     }
+    double emax = sqrt(emax2);
     for (int o = 16; o > 0; o >>= 1) {
         const double oe = __shfl_xor_sync(0xffffffffu, emax, o);
         const unsigned long long ow = __shfl_xor_sync(0xffffffffu, wloc, o);
