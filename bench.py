@@ -102,7 +102,7 @@ def _sha16(rel):
 
 def kind_flops(kind, form, n, nev, b=64):
     """Algorithmic flops of one solve for the kinds whose launches do not
-    carry them (SURVEY-style counts: Q_trd 4 n^2 nev, the FP64 form's
+    carry them (nominal counts: Q_trd 4 n^2 nev, the FP64 form's
     GEMM-type work 4/3 n^3 + 4 n^2 nev, the chase about 6 b n^2, the panel
     QRs about b n^2); None where no count is defined."""
     if kind == "qtrd":
