@@ -96,7 +96,9 @@ typedef enum {
 
 typedef struct {
     int mode;          /* skew_mode; default SKEW_MODE_FP64 */
-    int band;          /* panel width = band width b, a multiple of 64; 0 -> 64 */
+    int band;          /* panel width = band width b; 0 -> 64.  The kernels are
+                          built for b = 64: any other value returns
+                          SKEW_ERR_UNSUPPORTED */
     int check_finite;  /* 1: scan A for NaN/Inf first (SKEW_ERR_NONFINITE) */
     int fault;         /* SKEW_FAULT_* bits, tests only; 0 in production */
     int refine_iters;  /* mixed modes: maximum refinement iterations (1..8); 0 -> 8 */
