@@ -472,7 +472,7 @@ def run_ours(args, ws, rank, local):
         oc = opts.c()
 
         def host_solve():
-            code = L.skew_eig_host(n, sk._ptr(hA), n, nev, sk._ptr(hl), sk._ptr(hZr), sk._ptr(hZi),
+            code = L.skew_eig_host(n, sk._hptr(hA), n, nev, sk._hptr(hl), sk._hptr(hZr), sk._hptr(hZi),
                                    sk.ctypes.byref(oc), sk._stream(stream))
             if code != 0:
                 raise RuntimeError(f"host solve failed: {code}")

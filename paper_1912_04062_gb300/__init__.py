@@ -171,7 +171,43 @@ def fortran_empty(rows: int, cols: int, device="cuda"):
 
 
 def _ptr(t):
-    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+    """Address of a CUDA tensor (None -> NULL) for an argument the C ABI takes
+    as a DEVICE pointer.  A host tensor is refused: its address handed to a
+    kernel would be dereferenced on the GPU."""
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_cuda:
+        raise TypeError("expected a CUDA tensor for a device-pointer argument")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(t):
+    """Address of a host tensor (None -> NULL) for the host-buffer entry point
+    skew_eig_host."""
+    if t is None:
+        return ctypes.c_void_p(0)
+    if t.is_cuda:
+        raise TypeError("expected a host tensor for a host-pointer argument")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _out(t, dtype, numel, what):
+    """Device address of an output buffer of the given dtype holding at least
+    `numel` elements (None -> NULL)."""
+    if t is not None and (t.dtype != dtype or t.numel() < numel):
+        raise TypeError(f"{what}: expected {dtype} with at least {numel} elements, got {t.dtype} {tuple(t.shape)}")
+    return _ptr(t)
+
+
+def _zbuf(Z, n, nev, what):
+    """Device address of an eigenvector block: float64, n rows, at least nev
+    columns, column-major (None -> NULL)."""
+    torch = _torch()
+    if Z is not None and (Z.dtype != torch.float64 or Z.dim() != 2 or Z.shape[0] != n or Z.shape[1] < nev
+                          or (n > 1 and Z.stride(0) != 1)):
+        raise TypeError(f"{what}: expected a column-major float64 {n} x {nev} tensor, got {Z.dtype} "
+                        f"{tuple(Z.shape)} strides {tuple(Z.stride())}")
+    return _ptr(Z)
 
 
 def _ld(t):
@@ -239,13 +275,15 @@ def workspace_size(n: int, nev: int, opts: Options | None = None, vectors: bool 
 
 def skew_eig_ex(A, nev: int, lam, Zr, Zi, workspace, d_info, opts: Options | None = None, stream=None) -> int:
     """Asynchronous solve into caller buffers; returns the launch status."""
+    torch = _torch()
     A = _as_device_f64(A)
     n = A.shape[0]
     o = (opts or Options()).c()
     ldz = _ld(Zr) if Zr is not None else max(1, n)
-    return lib().skew_eig_ex(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), ldz, ctypes.byref(o),
-                             _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(d_info),
-                             _stream(stream))
+    return lib().skew_eig_ex(n, _ptr(A), _ld(A), nev, _out(lam, torch.float64, nev, "lam"),
+                             _zbuf(Zr, n, nev, "Zr"), _zbuf(Zi, n, nev, "Zi"), ldz, ctypes.byref(o),
+                             _ptr(workspace), workspace.numel() * workspace.element_size(),
+                             _out(d_info, torch.int32, 1, "d_info"), _stream(stream))
 
 
 STAGES = ["ingest", "band_reduce", "band_pack", "chase", "tridiag", "dmap", "qtrd", "qband", "refine", "output"]
@@ -254,12 +292,14 @@ STAGES = ["ingest", "band_reduce", "band_pack", "chase", "tridiag", "dmap", "qtr
 def skew_eig_profile(A, nev: int, lam, Zr, Zi, workspace, opts: Options | None = None, stream=None):
     """Synchronous solve into caller buffers with per-stage CUDA-event times.
     Returns (status, {stage: ms})."""
+    torch = _torch()
     A = _as_device_f64(A)
     n = A.shape[0]
     o = (opts or Options()).c()
     ldz = _ld(Zr) if Zr is not None else max(1, n)
     ms = (ctypes.c_float * len(STAGES))()
-    code = lib().skew_eig_profile(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), ldz, ctypes.byref(o),
+    code = lib().skew_eig_profile(n, _ptr(A), _ld(A), nev, _out(lam, torch.float64, nev, "lam"),
+                                  _zbuf(Zr, n, nev, "Zr"), _zbuf(Zi, n, nev, "Zi"), ldz, ctypes.byref(o),
                                   _ptr(workspace), workspace.numel() * workspace.element_size(), ms,
                                   _stream(stream))
     return code, dict(zip(STAGES, [float(x) for x in ms]))
@@ -572,14 +612,14 @@ def launch_count() -> int:
 def skew_eig_host(A, nev: int, vectors: bool = True, opts: Options | None = None, stream=None):
     """Solve from host (ideally pinned) float64 tensors; returns host tensors."""
     torch = _torch()
-    A = fortran(A.to(torch.float64))
+    A = fortran(A.to(device="cpu", dtype=torch.float64))
     n = A.shape[0]
     pin = torch.cuda.is_available()
     lam = torch.empty(max(nev, 1), dtype=torch.float64, pin_memory=pin)
     Zr = torch.empty((nev, n), dtype=torch.float64, pin_memory=pin).t() if vectors else None
     Zi = torch.empty((nev, n), dtype=torch.float64, pin_memory=pin).t() if vectors else None
     o = (opts or Options()).c()
-    code = lib().skew_eig_host(n, _ptr(A), _ld(A), nev, _ptr(lam), _ptr(Zr), _ptr(Zi), ctypes.byref(o),
+    code = lib().skew_eig_host(n, _hptr(A), _ld(A), nev, _hptr(lam), _hptr(Zr), _hptr(Zi), ctypes.byref(o),
                                _stream(stream))
     _check(code, "skew_eig_host")
     return lam[:nev], Zr, Zi
