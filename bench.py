@@ -162,6 +162,20 @@ def select_roofline(kinds, form, n, nev, solves, peaks=None, traffic=None):
     return None
 
 
+def batched_roofline(sizes, nevs, seconds):
+    """Roofline entry of the batched launch: the one-step route's algorithmic
+    flops per matrix (tridiagonalisation 4/3 n^3, back-transformation of the
+    2 nev real columns through the reflectors 4 n^2 nev; bisection and inverse
+    iteration not counted) over the launch time, against the derived FP64 ALU
+    peak (the kernel is FP64 SIMT, one CTA per matrix)."""
+    flops = float(sum(4.0 / 3.0 * n ** 3 + 4.0 * n * n * k for n, k in zip(sizes, nevs)))
+    achieved = flops / seconds / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "flops": flops,
+            "kernel": "bt_persistent_kernel (FP64 SIMT, one CTA per matrix)",
+            "peak_note": f"derived FP64 ALU peak: 2 FMA/clk/SM x {SM_COUNT} SMs x {SM_MHZ:.0f} MHz"}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -539,6 +553,7 @@ def run_ours(args, ws, rank, local):
                    "s": r["t_batched"], "replays": args.batched_leg, "loop_of_single_solves_s": r["t_loop"],
                    "speedup_vs_loop": r["t_loop"] / r["t_batched"],
                    "fp64_equiv_tflops": r["flops"] / r["t_batched"] / 1e12,
+                   "roofline": batched_roofline(r["my_sizes"], [m // 2 for m in r["my_sizes"]], r["t_batched"]),
                    "launch": {"kernels_per_batch": r["launches"], "cuda_graph": True, "ctas_per_sm": r["cfg"][0],
                               "smem_max_n": r["cfg"][1], "source": r["source"]},
                    "accuracy_sample": {"matrices": r["sampled"], "worst_resid_scaled": r["worst"]["resid"],
@@ -710,6 +725,7 @@ def run_batched(args, ws, rank, local):
                                      "kernels_per_batch": r["launches"], "cuda_graph": True},
                           "parallelism": f"lpt-shard x{ws}" if ws > 1 else "single"},
                "fp64_equiv_tflops": r["flops"] / t_batched / 1e12,
+               "roofline": batched_roofline(my_sizes, [m // 2 for m in my_sizes], t_batched),
                "loop_of_single_solves_s": r["t_loop"], "speedup_vs_loop": r["t_loop"] / t_batched,
                "accuracy_sample": {"matrices": r["sampled"], "worst_resid_scaled": r["worst"]["resid"],
                                    "worst_orth_scaled": r["worst"]["orth"], "all_info_zero": r["info_ok"]},

@@ -134,3 +134,18 @@ def test_roofline_selection():
     assert bench.select_roofline(k, "mixed", n, nev, 1, peaks, traffic=t)["traffic"] is None
     t["ozaki_refine"]["sha256_16"] = bench._sha16("bench.py")
     assert bench.select_roofline(k, "mixed", n, nev, 1, peaks, traffic=t)["traffic"] == 1e11
+
+
+def test_batched_roofline():
+    sys.path.insert(0, ROOT)
+    import bench
+    # one n = 1024 matrix, all 512 pairs: 4/3 n^3 + 4 n^2 (n/2) = 10/3 n^3 flops
+    r = bench.batched_roofline([1024], [512], 1.0)
+    assert abs(r["flops"] - 10.0 / 3.0 * 1024 ** 3) < 1.0
+    assert abs(r["achieved"] - r["flops"] / 1e12) < 1e-12 and r["bound"] == "alu"
+    assert abs(r["peak"] - bench.FP64_PEAK_TFLOPS) < 1e-12 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
+    # the 2000-matrix batch in 2.39 s: a fraction of the FP64 pipe, well below 1
+    import inputs
+    sizes = [int(x) for x in inputs.batch_sizes(2000, seed=5)]
+    r = bench.batched_roofline(sizes, [m // 2 for m in sizes], 2.39)
+    assert 0.05 < r["frac"] < 1.0
